@@ -1,0 +1,177 @@
+/*
+ * sft.h — C ABI of the GB300 Gaussian-filtered discrete sparse Fourier transform.
+ *
+ * Problem (Section 2 and Algorithm 1 of Merhi, Zhang, Iwen, Christlieb, "A New Class of Fully
+ * Discrete Sparse Fourier Transforms"): given the N samples f_j = f(-pi + 2 pi j / N) of a
+ * length-N vector, any N >= 2, return a near best s-term approximation of its DFT
+ *     f_hat = F f,   F[w, j] = (-1)^w exp(-2 pi i w j / N) / N,   w in B = (-ceil(N/2), floor(N/2)],
+ * as at most s (frequency, coefficient) pairs.  The method (Algorithm 1) filters f with ceil(c2)
+ * modulated periodic Gaussians, evaluates each filtered function at the off-grid nodes of an
+ * unequally spaced SFT from a short window of f (Section 3.1, Lemma fewer_points_error), runs that
+ * SFT (prime-modulus DFT measurements, CRT identification, majority vote, median estimates,
+ * Appendix B), keeps each shift's in-band frequencies divided by the filter's Fourier coefficient,
+ * and returns the s largest.
+ *
+ * Conventions shared by every entry point
+ *  - Every pointer argument named *_dev is a CUDA device pointer on the current device; every
+ *    other pointer is host memory.  The caller owns all buffers it passes; the plan owns its own
+ *    device tables and scratch and frees them in sft_plan_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Execution entry
+ *    points only enqueue work and return; results are valid after the stream is synchronised.
+ *  - No entry point throws or aborts.  Each returns an sft_status; on failure the plan is left
+ *    usable (or untouched) and sft_last_error() gives a thread-local message.
+ *  - A plan is not re-entrant: two executions of one plan must not overlap on the GPU (they share
+ *    the plan's scratch).  Distinct plans may run concurrently on distinct streams.
+ */
+#ifndef SFT_H
+#define SFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFT_OK = 0,
+  SFT_EINVAL = 1,    /* invalid argument or plan parameters */
+  SFT_ENOMEM = 2,    /* device or host allocation failed (nothing leaked) */
+  SFT_ECUDA = 3,     /* a CUDA runtime call failed */
+  SFT_ETIMEOUT = 4,  /* a bounded device wait ran out (status word set by a kernel) */
+  SFT_EBUSY = 5      /* server full: request not admitted */
+} sft_status;
+
+/* Window half-widths of the paper's DMSFT-4 and DMSFT-6 implementations (Section 5). */
+enum { SFT_DMSFT4 = 4, SFT_DMSFT6 = 6 };
+
+typedef enum { SFT_FP32 = 0, SFT_FP64 = 1 } sft_precision;
+typedef enum { SFT_IN_C64 = 0, SFT_IN_C128 = 1 } sft_input_type;
+
+/*
+ * Method parameters.  Fill with sft_variant_init() and override fields.
+ *  kappa      window half-width: each filtered sample uses f_{j'-kappa..j'+kappa} (Lemma
+ *             fewer_points_error); SFT_DMSFT4 or SFT_DMSFT6, or any 1..48.
+ *  alpha,beta passband / filter parameters of Lemma Periodic_Gaussian_Decay and Algorithm 1:
+ *             c1 = beta sqrt(ln N)/N, L = ceil(N/(alpha sqrt(ln N))), ceil(alpha sqrt(ln N)/2) shifts.
+ *  K, c_p     number of prime moduli p_j of the inner SFT and their size, p_j >= c_p * s.
+ *  seed       selects the primes (the randomized inner SFT reads a random subset of moduli).
+ *  precision  SFT_FP32: window sums and DFTs in FP32 with FP32 accumulation, phases reduced exactly
+ *             as integers; the s winners are then re-estimated from the samples with exact
+ *             twiddles and compensated accumulation, medians and division in FP64.
+ *             SFT_FP64: every stage in FP64.
+ *  input      element type of f: SFT_IN_C64 (interleaved float re,im) or SFT_IN_C128 (double).
+ */
+typedef struct {
+  int32_t kappa;
+  int32_t precision;
+  int32_t input;
+  int32_t K;
+  double c_p;
+  double alpha;
+  double beta;
+  uint64_t seed;
+} sft_variant;
+
+typedef struct sft_plan_s* sft_plan_t;
+
+/* Plan description returned by sft_plan_info (host memory, filled by the library). */
+#define SFT_MAX_K 15
+#define SFT_MAX_SMALL 12
+#define SFT_MAX_SHIFTS 32
+typedef struct {
+  int64_t N;
+  int32_t s;
+  int32_t kappa;
+  int32_t K;                          /* number of prime moduli p_j */
+  int32_t n_small;                    /* number of small moduli t_l */
+  int32_t n_shifts;                   /* ceil(c2) */
+  int32_t n_sub;                      /* node subsets per prime: 1 + sum_l (t_l - 1) */
+  int64_t primes[SFT_MAX_K];
+  int32_t small[SFT_MAX_SMALL];
+  int64_t shifts[SFT_MAX_SHIFTS];     /* q_1 .. q_{n_shifts} */
+  int64_t L;                          /* band half-width ceil(N/(alpha sqrt(ln N))) */
+  double c1;                          /* Gaussian width beta sqrt(ln N)/N */
+  int64_t nodes;                      /* distinct nodes m = n_sub * sum_j p_j */
+  int32_t fft_size;                   /* power-of-two length of the chirp convolutions */
+  int32_t precision;
+  int32_t input;
+  int32_t reserved;
+} sft_plan_desc;
+
+/* Fill *v with the defaults: kappa 6 (DMSFT-6), FP32, complex64 input, K 5, c_p 3,
+ * alpha = beta = 1.5, seed 0.  Returns SFT_EINVAL if v is NULL. */
+sft_status sft_variant_init(sft_variant* v);
+
+/*
+ * Build a plan for length-N inputs and sparsity s (Algorithm 1, its set-up lines: c1, c2, L and the
+ * shifts q_j = -ceil(N/2) + 1 + (2j - 1) L).
+ *  n_shifts      0 = ceil(alpha sqrt(ln N)/2); otherwise that many shifts (must still cover B).
+ *  primes        NULL = K primes chosen by v->seed from the 4K smallest primes >= max(c_p s, 5);
+ *                else n_primes distinct primes (1 <= n_primes <= SFT_MAX_K) used as given.
+ *  small_moduli  NULL = the smallest primes, none equal to a p_j, until p_1 prod(t) >= N;
+ *                else n_small pairwise-coprime moduli >= 2, coprime to every p_j, p_1 prod >= N.
+ * Requires 2 <= N < 2^31, 1 <= s <= N, 2 kappa + 1 <= N, every p_j <= 8192 (FP32) or 4096 (FP64).
+ * Allocates the plan's device tables and scratch on the current device (sft_plan_device_bytes).
+ * On failure *out is set to NULL and nothing is leaked.
+ */
+sft_status sft_plan(sft_plan_t* out, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
+                    const int64_t* primes, int32_t n_primes, const int32_t* small_moduli,
+                    int32_t n_small);
+
+/*
+ * Run Algorithm 1 on f_dev (N elements of the plan's input type, 8-byte aligned; 16-byte
+ * alignment enables vector loads) and write, on `stream`:
+ *   out_freqs_dev[0..s)   int64 frequencies in B, sorted by |coefficient| descending, ties by the
+ *                         smaller frequency (Section 2's tie-break for R_s^opt);
+ *   out_coefs_dev[0..s)   complex128 (interleaved double re,im) coefficient estimates in the
+ *                         f_hat = F f convention;
+ *   out_count_dev[0]      int32 number of pairs written (<= s; unused slots are zeroed).
+ * Any of the three may be NULL only if all are NULL (a dry run that still executes every stage).
+ */
+sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_dev,
+                       void* out_coefs_dev, int32_t* out_count_dev, void* stream);
+
+/*
+ * Host-only, no device work: the moduli sft_plan would choose for (N, s, K, c_p, seed) when given
+ * NULL primes and NULL small moduli (Monte Carlo inner SFT: K primes drawn by a SplitMix64-seeded
+ * partial Fisher-Yates shuffle from the 4K smallest primes >= max(ceil(c_p s), 5), ascending; then
+ * the smallest primes t != p_j until p_1 prod(t) >= N).  primes_out holds K entries, small_out
+ * SFT_MAX_SMALL; *n_small_out receives the count.  SFT_EINVAL on bad arguments.
+ */
+sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
+                             int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);
+
+/* Release every device and host resource of the plan (NULL is a no-op).  The caller must ensure
+ * no execution of the plan is still running on the GPU. */
+sft_status sft_plan_destroy(sft_plan_t plan);
+
+/* Device bytes held by the plan (tables + scratch), for admission by memory budget. */
+size_t sft_plan_device_bytes(sft_plan_t plan);
+
+/* Copy the plan's parameters into *out (host). */
+sft_status sft_plan_info(sft_plan_t plan, sft_plan_desc* out);
+
+/*
+ * Expose one of the plan's intermediate device buffers (valid after an execution has completed),
+ * for stage-by-stage checks.  which:
+ *   0 samples  filtered samples h_q(x), [n_shifts][nodes] complex (FP32 or FP64 per precision);
+ *              node order: prime j, then node subset u (u = 0: the p_j nodes -pi + 2 pi k/p_j;
+ *              u >= 1: the p_j nodes offset by 2 pi k2 / t_l), then k = 0..p_j-1.
+ *   1 bins     length-p_j DFTs of every node subset, same layout as samples (eq. DFT_GKlam_Comp).
+ *   2 cand     int64 [n_shifts][sum_j p_j]: frequency identified in bin b of modulus p_j, or
+ *              INT64_MIN when the CRT representative lies outside B.
+ *   3 residues uint8 [n_shifts][sum_j p_j][n_small]: residue of bin b modulo each t_l.
+ *   4 voted    per-shift voted lists: int32 count[n_shifts] then records (see csrc).
+ * *bytes receives the buffer size.  Returns SFT_EINVAL for an unknown index.
+ */
+sft_status sft_plan_debug_buffer(sft_plan_t plan, int32_t which, void** dev_ptr, size_t* bytes);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* sft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFT_H */

@@ -1,0 +1,225 @@
+"""Python binding of the GB300 discrete sparse Fourier transform library (include/sft.h).
+
+Argument marshalling only: every step of the transform runs in the CUDA kernels of libsft.so.
+The functions keep the C names (sft_plan, sft_execute, ...).  Device buffers are passed as raw
+pointers; the torch helpers below only allocate outputs and pass tensor pointers and the current
+stream.  If the library has not been built, importing the package still works but every call
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SFT_OK, SFT_EINVAL, SFT_ENOMEM, SFT_ECUDA, SFT_ETIMEOUT, SFT_EBUSY = range(6)
+SFT_DMSFT4, SFT_DMSFT6 = 4, 6
+SFT_FP32, SFT_FP64 = 0, 1
+SFT_IN_C64, SFT_IN_C128 = 0, 1
+SFT_MAX_K, SFT_MAX_SMALL, SFT_MAX_SHIFTS = 15, 12, 32
+BUF_SAMPLES, BUF_BINS, BUF_CAND, BUF_RESID, BUF_COUNTERS, BUF_VOTED = range(6)
+
+_STATUS = {0: "SFT_OK", 1: "SFT_EINVAL", 2: "SFT_ENOMEM", 3: "SFT_ECUDA", 4: "SFT_ETIMEOUT",
+           5: "SFT_EBUSY"}
+
+
+class SftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sft_variant(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("input", ctypes.c_int32), ("K", ctypes.c_int32), ("c_p", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class sft_plan_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("s", ctypes.c_int32), ("kappa", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("n_small", ctypes.c_int32), ("n_shifts", ctypes.c_int32),
+                ("n_sub", ctypes.c_int32), ("primes", ctypes.c_int64 * SFT_MAX_K),
+                ("small", ctypes.c_int32 * SFT_MAX_SMALL),
+                ("shifts", ctypes.c_int64 * SFT_MAX_SHIFTS), ("L", ctypes.c_int64),
+                ("c1", ctypes.c_double), ("nodes", ctypes.c_int64), ("fft_size", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("input", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+EXPORTS = {
+    "sft_variant_init": (ctypes.c_int, [ctypes.POINTER(sft_variant)]),
+    "sft_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int32,
+                                ctypes.POINTER(sft_variant), ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "sft_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sft_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sft_plan_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "sft_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sft_plan_desc)]),
+    "sft_plan_debug_buffer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(ctypes.c_size_t)]),
+    "sft_last_error": (ctypes.c_char_p, []),
+    "sft_choose_moduli": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32)]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libsft.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsft.so not built ({path}); run paper_1706_02740_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != SFT_OK:
+        raise SftError(status, sft_last_error())
+
+
+def sft_last_error() -> str:
+    return load().sft_last_error().decode()
+
+
+def sft_variant_init(**overrides) -> sft_variant:
+    v = sft_variant()
+    _check(load().sft_variant_init(ctypes.byref(v)))
+    for k, val in overrides.items():
+        if not hasattr(v, k):
+            raise TypeError(f"unknown variant field {k}")
+        setattr(v, k, val)
+    return v
+
+
+class Plan:
+    """Owns an sft_plan_t; destroy() (or garbage collection) releases it."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def destroy(self):
+        if self.handle:
+            load().sft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().sft_plan_device_bytes(self.handle))
+
+    def info(self) -> dict:
+        return sft_plan_info(self)
+
+
+def sft_plan(N: int, s: int, variant: sft_variant | None = None, n_shifts: int = 0,
+             primes=None, small_moduli=None) -> Plan:
+    lib = load()
+    v = variant if variant is not None else sft_variant_init()
+    h = ctypes.c_void_p()
+    pp, np_ = None, 0
+    if primes is not None:
+        pp = (ctypes.c_int64 * len(primes))(*[int(p) for p in primes])
+        np_ = len(primes)
+    sp, ns = None, 0
+    if small_moduli is not None:
+        sp = (ctypes.c_int32 * max(1, len(small_moduli)))(*[int(t) for t in small_moduli])
+        ns = len(small_moduli)
+    _check(lib.sft_plan(ctypes.byref(h), int(N), int(s), ctypes.byref(v), int(n_shifts),
+                        pp, np_, sp, ns))
+    return Plan(h.value)
+
+
+def sft_execute(plan: Plan, f_dev: int, out_freqs_dev: int, out_coefs_dev: int,
+                out_count_dev: int, stream: int = 0):
+    _check(load().sft_execute(plan.handle, f_dev, out_freqs_dev, out_coefs_dev, out_count_dev,
+                              stream))
+
+
+def sft_choose_moduli(N: int, s: int, K: int = 5, c_p: float = 3.0, seed: int = 0):
+    """Host-only: the (primes, small moduli) sft_plan would choose."""
+    pr = (ctypes.c_int64 * K)()
+    sm = (ctypes.c_int32 * SFT_MAX_SMALL)()
+    ns = ctypes.c_int32()
+    _check(load().sft_choose_moduli(int(N), int(s), int(K), float(c_p), int(seed) & (2**64 - 1),
+                                    pr, sm, ctypes.byref(ns)))
+    return list(pr), list(sm[: ns.value])
+
+
+def sft_plan_info(plan: Plan) -> dict:
+    d = sft_plan_desc()
+    _check(load().sft_plan_info(plan.handle, ctypes.byref(d)))
+    return {
+        "N": d.N, "s": d.s, "kappa": d.kappa, "K": d.K, "n_small": d.n_small,
+        "n_shifts": d.n_shifts, "n_sub": d.n_sub, "primes": list(d.primes[: d.K]),
+        "small": list(d.small[: d.n_small]), "shifts": list(d.shifts[: d.n_shifts]),
+        "L": d.L, "c1": d.c1, "nodes": d.nodes, "fft_size": d.fft_size,
+        "precision": d.precision, "input": d.input,
+    }
+
+
+def sft_plan_debug_buffer(plan: Plan, which: int):
+    ptr = ctypes.c_void_p()
+    nbytes = ctypes.c_size_t()
+    _check(load().sft_plan_debug_buffer(plan.handle, int(which), ctypes.byref(ptr),
+                                        ctypes.byref(nbytes)))
+    return ptr.value, nbytes.value
+
+
+# ---------------------------------------------------------------------------------------------
+# torch conveniences (allocation of outputs, pointers, current stream)
+# ---------------------------------------------------------------------------------------------
+def execute_torch(plan: Plan, f, stream=None):
+    """Run sft_execute on a CUDA tensor f (complex64 or complex128); returns device tensors
+    (freqs int64 [s], coefs complex128 [s], count int32 [1]) on the same stream."""
+    import torch
+    info = sft_plan_info(plan)
+    s = info["s"]
+    dev = f.device
+    freqs = torch.empty(s, dtype=torch.int64, device=dev)
+    coefs = torch.empty(s, dtype=torch.complex128, device=dev)
+    count = torch.empty(1, dtype=torch.int32, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    sft_execute(plan, f.data_ptr(), freqs.data_ptr(), coefs.data_ptr(), count.data_ptr(),
+                st.cuda_stream)
+    return freqs, coefs, count
+
+
+class _DevArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3}
+
+
+def debug_tensor(plan: Plan, which: int, dtype, shape):
+    """Zero-copy torch view of one of the plan's intermediate device buffers."""
+    import torch
+    ptr, nbytes = sft_plan_debug_buffer(plan, which)
+    typestr = {torch.complex64: "<c8", torch.complex128: "<c16", torch.int64: "<i8",
+               torch.uint8: "|u1", torch.int32: "<i4"}[dtype]
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")

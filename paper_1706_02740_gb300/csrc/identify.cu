@@ -1,0 +1,153 @@
+// Kernels (c) and (d) of the inner SFT (Appendix B reading): identification and estimation.
+//
+// identify: for each shift q, prime p_j and bin b, the residue of the bin's frequency modulo each
+// small modulus t_l is the sub-bin of largest magnitude of the length-(p_j t_l) measurement that
+// folds onto b.  By the prime-factor (Good-Thomas) index map, those t_l sub-bins are a length-t_l
+// DFT over the node subsets offset by 2 pi k2 / t_l (k2 = 0 is the p_j nodes themselves):
+//     X_r = (1/t) sum_{k2 < t} Z_{k2}[b] e^{-2 pi i k2 r / t},   r = frequency mod t,
+// where Z_{k2} is the length-p_j measurement of subset k2.  The argmax breaks exact ties toward the
+// smaller sub-bin index u = (r - b) p_j^{-1} mod t.  Garner's mixed-radix CRT of (b mod p_j,
+// r_1 mod t_1, ...) then gives the representative in [0, p_j prod t), mapped to B or rejected.
+// All integer work is exact.
+//
+// vote: a frequency w found in bin b of p_j counts one vote for every prime p_j' whose bin
+// w mod p_j' reconstructed exactly w; it is kept when it has more than K/2 votes and is emitted
+// once, by the smallest such j'.  Its estimate is (-1)^w times the componentwise medians of
+// Z_0[w mod p_j'] over all K primes (eq. GSFT_Estimate).
+#include "cplx.cuh"
+#include "sft_internal.h"
+
+namespace sft {
+
+namespace {
+
+__device__ __forceinline__ void decode_bin(const DevPlan& d, int64_t gid, int& qi, int& j, int& b) {
+  qi = (int)(gid / d.Ptot);
+  const int bin = (int)(gid - (int64_t)qi * d.Ptot);
+  j = 0;
+  while (j + 1 < d.K && bin >= d.poff[j + 1]) ++j;
+  b = bin - d.poff[j];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) identify_kernel(DevPlan d) {
+  using C = typename Cx<R>::T;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)d.nq * d.Ptot) return;
+  int qi, j, b;
+  decode_bin(d, gid, qi, j, b);
+  const int p = d.p[j];
+  const C* Z = reinterpret_cast<const C*>(d.bins) + (int64_t)qi * d.m + d.nodeoff[j] + b;
+  const C* tw = reinterpret_cast<const C*>(d.twsmall);
+  const C z0 = Z[0];
+  int64_t x = b, Mx = p;
+  for (int l = 0; l < d.nT; ++l) {
+    const int t = d.t[l];
+    const C* Zl = Z + (int64_t)(d.subbase[l] - 1) * p;   // Zl[k2 * p] = Z_{k2}[b], k2 >= 1
+    const C* twl = tw + d.twoff[l];
+    const int pinv = d.pinv[j * d.nT + l];
+    const int bt = b % t;
+    R best = (R)-1;
+    int bestu = 1 << 30, bestr = 0;
+    for (int r = 0; r < t; ++r) {
+      C X = z0;
+      int idx = 0;
+      for (int k2 = 1; k2 < t; ++k2) {
+        idx += r;
+        if (idx >= t) idx -= t;                              // idx = k2 r mod t
+        X = cadd(X, cmul(Zl[(int64_t)k2 * p], __ldg(twl + idx)));
+      }
+      const R m2 = X.x * X.x + X.y * X.y;
+      const int u = (((r - bt) % t + t) % t) * pinv % t;
+      if (m2 > best || (m2 == best && u < bestu)) {
+        best = m2;
+        bestu = u;
+        bestr = r;
+      }
+    }
+    d.resid[gid * d.nT + l] = (uint8_t)bestr;
+    const int g = d.garner[j * d.nT + l];
+    const int xm = (int)(x % t);
+    const int v = (((bestr - xm) % t + t) % t) * g % t;
+    x += Mx * v;
+    Mx *= t;
+  }
+  const int64_t N = d.N;
+  int64_t w = (x <= N / 2) ? x : x - d.Mj[j];
+  d.cand[gid] = (w > -((N + 1) / 2)) ? w : kNoFreq;
+}
+
+template <typename T>
+__device__ __forceinline__ void sort_small(T* a, int n) {
+  for (int i = 1; i < n; ++i) {
+    T v = a[i];
+    int k = i - 1;
+    while (k >= 0 && a[k] > v) { a[k + 1] = a[k]; --k; }
+    a[k + 1] = v;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ double median_sorted(const T* a, int n) {
+  return (n & 1) ? (double)a[n / 2] : 0.5 * ((double)a[n / 2 - 1] + (double)a[n / 2]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) vote_kernel(DevPlan d) {
+  using C = typename Cx<R>::T;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)d.nq * d.Ptot) return;
+  const int64_t w = d.cand[gid];
+  if (w == kNoFreq) return;
+  int qi, j, b;
+  decode_bin(d, gid, qi, j, b);
+  const int64_t* cq = d.cand + (int64_t)qi * d.Ptot;
+  int cnt = 0, jmin = d.K;
+  int bb[kMaxK];
+  for (int jj = 0; jj < d.K; ++jj) {
+    bb[jj] = (int)fmod64(w, d.p[jj]);
+    if (cq[d.poff[jj] + bb[jj]] == w) {
+      ++cnt;
+      if (jj < jmin) jmin = jj;
+    }
+  }
+  if (cnt < d.K / 2 + 1 || jmin != j) return;
+  const C* Zq = reinterpret_cast<const C*>(d.bins) + (int64_t)qi * d.m;
+  R re[kMaxK], im[kMaxK];
+  for (int jj = 0; jj < d.K; ++jj) {
+    const C y = Zq[d.nodeoff[jj] + bb[jj]];
+    re[jj] = y.x;
+    im[jj] = y.y;
+  }
+  sort_small(re, d.K);
+  sort_small(im, d.K);
+  const double sg = (w & 1) ? -1.0 : 1.0;
+  Voted rec;
+  rec.w = w;
+  rec.zre = sg * median_sorted(re, d.K);
+  rec.zim = sg * median_sorted(im, d.K);
+  rec.votes = cnt;
+  rec.jmin = jmin;
+  const int slot = atomicAdd(d.counters + qi, 1);
+  if (slot < d.vcap) d.voted[(int64_t)qi * d.vcap + slot] = rec;
+}
+
+}  // namespace
+
+cudaError_t launch_identify(const DevPlan& d, cudaStream_t st) {
+  const int64_t n = (int64_t)d.nq * d.Ptot;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (d.prec == SFT_FP32) identify_kernel<float><<<grid, 256, 0, st>>>(d);
+  else identify_kernel<double><<<grid, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vote(const DevPlan& d, cudaStream_t st) {
+  const int64_t n = (int64_t)d.nq * d.Ptot;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (d.prec == SFT_FP32) vote_kernel<float><<<grid, 256, 0, st>>>(d);
+  else vote_kernel<double><<<grid, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace sft

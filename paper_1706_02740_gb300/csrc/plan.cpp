@@ -1,0 +1,389 @@
+// Host side of a plan: Algorithm 1's parameters, the inner SFT's moduli, and the constant tables
+// the kernels read (all computed in FP64 with integer-exact phase reduction, then stored in the
+// plan's precision).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "sft_internal.h"
+
+namespace sft {
+
+namespace {
+
+using cd = std::complex<double>;
+const double kPi = 3.14159265358979323846;
+
+// SplitMix64 (Steele, Lea and Flood, 2014; constants as published by Vigna).
+uint64_t splitmix64(uint64_t* state) {
+  *state += 0x9E3779B97F4A7C15ULL;
+  uint64_t z = *state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+bool is_prime(int64_t n) {
+  if (n < 2) return false;
+  if (n < 4) return true;
+  if (n % 2 == 0) return false;
+  for (int64_t i = 3; i * i <= n; i += 2)
+    if (n % i == 0) return false;
+  return true;
+}
+
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a < 0 ? -a : a;
+}
+
+// Inverse of a modulo m (a, m coprime, m >= 1) by the extended Euclidean algorithm.
+int64_t inv_mod(int64_t a, int64_t m) {
+  if (m == 1) return 0;
+  int64_t g = m, x = 0, x1 = 1, a1 = ((a % m) + m) % m;
+  while (a1) {
+    int64_t qq = g / a1;
+    int64_t t = g - qq * a1; g = a1; a1 = t;
+    t = x - qq * x1; x = x1; x1 = t;
+  }
+  return ((x % m) + m) % m;
+}
+
+// The inner SFT's K primes: a seeded partial Fisher-Yates draw from the 4K smallest primes
+// >= max(ceil(c_p s), 5), returned ascending (randomized inner SFT reading a random subset of moduli).
+std::vector<int32_t> choose_primes(int32_t s, int K, double c_p, uint64_t seed) {
+  int64_t lo = std::max<int64_t>((int64_t)ceil(c_p * (double)s), 5);
+  std::vector<int64_t> pool;
+  for (int64_t n = lo; (int)pool.size() < 4 * K; ++n)
+    if (is_prime(n)) pool.push_back(n);
+  uint64_t state = seed;
+  for (int i = 0; i < K; ++i) {
+    uint64_t r = splitmix64(&state);
+    size_t j = (size_t)i + (size_t)(r % (uint64_t)(pool.size() - (size_t)i));
+    std::swap(pool[i], pool[j]);
+  }
+  std::vector<int32_t> out(pool.begin(), pool.begin() + K);
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+// Smallest primes t, none equal to a p_j, until p_1 * prod(t) >= N.
+std::vector<int32_t> choose_small(int64_t N, const std::vector<int32_t>& primes) {
+  std::vector<int32_t> T;
+  int64_t prod = primes[0];
+  for (int32_t t = 2; prod < N; ++t) {
+    if (is_prime(t) && std::find(primes.begin(), primes.end(), t) == primes.end()) {
+      T.push_back(t);
+      prod *= t;
+    }
+  }
+  return T;
+}
+
+// In-place iterative radix-2 FFT (forward, exp(-2 pi i n k / M)), M a power of two, used once per
+// plan to transform the chirp filter.
+void host_fft(std::vector<cd>& a) {
+  const size_t M = a.size();
+  for (size_t i = 1, j = 0; i < M; ++i) {
+    size_t bit = M >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= M; len <<= 1) {
+    for (size_t i = 0; i < M; i += len) {
+      for (size_t k = 0; k < len / 2; ++k) {
+        double ang = -2.0 * kPi * (double)k / (double)len;
+        cd w(cos(ang), sin(ang));
+        cd u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+    }
+  }
+}
+
+cd expi_turns(int64_t num, int64_t den) {
+  // exp(2 pi i num / den) with num reduced exactly modulo den first
+  int64_t r = ((num % den) + den) % den;
+  double a = 2.0 * kPi * (double)r / (double)den;
+  return cd(cos(a), sin(a));
+}
+
+template <typename T>
+void put(std::vector<char>& blob, size_t off, const std::vector<cd>& v, bool fp64) {
+  if (fp64) {
+    double* d = reinterpret_cast<double*>(blob.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) { d[2 * i] = v[i].real(); d[2 * i + 1] = v[i].imag(); }
+  } else {
+    float* d = reinterpret_cast<float*>(blob.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) {
+      d[2 * i] = (float)v[i].real(); d[2 * i + 1] = (float)v[i].imag();
+    }
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
+                      const int64_t* primes_in, int32_t n_primes, const int32_t* small_in,
+                      int32_t n_small) {
+  DevPlan& d = P->d;
+  memset(&d, 0, sizeof(d));
+  if (!v) { set_error("variant is NULL"); return SFT_EINVAL; }
+  if (N < 2 || N >= (int64_t(1) << 31)) { set_error("need 2 <= N < 2^31"); return SFT_EINVAL; }
+  if (s < 1 || s > N) { set_error("need 1 <= s <= N"); return SFT_EINVAL; }
+  if (v->kappa < 1 || v->kappa > kMaxKappa) { set_error("kappa must be in 1..48"); return SFT_EINVAL; }
+  if (2 * (int64_t)v->kappa + 1 > N) { set_error("window 2*kappa+1 exceeds N"); return SFT_EINVAL; }
+  if (v->precision != SFT_FP32 && v->precision != SFT_FP64) { set_error("bad precision"); return SFT_EINVAL; }
+  if (v->input != SFT_IN_C64 && v->input != SFT_IN_C128) { set_error("bad input type"); return SFT_EINVAL; }
+  if (!(v->alpha >= 1.0) || !(v->beta > 0.0) || !(v->c_p > 0.0)) {
+    set_error("need alpha >= 1, beta > 0, c_p > 0"); return SFT_EINVAL;
+  }
+  const bool fp64 = v->precision == SFT_FP64;
+
+  // ---- Algorithm 1 set-up: c1, c2, L, shifts
+  const double lnN = log((double)N);
+  const double c1 = v->beta * sqrt(lnN) / (double)N;
+  const int64_t L = (int64_t)ceil((double)N / (v->alpha * sqrt(lnN)));
+  int64_t nq = n_shifts > 0 ? n_shifts : (int64_t)ceil(v->alpha * sqrt(lnN) / 2.0);
+  if (nq < 1 || nq > kMaxQ) { set_error("number of shifts out of range 1..32"); return SFT_EINVAL; }
+  if (2 * nq * L < N) { set_error("the bands [q-L, q+L) do not cover B"); return SFT_EINVAL; }
+  const int64_t ceil_half = (N + 1) / 2;
+
+  // ---- moduli
+  std::vector<int32_t> primes;
+  if (primes_in) {
+    if (n_primes < 1 || n_primes > kMaxK) { set_error("n_primes must be 1..15"); return SFT_EINVAL; }
+    for (int i = 0; i < n_primes; ++i) {
+      if (primes_in[i] < 2 || primes_in[i] > (1 << 20) || !is_prime(primes_in[i])) {
+        set_error("primes must be primes in [2, 2^20]"); return SFT_EINVAL;
+      }
+      primes.push_back((int32_t)primes_in[i]);
+    }
+    std::sort(primes.begin(), primes.end());
+    if (std::adjacent_find(primes.begin(), primes.end()) != primes.end()) {
+      set_error("primes must be distinct"); return SFT_EINVAL;
+    }
+  } else {
+    if (v->K < 1 || v->K > kMaxK) { set_error("K must be 1..15"); return SFT_EINVAL; }
+    if (v->c_p * (double)s > 1.0e6) { set_error("c_p * s too large"); return SFT_EINVAL; }
+    primes = choose_primes(s, v->K, v->c_p, v->seed);
+  }
+  std::vector<int32_t> small;
+  if (small_in) {
+    if (n_small < 0 || n_small > kMaxT) { set_error("n_small must be 0..12"); return SFT_EINVAL; }
+    for (int i = 0; i < n_small; ++i) {
+      if (small_in[i] < 2 || small_in[i] > 64) { set_error("small moduli must be in 2..64"); return SFT_EINVAL; }
+      small.push_back(small_in[i]);
+    }
+  } else {
+    small = choose_small(N, primes);
+    if ((int)small.size() > kMaxT) { set_error("too many small moduli"); return SFT_EINVAL; }
+  }
+  for (size_t a = 0; a < small.size(); ++a)
+    for (size_t b = a + 1; b < small.size(); ++b)
+      if (gcd64(small[a], small[b]) != 1) { set_error("small moduli must be pairwise coprime"); return SFT_EINVAL; }
+  for (int32_t p : primes)
+    for (int32_t t : small)
+      if (gcd64(p, t) != 1) { set_error("every p_j must be coprime to every small modulus"); return SFT_EINVAL; }
+  {
+    // p_1 * prod(t) >= N, computed without overflow
+    int64_t prod = primes[0];
+    for (int32_t t : small) { if (prod >= N) break; prod *= t; }
+    if (prod < N) { set_error("p_1 * prod(small moduli) must be >= N"); return SFT_EINVAL; }
+  }
+  const int K = (int)primes.size();
+  const int nT = (int)small.size();
+  int nsub = 1;
+  for (int32_t t : small) nsub += t - 1;
+  if (nsub > kMaxSub) { set_error("too many node subsets (sum of t_l - 1 must be < 128)"); return SFT_EINVAL; }
+  const int32_t pmax = primes.back();
+  int M = 64;
+  while (M < 2 * pmax - 1) M <<= 1;
+  if (M > (fp64 ? kMaxFFT64 : kMaxFFT32)) {
+    set_error(fp64 ? "FP64 plans need every p_j <= 4096" : "FP32 plans need every p_j <= 8192");
+    return SFT_EINVAL;
+  }
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+
+  // ---- fill the device-plan scalars
+  d.N = N; d.s = s; d.kappa = v->kappa; d.K = K; d.nT = nT; d.nq = (int32_t)nq; d.nsub = nsub;
+  d.prec = v->precision; d.input = v->input;
+  d.fftM = M; d.fftLog2 = logM; d.pmax = pmax;
+  int64_t sump = 0;
+  for (int j = 0; j < K; ++j) {
+    d.p[j] = primes[j];
+    d.poff[j] = (int32_t)sump;
+    d.nodeoff[j] = sump * nsub;
+    sump += primes[j];
+    int64_t Mj = primes[j];
+    for (int32_t t : small) Mj *= t;
+    d.Mj[j] = Mj;
+  }
+  d.poff[K] = (int32_t)sump;
+  d.nodeoff[K] = sump * nsub;
+  d.Ptot = (int32_t)sump;
+  d.m = sump * nsub;
+  int sb = 1, tw = 0;
+  d.sub_l[0] = -1; d.sub_k2[0] = 0;
+  for (int l = 0; l < nT; ++l) {
+    d.t[l] = small[l];
+    d.subbase[l] = sb;
+    d.twoff[l] = tw;
+    for (int k2 = 1; k2 < small[l]; ++k2) { d.sub_l[sb] = (int8_t)l; d.sub_k2[sb] = (int8_t)k2; ++sb; }
+    tw += small[l];
+  }
+  std::vector<int64_t> shifts;
+  for (int64_t jq = 1; jq <= nq; ++jq) shifts.push_back(-ceil_half + 1 + (2 * jq - 1) * L);
+  for (int i = 0; i < nq; ++i) d.q[i] = shifts[i];
+  d.L = L;
+  d.c1 = c1;
+  d.G0 = 1.0 / ((double)N * c1);
+  d.gamma = 2.0 * kPi * kPi / (((double)N * c1) * ((double)N * c1));
+  d.vcap = (int32_t)sump;
+  {
+    const double far = (double)N - v->kappa - 0.5;
+    if (d.gamma * far * far < 40.0) {
+      set_error("N too small for these filter parameters (periodic images of g would matter)");
+      return SFT_EINVAL;
+    }
+  }
+
+  // ---- constant tables (host, FP64), laid out in one blob
+  const size_t cs = fp64 ? 16 : 8;
+  const int W = 2 * v->kappa + 1;
+  size_t off = 0;
+  const size_t o_T = off;      off = align256(off + (size_t)nq * W * cs);
+  const size_t o_chirp = off;  off = align256(off + (size_t)K * pmax * cs);
+  const size_t o_vhat = off;   off = align256(off + (size_t)K * M * cs);
+  const size_t o_fftw = off;   off = align256(off + (size_t)M * cs);
+  const size_t o_tws = off;    off = align256(off + (size_t)std::max(tw, 1) * cs);
+  const size_t o_wp = off;     off = align256(off + (size_t)K * pmax * 8);
+  const size_t o_gar = off;    off = align256(off + (size_t)K * std::max(nT, 1) * 4);
+  const size_t o_pinv = off;   off = align256(off + (size_t)K * std::max(nT, 1) * 4);
+  const size_t table_bytes = off;
+  std::vector<char> blob(table_bytes, 0);
+  {
+    std::vector<cd> Tt((size_t)nq * W);
+    for (int qi = 0; qi < nq; ++qi)
+      for (int i = -v->kappa; i <= v->kappa; ++i)
+        Tt[(size_t)qi * W + (i + v->kappa)] = expi_turns(-(shifts[qi] % N) * i, N);
+    put<cd>(blob, o_T, Tt, fp64);
+  }
+  {
+    std::vector<cd> ch((size_t)K * pmax, cd(0, 0)), vh((size_t)K * M), wp((size_t)K * pmax, cd(0, 0));
+    for (int j = 0; j < K; ++j) {
+      const int64_t p = primes[j];
+      std::vector<cd> V(M, cd(0, 0));
+      for (int64_t n = 0; n < p; ++n) {
+        cd w = expi_turns(-((n * n) % (2 * p)), 2 * p);  // exp(-pi i n^2 / p)
+        ch[(size_t)j * pmax + n] = w;
+        V[n] = std::conj(w);
+        if (n > 0) V[M - n] = std::conj(w);
+        wp[(size_t)j * pmax + n] = expi_turns(-n, p);
+      }
+      host_fft(V);
+      for (int n = 0; n < M; ++n) vh[(size_t)j * M + n] = V[n] / ((double)M * (double)p);
+    }
+    put<cd>(blob, o_chirp, ch, fp64);
+    put<cd>(blob, o_vhat, vh, fp64);
+    put<cd>(blob, o_wp, wp, false);
+  }
+  {
+    std::vector<cd> fw(M);
+    for (int n = 0; n < M; ++n) fw[n] = expi_turns(-n, M);
+    put<cd>(blob, o_fftw, fw, fp64);
+    std::vector<cd> ts(std::max(tw, 1), cd(1, 0));
+    for (int l = 0; l < nT; ++l)
+      for (int n = 0; n < small[l]; ++n) ts[d.twoff[l] + n] = expi_turns(-n, small[l]);
+    put<cd>(blob, o_tws, ts, fp64);
+    int32_t* gar = reinterpret_cast<int32_t*>(blob.data() + o_gar);
+    int32_t* pin = reinterpret_cast<int32_t*>(blob.data() + o_pinv);
+    for (int j = 0; j < K; ++j) {
+      int64_t Mprev = primes[j];
+      for (int l = 0; l < nT; ++l) {
+        gar[j * nT + l] = (int32_t)inv_mod(Mprev % small[l], small[l]);
+        pin[j * nT + l] = (int32_t)inv_mod(primes[j] % small[l], small[l]);
+        Mprev *= small[l];
+      }
+    }
+  }
+
+  // ---- scratch layout
+  size_t soff = align256(table_bytes);
+  const size_t o_samples = soff; soff = align256(soff + (size_t)nq * d.m * cs);
+  const size_t o_bins = soff;    soff = align256(soff + (size_t)nq * d.m * cs);
+  const size_t o_cand = soff;    soff = align256(soff + (size_t)nq * sump * 8);
+  const size_t o_resid = soff;   soff = align256(soff + (size_t)nq * sump * std::max(nT, 1));
+  const size_t o_cnt = soff;     soff = align256(soff + (size_t)(nq + 4) * 4);
+  const size_t o_voted = soff;   soff = align256(soff + (size_t)nq * d.vcap * sizeof(Voted));
+  const size_t o_pool = soff;    soff = align256(soff + (size_t)nq * s * sizeof(Pooled));
+  const size_t o_win = soff;     soff = align256(soff + (size_t)s * sizeof(Pooled));
+  const size_t o_ybuf = soff;    soff = align256(soff + (size_t)s * K * sizeof(double2));
+  const size_t total = soff;
+
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc((void**)&base, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc of plan memory failed: ") + cudaGetErrorString(e));
+    return SFT_ENOMEM;
+  }
+  P->allocations.push_back(base);
+  e = cudaMemcpy(base, blob.data(), table_bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_error(std::string("copy of plan tables failed: ") + cudaGetErrorString(e));
+    free_plan(P);
+    return SFT_ECUDA;
+  }
+  d.Ttab = base + o_T; d.chirp = base + o_chirp; d.vhat = base + o_vhat; d.fftw = base + o_fftw;
+  d.twsmall = base + o_tws; d.wp32 = reinterpret_cast<const float2*>(base + o_wp);
+  d.garner = reinterpret_cast<const int32_t*>(base + o_gar);
+  d.pinv = reinterpret_cast<const int32_t*>(base + o_pinv);
+  d.samples = base + o_samples; d.bins = base + o_bins;
+  d.cand = reinterpret_cast<int64_t*>(base + o_cand);
+  d.resid = reinterpret_cast<uint8_t*>(base + o_resid);
+  d.counters = reinterpret_cast<int32_t*>(base + o_cnt);
+  d.voted = reinterpret_cast<Voted*>(base + o_voted);
+  d.pool = reinterpret_cast<Pooled*>(base + o_pool);
+  d.winners = reinterpret_cast<Pooled*>(base + o_win);
+  d.ybuf = reinterpret_cast<double2*>(base + o_ybuf);
+  P->device_bytes = total;
+  P->alpha = v->alpha; P->beta = v->beta; P->seed = v->seed;
+  P->shifts = shifts; P->primes = primes; P->small = small;
+  cudaGetDevice(&P->device);
+  return SFT_OK;
+}
+
+sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
+                         int64_t* primes_out, int32_t* small_out, int32_t* n_small_out) {
+  if (!primes_out || !small_out || !n_small_out) { set_error("NULL output"); return SFT_EINVAL; }
+  if (N < 2 || N >= (int64_t(1) << 31) || s < 1 || s > N) { set_error("need 2 <= N < 2^31, 1 <= s <= N"); return SFT_EINVAL; }
+  if (K < 1 || K > kMaxK || !(c_p > 0.0) || c_p * (double)s > 1.0e6) { set_error("bad K or c_p"); return SFT_EINVAL; }
+  std::vector<int32_t> pr = choose_primes(s, K, c_p, seed);
+  std::vector<int32_t> sm = choose_small(N, pr);
+  if ((int)sm.size() > kMaxT) { set_error("too many small moduli"); return SFT_EINVAL; }
+  for (int j = 0; j < K; ++j) primes_out[j] = pr[j];
+  for (size_t l = 0; l < sm.size(); ++l) small_out[l] = sm[l];
+  *n_small_out = (int32_t)sm.size();
+  return SFT_OK;
+}
+
+void free_plan(Plan* P) {
+  for (void* a : P->allocations) cudaFree(a);
+  P->allocations.clear();
+}
+
+}  // namespace sft

@@ -1,0 +1,203 @@
+// Kernel (a): filtered samples h_q(x) = (1/N) sum_{i=-kappa}^{kappa} f_{(j'+i) mod N} g_q(x - y_{j'+i})
+// at every node the inner SFT reads, for every shift q at once (eq. UntruncatedFiniteSum cut to
+// the window of Lemma fewer_points_error; modulated filter g_q(x) = e^{iqx} g(x)).
+//
+// One thread per node.  The node's window of f (2 kappa + 1 complex values, contiguous except at
+// the ends of f) is fetched once with 16-byte vector loads and reused by all shifts.  Writing
+// x - y_{j'+i} = 2 pi (v0 - i) / N with the exact integer offset d0 = kN - j'P (v0 = d0 / P), the
+// shift-q sample factors as
+//     h_q(x) = e^{2 pi i q d0 / (P N)} * sum_i [f_{j'+i} G0 e^{-gamma (v0 - i)^2}] * e^{-2 pi i q i / N}
+// (G0 = 1/(N c1), gamma = 2 pi^2 / (N c1)^2).  Only the n = 0 image of the periodic Gaussian is
+// kept: the plan requires gamma (N - kappa - 1/2)^2 >= 40, so every other image is below e^{-40} of
+// the window's central weight.  The table
+// e^{-2 pi i (q i mod N) / N} is reduced exactly on the host; the node phase q d0 is an exact
+// integer with |q d0| <= P N / 4, so no reduction is needed before the sincos.
+#include "cplx.cuh"
+#include "sft_internal.h"
+
+namespace sft {
+
+namespace {
+
+struct NodeGeom {
+  int64_t jp;   // nearest grid index reduced to [0, N)
+  int32_t d0;   // kN - j'P (exact, |d0| <= P/2)
+  int32_t PP;   // node modulus P (p_j or p_j t_l)
+};
+
+__device__ __forceinline__ void decode_node(const DevPlan& d, int64_t node, int& j, int& k1, NodeGeom& g) {
+  j = 0;
+  while (j + 1 < d.K && node >= d.nodeoff[j + 1]) ++j;
+  const int p = d.p[j];
+  const int local = (int)(node - d.nodeoff[j]);
+  const int sub = local / p;
+  k1 = local - sub * p;
+  int64_t k, PP;
+  if (sub == 0) {
+    PP = p;
+    k = k1;
+  } else {
+    const int t = d.t[d.sub_l[sub]];
+    const int k2 = d.sub_k2[sub];
+    PP = (int64_t)p * t;
+    k = ((int64_t)k1 * t + (int64_t)k2 * p) % PP;   // node -pi + 2 pi (k1/p + k2/t)
+  }
+  const int64_t kN = k * d.N;
+  int64_t jp = (2 * kN + PP) / (2 * PP);            // round(kN/P), ties up
+  g.d0 = (int32_t)(kN - jp * PP);
+  if (jp >= d.N) jp -= d.N;
+  g.jp = jp;
+  g.PP = (int32_t)PP;
+}
+
+template <typename IN> struct InLoad;
+template <> struct InLoad<float2> {
+  __device__ static __forceinline__ float2 one(const float2* f, int64_t i) { return __ldg(f + i); }
+};
+template <> struct InLoad<double2> {
+  __device__ static __forceinline__ double2 one(const double2* f, int64_t i) { return __ldg(f + i); }
+};
+
+template <typename R, typename C, typename IN>
+__device__ __forceinline__ C widen(IN v) {
+  return cmake<C>((double)v.x, (double)v.y);
+}
+template <> __device__ __forceinline__ float2 widen<float, float2, float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ double2 widen<double, double2, double2>(double2 v) { return v; }
+
+// Fetch the 2*KAPPA+1 window values f_{(jp+i) mod N}, i = -KAPPA..KAPPA, into win[].
+template <int KAPPA, typename C, typename R, typename IN>
+__device__ __forceinline__ void fetch_window(const DevPlan& d, const IN* f, int64_t jp, C* win) {
+  constexpr int W = 2 * KAPPA + 1;
+  const int64_t N = d.N;
+  if constexpr (sizeof(IN) == 8) {
+    if (d.aligned16 && jp >= KAPPA && jp + KAPPA + 2 <= N) {
+      const int64_t start = jp - KAPPA;
+      const int64_t base = start & ~int64_t(1);
+      const float4* v = reinterpret_cast<const float4*>(f + base);
+      float2 e[W + 1];
+#pragma unroll
+      for (int h = 0; h < (W + 1) / 2; ++h) {
+        float4 x = __ldg(v + h);
+        e[2 * h] = make_float2(x.x, x.y);
+        e[2 * h + 1] = make_float2(x.z, x.w);
+      }
+      if (start == base) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) win[i] = widen<R, C, float2>(e[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) win[i] = widen<R, C, float2>(e[i + 1]);
+      }
+      return;
+    }
+  } else {
+    if (jp >= KAPPA && jp + KAPPA < N) {
+#pragma unroll
+      for (int i = 0; i < W; ++i) win[i] = widen<R, C, IN>(InLoad<IN>::one(f, jp - KAPPA + i));
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    int64_t idx = jp - KAPPA + i;
+    if (idx < 0) idx += N;
+    if (idx >= N) idx -= N;
+    win[i] = widen<R, C, IN>(InLoad<IN>::one(f, idx));
+  }
+}
+
+template <int KAPPA, typename R, typename IN>
+__global__ void __launch_bounds__(256) resample_kernel(DevPlan d, const IN* __restrict__ f) {
+  using C = typename Cx<R>::T;
+  constexpr int W = 2 * KAPPA + 1;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= d.m) return;
+  int j, k1;
+  NodeGeom g;
+  decode_node(d, node, j, k1, g);
+
+  C win[W];
+  fetch_window<KAPPA, C, R, IN>(d, f, g.jp, win);
+
+  // Gaussian weights G0 exp(-gamma (v0 - i)^2), v0 = d0 / P
+  const R v0 = (R)g.d0 / (R)g.PP;
+  const R gam = (R)d.gamma, G0 = (R)d.G0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    const R v = v0 - (R)(i - KAPPA);
+    win[i] = cscale(win[i], G0 * r_exp(-gam * v * v));
+  }
+
+  const C* T = reinterpret_cast<const C*>(d.Ttab);
+  C* out = reinterpret_cast<C*>(d.samples);
+  const R inv_PN = (R)1 / ((R)g.PP * (R)d.N);
+  for (int qi = 0; qi < d.nq; ++qi) {
+    C acc = czero<C>();
+    const C* Tq = T + qi * W;
+#pragma unroll
+    for (int i = 0; i < W; ++i) acc = cadd(acc, cmul(win[i], __ldg(Tq + i)));
+    const int64_t num = d.q[qi] * (int64_t)g.d0;           // exact, |num| <= P N / 4
+    const C ph = expi_turns((R)num * inv_PN);
+    out[(int64_t)qi * d.m + node] = cmul(acc, ph);
+  }
+}
+
+// Any window half-width up to kMaxKappa (theorem-parameter mode): scalar loads, runtime loops.
+template <typename R, typename IN>
+__global__ void __launch_bounds__(128) resample_kernel_generic(DevPlan d, const IN* __restrict__ f) {
+  using C = typename Cx<R>::T;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= d.m) return;
+  int j, k1;
+  NodeGeom g;
+  decode_node(d, node, j, k1, g);
+  const int KAPPA = d.kappa, W = 2 * KAPPA + 1;
+  const R v0 = (R)g.d0 / (R)g.PP;
+  const R gam = (R)d.gamma, G0 = (R)d.G0;
+  const C* T = reinterpret_cast<const C*>(d.Ttab);
+  C* out = reinterpret_cast<C*>(d.samples);
+  const R inv_PN = (R)1 / ((R)g.PP * (R)d.N);
+  C acc[kMaxQ];
+  for (int qi = 0; qi < d.nq; ++qi) acc[qi] = czero<C>();
+  for (int i = 0; i < W; ++i) {
+    int64_t idx = g.jp - KAPPA + i;
+    if (idx < 0) idx += d.N;
+    if (idx >= d.N) idx -= d.N;
+    const R v = v0 - (R)(i - KAPPA);
+    const C fw = cscale(widen<R, C, IN>(InLoad<IN>::one(f, idx)), G0 * r_exp(-gam * v * v));
+    for (int qi = 0; qi < d.nq; ++qi) acc[qi] = cadd(acc[qi], cmul(fw, __ldg(T + qi * W + i)));
+  }
+  for (int qi = 0; qi < d.nq; ++qi) {
+    const int64_t num = d.q[qi] * (int64_t)g.d0;
+    out[(int64_t)qi * d.m + node] = cmul(acc[qi], expi_turns((R)num * inv_PN));
+  }
+}
+
+template <typename R, typename IN>
+cudaError_t launch_typed(const DevPlan& d, const void* f, cudaStream_t st) {
+  const IN* fin = reinterpret_cast<const IN*>(f);
+  if (d.kappa == 6) {
+    const unsigned grid = (unsigned)((d.m + 255) / 256);
+    resample_kernel<6, R, IN><<<grid, 256, 0, st>>>(d, fin);
+  } else if (d.kappa == 4) {
+    const unsigned grid = (unsigned)((d.m + 255) / 256);
+    resample_kernel<4, R, IN><<<grid, 256, 0, st>>>(d, fin);
+  } else {
+    const unsigned grid = (unsigned)((d.m + 127) / 128);
+    resample_kernel_generic<R, IN><<<grid, 128, 0, st>>>(d, fin);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_resample(const DevPlan& d, const void* f, cudaStream_t st) {
+  if (d.prec == SFT_FP32)
+    return d.input == SFT_IN_C64 ? launch_typed<float, float2>(d, f, st)
+                                 : launch_typed<float, double2>(d, f, st);
+  return d.input == SFT_IN_C64 ? launch_typed<double, float2>(d, f, st)
+                               : launch_typed<double, double2>(d, f, st);
+}
+
+}  // namespace sft

@@ -1,0 +1,117 @@
+// Internal declarations shared by the plan, the kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sft.h"
+
+namespace sft {
+
+constexpr int kMaxK = SFT_MAX_K;          // prime moduli
+constexpr int kMaxT = SFT_MAX_SMALL;      // small moduli
+constexpr int kMaxQ = SFT_MAX_SHIFTS;     // shifts
+constexpr int kMaxKappa = 48;             // window half-width
+constexpr int kMaxSub = 128;              // node subsets per prime: 1 + sum_l (t_l - 1)
+constexpr int kMaxFFT32 = 16384;          // chirp convolution length, FP32 (128 KiB of smem)
+constexpr int kMaxFFT64 = 8192;           // FP64 (128 KiB of smem)
+constexpr int64_t kNoFreq = INT64_MIN;    // "no frequency" marker in candidate arrays
+
+// Record of one voted frequency of one shift (written by the vote/median kernel).
+struct Voted {
+  int64_t w;       // frequency in B
+  double zre, zim; // median estimate (FP64 storage; FP32 path values are FP32-exact)
+  int32_t votes;
+  int32_t jmin;
+};
+
+// Record of one in-band, filter-divided coefficient (per-shift top-s, Algorithm 1's R-hat).
+struct Pooled {
+  int64_t w;
+  double cre, cim;
+  int32_t qi;      // shift index
+  int32_t pad;
+};
+
+// Everything a kernel needs about a plan; passed by value.
+struct DevPlan {
+  int64_t N;
+  int32_t s, kappa, K, nT, nq, nsub;
+  int32_t prec, input;
+  int64_t m;                  // distinct nodes: nsub * sum_j p_j
+  int32_t Ptot;               // sum_j p_j
+  int32_t fftM, fftLog2;      // chirp convolution length (power of two)
+  int32_t p[kMaxK];
+  int64_t nodeoff[kMaxK + 1]; // first node of prime j
+  int32_t poff[kMaxK + 1];    // first bin of prime j
+  int64_t Mj[kMaxK];          // p_j * prod(t)
+  int32_t t[kMaxT];
+  int32_t subbase[kMaxT];     // node subset index of (l, k2 = 1)
+  int32_t twoff[kMaxT];       // offset of l's twiddles in twsmall
+  int8_t sub_l[kMaxSub];      // small-modulus index of subset u (-1 for u = 0)
+  int8_t sub_k2[kMaxSub];     // offset numerator k2 of subset u
+  int64_t q[kMaxQ];
+  int64_t L;
+  double c1;
+  double gamma;               // 2 pi^2 / (N c1)^2: Gaussian exponent per squared grid offset
+  double G0;                  // 1 / (N c1): weight prefactor
+  int32_t vcap;               // capacity of each shift's voted list
+  int32_t aligned16;          // f is 16-byte aligned (set per execution)
+  // device tables
+  const void* Ttab;           // [nq][2 kappa + 1] exp(-2 pi i (q i mod N) / N)   (prec type)
+  const void* chirp;          // [K][pmax] exp(-pi i (n^2 mod 2p) / p)           (prec type)
+  const void* vhat;           // [K][fftM] FFT of the conjugate chirp / (M p)    (prec type)
+  const void* fftw;           // [fftM] exp(-2 pi i n / M)                        (prec type)
+  const void* twsmall;        // [sum_l t_l] exp(-2 pi i n / t_l)                (prec type)
+  const float2* wp32;         // [K][pmax] exp(-2 pi i n / p_j) for the FP32 re-estimation
+  const int32_t* garner;      // [K][nT] (p_j t_1 .. t_{l-1})^{-1} mod t_l
+  const int32_t* pinv;        // [K][nT] p_j^{-1} mod t_l
+  int32_t pmax;
+  // scratch
+  void* samples;              // [nq][m] prec complex
+  void* bins;                 // [nq][m] prec complex
+  int64_t* cand;              // [nq][Ptot]
+  uint8_t* resid;             // [nq][Ptot][nT]
+  int32_t* counters;          // [0..nq): voted counts, [nq]: pool count, [nq+1]: status word
+  Voted* voted;               // [nq][vcap]
+  Pooled* pool;               // [nq * s]
+  Pooled* winners;            // [s]
+  double2* ybuf;              // [s][K] re-estimated bins
+};
+
+struct Plan {
+  DevPlan d;
+  double alpha = 0, beta = 0;
+  uint64_t seed = 0;
+  std::vector<int64_t> shifts;
+  std::vector<int32_t> primes, small;
+  size_t device_bytes = 0;
+  std::vector<void*> allocations;
+  int device = 0;
+};
+
+// Kernel launch wrappers (each returns cudaGetLastError()).
+cudaError_t launch_resample(const DevPlan& d, const void* f, cudaStream_t st);
+cudaError_t launch_bluestein(const DevPlan& d, cudaStream_t st);
+cudaError_t launch_identify(const DevPlan& d, cudaStream_t st);
+cudaError_t launch_vote(const DevPlan& d, cudaStream_t st);
+cudaError_t launch_select(const DevPlan& d, int64_t* out_w, double2* out_c, int32_t* out_n,
+                          cudaStream_t st);
+cudaError_t launch_refine(const DevPlan& d, int64_t* out_w, double2* out_c, int32_t* out_n,
+                          cudaStream_t st);
+
+// Host plan construction (plan.cpp).
+sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
+                      const int64_t* primes, int32_t n_primes, const int32_t* small,
+                      int32_t n_small);
+void free_plan(Plan* P);
+sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
+                         int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);
+
+// Thread-local error text.
+void set_error(const std::string& msg);
+
+}  // namespace sft

@@ -1,0 +1,82 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every symbol include/sft.h declares,
+and its host-only logic (argument validation, seeded moduli choice) agrees with the oracle.
+No device work runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1706_02740_gb300 as sft
+from paper_1706_02740_gb300 import build as sft_build
+from oracle import dsft as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    sft_build.build()
+    return sft.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sft.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(sft_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "sft_plan" in names and "sft_execute" in names and len(names) >= 9
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in sft.EXPORTS, f"binding misses {name}"
+
+
+def test_struct_sizes_match_header_layout():
+    # sft_variant: 4 x int32, 3 x double, uint64
+    assert ctypes.sizeof(sft.sft_variant) == 48
+    assert ctypes.sizeof(sft.sft_plan_desc) == 8 + 6 * 4 + 15 * 8 + 12 * 4 + 32 * 8 + 8 + 8 + 8 + 16
+
+
+def test_variant_defaults(lib):
+    v = sft.sft_variant_init()
+    assert (v.kappa, v.precision, v.input, v.K) == (6, 0, 0, 5)
+    assert (v.c_p, v.alpha, v.beta, v.seed) == (3.0, 1.5, 1.5, 0)
+
+
+@pytest.mark.parametrize("N,s,K,c_p,seed", [(2 ** 16, 8, 5, 4.0, 0), (2 ** 22, 64, 5, 3.0, 7),
+                                            (2 ** 26, 1000, 5, 3.0, 123), (4194301, 64, 7, 8.0, 2),
+                                            (1000003, 3, 3, 10.0, 2 ** 63 + 5), (97, 2, 5, 3.0, 1)])
+def test_moduli_choice_matches_oracle(lib, N, s, K, c_p, seed):
+    primes, small = sft.sft_choose_moduli(N, s, K, c_p, seed)
+    assert primes == O.choose_primes(s, K, c_p, seed)
+    assert small == O.choose_small_moduli(N, primes)
+
+
+@pytest.mark.parametrize("kw", [dict(N=1, s=1), dict(N=100, s=0), dict(N=100, s=101),
+                                dict(N=2 ** 31, s=2), dict(N=12, s=2)])
+def test_plan_rejects_bad_sizes_without_touching_the_device(lib, kw):
+    with pytest.raises(sft.SftError) as e:
+        sft.sft_plan(kw["N"], kw["s"])
+    assert e.value.status == sft.SFT_EINVAL
+
+
+def test_plan_rejects_bad_moduli(lib):
+    for primes, small in [([101, 101, 103], None), ([100, 103, 107], None),
+                          ([101, 103, 107], [2, 4]), ([101, 103, 107], [2, 3]),
+                          ([101, 103, 107], [101, 2, 3, 5, 7])]:
+        with pytest.raises(sft.SftError) as e:
+            sft.sft_plan(2 ** 16, 8, primes=primes, small_moduli=small)
+        assert e.value.status == sft.SFT_EINVAL
+    with pytest.raises(sft.SftError):
+        sft.sft_plan(2 ** 16, 8, sft.sft_variant_init(kappa=0))
+    with pytest.raises(sft.SftError):
+        sft.sft_plan(2 ** 16, 4000, sft.sft_variant_init(precision=1))   # p_j > 4096 in FP64
+    assert "4096" in sft.sft_last_error()
+
+
+def test_execute_rejects_null_and_partial_outputs(lib):
+    with pytest.raises(sft.SftError):
+        sft.sft_execute(sft.Plan(None), 0, 0, 0, 0, 0)

@@ -1,0 +1,158 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, stage by stage.
+
+Tolerances (north-star): coefficients within 1e-5 relative on the FP32 path and 1e-11 on the FP64
+path; integer stages bit-exact (CRT and vote are re-run by the oracle on the GPU's own residues and
+candidates); FP decisions (argmax residues) compared where the oracle's decision has margin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1706_02740_gb300 as sft
+from oracle import dsft as O
+from synth.signals import as_complex64, make_signal, upcast
+from tests import gpu_parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1706_02740_gb300 import build
+    build.build()
+    sft.load()
+
+
+CASES = [
+    # N, s, seed, kappa, K, c_p, snr, magnitude
+    (2 ** 14, 6, 11, 6, 5, 8.0, None, "unit"),
+    (3 ** 9, 8, 12, 4, 5, 8.0, None, "unit"),
+    (65521, 10, 13, 6, 5, 6.0, 30.0, "loguniform"),
+    (2 ** 16, 8, 1000, 6, 5, 4.0, None, "unit"),           # configuration 1, trial 0
+    (100003, 12, 14, 6, 7, 5.0, 40.0, "unit"),
+]
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+@pytest.mark.parametrize("case", CASES)
+def test_stages_and_output_match_oracle(case, prec):
+    N, s, seed, kappa, K, c_p, snr, mag = case
+    sig = make_signal(N, s, seed, mag, snr)
+    f32 = as_complex64(sig.f)
+    f = upcast(f32)
+    g = U.run_gpu(sft, N, s, f32 if prec == U.FP32 else f, prec, kappa, K, c_p, seed, keep=True)
+    info, plan = g["info"], g["plan"]
+    oplan = U.oracle_plan(info, N, s)
+    assert oplan.shifts == info["shifts"] and oplan.L == info["L"]
+    samples, bins, cand, resid = U.debug_arrays(sft, plan, info)
+    plan.destroy()
+
+    # (a) resampling at every node, every shift
+    ref = U.oracle_samples(f, oplan, info)
+    scale = np.max(np.abs(ref))
+    tol_s = 2e-6 if prec == U.FP32 else 1e-13
+    assert np.max(np.abs(samples - ref)) <= tol_s * scale
+
+    res = O.dsft(f, oplan)
+    primes, small = info["primes"], info["small"]
+    offs = np.cumsum([0] + primes)
+    for qi, sr in enumerate(res.shifts):
+        bmax = max(np.max(np.abs(y)) for y in sr.Y)
+        for j, p in enumerate(primes):
+            Z = U.subbins(info, bins[qi], j)
+            # (b) the p_j-node measurements Y_j
+            tol_b = 2e-6 if prec == U.FP32 else 1e-13
+            assert np.max(np.abs(Z[0] - sr.Y[j])) <= tol_b * bmax
+            # (b') the folded sub-bins equal the oracle's length-(p t) measurement bins
+            for l, t in enumerate(small):
+                Xr = U.folded_subbins(info, Z, l)
+                X = O.measure(f, oplan, sr.q, p * t)
+                b = np.arange(p)
+                for r in range(t):
+                    u = ((r - b) * pow(p, -1, t)) % t
+                    assert np.max(np.abs(Xr[r] - X[b + p * u])) <= tol_b * bmax
+            # (c) residues agree wherever the oracle's decision has margin and the bin has energy
+            energy = np.abs(sr.Y[j]) >= 1e-3 * bmax
+            for l in range(len(small)):
+                ok = (sr.margins[j][l] > 1e-3) & energy
+                assert np.array_equal(resid[qi, offs[j]:offs[j + 1], l][ok], sr.residues[j][l][ok])
+            # (c') CRT bit-exact on the GPU's own residues, every bin
+            for b in range(p):
+                w = U.crt_band(b, resid[qi, offs[j] + b, :len(small)], p, small, N)
+                expect = np.iinfo(np.int64).min if w is None else w
+                assert cand[qi, offs[j] + b] == expect
+        # (c'') the vote re-run on the GPU's candidates reproduces the oracle's significant votes
+        gv = U.oracle_vote(cand[qi], primes, len(primes))
+        sig_or = {int(w) for w, z in zip(sr.voted, sr.z) if abs(z) > 1e-3 * bmax}
+        assert sig_or <= set(gv)
+
+    # final output: same support and ordering, coefficients within tolerance
+    n = g["count"]
+    assert n == len(res.freqs)
+    tol = 1e-5 if prec == U.FP32 else 1e-11
+    U.assert_same_output(g["freqs"][:n], g["coefs"][:n], res.freqs, res.coefs, tol)
+    assert np.all(g["freqs"][n:] == 0) and np.all(g["coefs"][n:] == 0)
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_config1_recovers_truth(prec):
+    """Configuration 1 (N = 2^16, s = 8, unit magnitudes, no noise): the exact support, against
+    the brute-force DFT's best s-term approximation (here: the generating spectrum)."""
+    for trial in range(5):
+        sig = make_signal(2 ** 16, 8, 1000 + trial, "unit", None)
+        f = sig.f if prec == U.FP64 else as_complex64(sig.f)
+        g = U.run_gpu(sft, 2 ** 16, 8, f, prec, 6, 5, 8.0, trial)
+        assert g["count"] == 8
+        assert sorted(g["freqs"].tolist()) == sorted(sig.omega.tolist())
+
+
+def test_input_types_and_precisions_agree():
+    N, s = 2 ** 15, 7
+    sig = make_signal(N, s, 5, "unit", None)
+    f32 = as_complex64(sig.f)
+    outs = []
+    for prec, f in [(U.FP32, f32), (U.FP32, upcast(f32)), (U.FP64, f32), (U.FP64, upcast(f32))]:
+        outs.append(U.run_gpu(sft, N, s, f, prec, 6, 5, 8.0, 1))
+    for o in outs[1:]:
+        assert sorted(o["freqs"].tolist()) == sorted(outs[0]["freqs"].tolist())
+    assert np.array_equal(outs[2]["coefs"], outs[3]["coefs"])   # FP64 path: same widened input
+    U.assert_same_output(outs[0]["freqs"], outs[0]["coefs"], outs[2]["freqs"], outs[2]["coefs"], 1e-5)
+    assert np.array_equal(outs[0]["coefs"], outs[1]["coefs"])   # FP32 path narrows c128 exactly
+
+
+@pytest.mark.parametrize("N,s,kappa,K,c_p", [(13, 1, 6, 3, 3.0), (9, 2, 4, 5, 3.0),
+                                             (31, 31, 4, 3, 2.0), (1009, 1, 6, 1, 3.0),
+                                             (3001, 1, 6, 3, 3100.0)])
+def test_edge_cases_match_oracle(N, s, kappa, K, c_p):
+    """Tiny N (window equal to N), s = N, a single modulus, and p_1 >= N (no small moduli)."""
+    sig = make_signal(N, s, 7, "unit", None)
+    f = sig.f
+    g = U.run_gpu(sft, N, s, f, U.FP64, kappa, K, c_p, 3)
+    oplan = U.oracle_plan(g["info"], N, s)
+    res = O.dsft(f, oplan)
+    n = g["count"]
+    assert n == len(res.freqs)
+    if n:
+        U.assert_same_output(g["freqs"][:n], g["coefs"][:n], res.freqs, res.coefs, 1e-11)
+
+
+def test_repeated_execution_is_deterministic():
+    N, s = 2 ** 17, 16
+    sig = make_signal(N, s, 9, "unit", 30.0)
+    f32 = as_complex64(sig.f)
+    import torch
+    plan = sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=6.0))
+    ft = torch.from_numpy(f32).cuda()
+    first = None
+    for _ in range(3):
+        w, c, n = sft.execute_torch(plan, ft)
+        torch.cuda.synchronize()
+        cur = (w.cpu().numpy().copy(), c.cpu().numpy().copy(), int(n.item()))
+        if first is None:
+            first = cur
+        else:
+            assert np.array_equal(cur[0], first[0]) and np.array_equal(cur[1], first[1])
+    plan.destroy()
