@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 discrete sparse Fourier transform (Algorithm 1) on the precision-study
+workload: N = 2^26, s = 1000, complex64 input, log-uniform magnitudes on [1e-2, 1], random phases,
+complex Gaussian noise at 30 dB SNR.
+
+A step is one pass of the whole hot path (resampling, chirp-convolution DFTs, residues + CRT,
+vote + medians, selections, re-estimation) over one batch of `batch` signals, each a separate
+sft_execute through the C ABI.  Eight distinct 512 MiB inputs rotate so that the windows one SFT
+gathers are not left in the 129 MB L2 by the previous one.
+
+  python bench.py [--gpus N --steps K --warmup W]          # this library
+  python bench.py --impl reference [--steps K --warmup W]  # the CPU oracle on host cores
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs independent replicas on its own GPU
+(no collective on the data path); value = SFTs of all ranks / max elapsed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT, S_DEFAULT = 2 ** 26, 1000
+PLAN = dict(kappa=6, K=5, c_p=3.0, alpha=1.5, beta=1.5, seed=1)
+METRIC = "SFTs/sec at N=2^26, s=1000 (p50/p99 latency, vs plain FP64 path and cuFFT; % HBM roofline)"
+N_INPUTS = 8
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--s", type=int, default=S_DEFAULT)
+    ap.add_argument("--batch", type=int, default=0, help="SFTs per step (0 = about 50 ms of work)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, batch):
+    return {
+        "workload": f"precision study: N={args.N}, s={args.s}, complex64, |c| log-uniform "
+                    "[1e-2,1], random phase, SNR 30 dB",
+        "N": args.N, "s": args.s, "kappa": PLAN["kappa"], "K": PLAN["K"], "c_p": PLAN["c_p"],
+        "alpha": PLAN["alpha"], "beta": PLAN["beta"], "precision": "fp32 bulk + fp64 refine",
+        "batch_per_step": batch,
+        "l2": f"{N_INPUTS} rotating distinct inputs of {args.N * 8 >> 20} MiB (> 129 MB L2)",
+    }
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "50"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# roofline helpers
+# ------------------------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_digest(*names):
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_1706_02740_gb300", "csrc", nm), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag, digest):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel, if it was taken on the
+    current source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_src = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m_src and m_tr) or m_src.group(1) != digest:
+        return None
+    return float(m_tr.group(1))
+
+
+def dft_flops(info):
+    """Conventional flop count of the chirp-convolution stage per SFT: two length-M FFTs
+    (5 M log2 M each) plus the pointwise products, for every node subset of every prime and shift."""
+    M = info["fft_size"]
+    per = 2 * 5 * M * math.log2(M) + 6 * M
+    return info["n_shifts"] * info["n_sub"] * sum(per + 12 * p for p in info["primes"])
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1706_02740_gb300 as sft
+    from synth.device_signals import make_device_signal
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    N, s = args.N, args.s
+    inputs = []
+    for i in range(N_INPUTS):
+        f, _, _ = make_device_signal(N, s, 3000 + 100 * rank + i, "loguniform", 30.0, dev)
+        inputs.append(f)
+    torch.cuda.synchronize()
+
+    v = sft.sft_variant_init(precision=sft.SFT_FP32, kappa=PLAN["kappa"], K=PLAN["K"],
+                             c_p=PLAN["c_p"], alpha=PLAN["alpha"], beta=PLAN["beta"],
+                             seed=PLAN["seed"])
+    plan = sft.sft_plan(N, s, v)
+    info = plan.info()
+    stream = torch.cuda.current_stream(dev)
+    outs = [(torch.empty(s, dtype=torch.int64, device=dev),
+             torch.empty(s, dtype=torch.complex128, device=dev),
+             torch.empty(1, dtype=torch.int32, device=dev)) for _ in range(2)]
+
+    def one(i):
+        o = outs[i & 1]
+        sft.sft_execute(plan, inputs[i % N_INPUTS].data_ptr(), o[0].data_ptr(), o[1].data_ptr(),
+                        o[2].data_ptr(), stream.cuda_stream)
+
+    # pick the batch so that a step is about 50 ms
+    for i in range(4):
+        one(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(16):
+        one(i)
+    e1.record()
+    torch.cuda.synchronize()
+    est_ms = e0.elapsed_time(e1) / 16
+    batch = args.batch or max(1, int(round(50.0 / max(est_ms, 1e-3))))
+
+    for w in range(args.warmup):
+        for i in range(batch):
+            one(i)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K * batch)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K * batch)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sft.sft_plan_profile(plan, True)
+    launches0 = sft.sft_plan_launches(plan)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        t0.record()
+        for k in range(K):
+            for i in range(batch):
+                idx = k * batch + i
+                starts[idx].record()
+                one(idx)
+                ends[idx].record()
+        t1.record()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    launches = sft.sft_plan_launches(plan) - launches0
+    elapsed_ms = t0.elapsed_time(t1)
+    lat = sorted(a.elapsed_time(b) for a, b in zip(starts, ends))
+    stage_ms, n_rec = sft.sft_plan_profile_read(plan)
+    sft.sft_plan_profile(plan, False)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_sfts = K * batch * world
+    value = total_sfts / (elapsed_ms / 1e3)
+
+    # roofline of the gather (resampling) and of the dominant stage
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    per_launch_us = {k: 1e3 * v / max(n_rec, 1) for k, v in stage_ms.items()}
+    gather_bytes = 8 * (2 * info["kappa"] + 1) * info["nodes"]
+    rs_s = per_launch_us["resample"] * 1e-6
+    digest = source_digest("resample.cu", "cplx.cuh", "sft_internal.h")
+    traffic = profiled_traffic("resample_n2p26_s1000", digest)
+    roof_gather = {"kernel": "resample", "bound": "hbm", "achieved": gather_bytes / rs_s / 1e9,
+                   "peak": hbm, "unit": "GB/s", "frac": gather_bytes / rs_s / 1e9 / hbm,
+                   "traffic": traffic, "algorithmic_bytes": gather_bytes,
+                   "peak_source": f"{peak_kind} hbm_gbs"}
+    dominant = max(per_launch_us, key=per_launch_us.get)
+    if dominant == "chirp_dft":
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        fl = dft_flops(info)
+        ach = fl / (per_launch_us["chirp_dft"] * 1e-6) / 1e12
+        roof = {"kernel": "bluestein (chirp-convolution DFT)", "bound": "alu", "achieved": ach,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "algorithmic_flops": fl,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+    else:
+        roof = dict(roof_gather)
+
+    # end to end: host (pinned) input copied in, result read back, every step
+    e2e = None
+    if rank == 0 or world > 1:
+        hosts = [inputs[i].cpu().pin_memory() for i in range(2)]
+        dbuf = torch.empty_like(inputs[0])
+        hw = torch.empty(s, dtype=torch.int64).pin_memory()
+        hc = torch.empty(s, dtype=torch.complex128).pin_memory()
+        hn = torch.empty(1, dtype=torch.int32).pin_memory()
+        n_e2e = max(4, min(K, 16))
+        for rep in range(2):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for i in range(n_e2e):
+                dbuf.copy_(hosts[i & 1], non_blocking=True)
+                o = outs[0]
+                sft.sft_execute(plan, dbuf.data_ptr(), o[0].data_ptr(), o[1].data_ptr(),
+                                o[2].data_ptr(), stream.cuda_stream)
+                hw.copy_(o[0], non_blocking=True)
+                hc.copy_(o[1], non_blocking=True)
+                hn.copy_(o[2], non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / n_e2e
+        e2e = {"value": world * 1e3 / e2e_ms, "unit": "SFTs/s",
+               "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": s * (8 + 16) + 4,
+               "note": "per SFT: pinned host f (N complex64) -> device, sft_execute, results -> host"}
+        del hosts, dbuf
+
+    # the plain one-request-at-a-time FP64 path and a full cuFFT transform, same GPU, same inputs
+    plain = None
+    if rank == 0:
+        v64 = sft.sft_variant_init(precision=sft.SFT_FP64, kappa=PLAN["kappa"], K=PLAN["K"],
+                                   c_p=PLAN["c_p"], alpha=PLAN["alpha"], beta=PLAN["beta"],
+                                   seed=PLAN["seed"])
+        p64 = sft.sft_plan(N, s, v64)
+        o64 = outs[1]
+        for i in range(2):
+            sft.sft_execute(p64, inputs[i].data_ptr(), o64[0].data_ptr(), o64[1].data_ptr(),
+                            o64[2].data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for i in range(8):
+            sft.sft_execute(p64, inputs[i % N_INPUTS].data_ptr(), o64[0].data_ptr(),
+                            o64[1].data_ptr(), o64[2].data_ptr(), stream.cuda_stream)
+        b.record()
+        torch.cuda.synchronize()
+        plain_ms = a.elapsed_time(b) / 8
+        p64.destroy()
+        sign = torch.ones(N, dtype=torch.float32, device=dev)
+        sign[1::2] = -1.0
+
+        def cufft_step(f):
+            X = torch.fft.fft(f)
+            X = X * (sign / N)          # F f = (-1)^w X / N on the index grid
+            mag = X.real * X.real + X.imag * X.imag
+            top = torch.topk(mag, s)
+            return top.indices, X[top.indices]
+        for i in range(2):
+            cufft_step(inputs[i])
+        torch.cuda.synchronize()
+        a.record()
+        for i in range(8):
+            cufft_step(inputs[i % N_INPUTS])
+        b.record()
+        torch.cuda.synchronize()
+        cufft_ms = a.elapsed_time(b) / 8
+        plain = {"plain_fp64": {"value": 1e3 / plain_ms, "unit": "SFTs/s", "ms": plain_ms},
+                 "cufft": {"value": 1e3 / cufft_ms, "unit": "SFTs/s", "ms": cufft_ms,
+                           "what": "torch.fft.fft (cuFFT C2C FP32) + (-1)^w/N rescale + top-s"}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(N, s, sfts=2)
+
+    plan.destroy()
+    if rank != 0:
+        return
+    lat_ms = lat
+    out = {
+        "metric": METRIC, "value": value, "unit": "SFTs/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args, batch),
+        "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                          int(0.99 * len(lat_ms)))],
+                       "mean": sum(lat_ms) / len(lat_ms), "what": "device time of one SFT"},
+        "stages_us_per_sft": per_launch_us,
+        "roofline": roof, "roofline_gather": roof_gather,
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }
+    if plain:
+        out.update(plain)
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# the CPU oracle (CPU-baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------
+def _oracle_input(N, s):
+    from synth.signals import as_complex64, make_signal, upcast
+    sig = make_signal(N, s, 3000, "loguniform", 30.0)
+    return upcast(as_complex64(sig.f))
+
+
+def cpu_baseline_sample(N, s, sfts=2, f=None, plan=None):
+    """Times the oracle, as it stands, on sfts * ceil(c2) of Algorithm 1's shift iterations (each
+    is 1/ceil(c2) of one SFT; the final top-s is negligible) and scales to SFTs/s."""
+    from oracle.dsft import make_plan, ussft_shift
+    if f is None:
+        f = _oracle_input(N, s)
+    if plan is None:
+        plan = make_plan(N, s, kappa=PLAN["kappa"], K=PLAN["K"], c_p=PLAN["c_p"],
+                         alpha=PLAN["alpha"], beta=PLAN["beta"], seed=PLAN["seed"])
+    nq = len(plan.shifts)
+    shifts = sfts * nq
+    t = time.perf_counter()
+    for k in range(shifts):
+        ussft_shift(f, plan, plan.shifts[k % nq])
+    dt = time.perf_counter() - t
+    return {"value": (shifts / nq) / dt, "unit": "SFTs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{shifts} of the {nq} shift iterations of one N={N}, s={s} SFT "
+                      f"({dt:.1f} s; numpy FP64, single thread)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle.dsft import make_plan, ussft_shift
+    N, s = args.N, args.s
+    f = _oracle_input(N, s)
+    plan = make_plan(N, s, kappa=PLAN["kappa"], K=PLAN["K"], c_p=PLAN["c_p"],
+                     alpha=PLAN["alpha"], beta=PLAN["beta"], seed=PLAN["seed"])
+    nq = len(plan.shifts)
+    for w in range(args.warmup):
+        ussft_shift(f, plan, plan.shifts[w % nq])
+    times = []
+    t_all = time.perf_counter()
+    for k in range(args.steps):
+        t = time.perf_counter()
+        ussft_shift(f, plan, plan.shifts[k % nq])
+        times.append(time.perf_counter() - t)
+    elapsed = time.perf_counter() - t_all
+    value = (args.steps / nq) / elapsed
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SFTs/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(args, 1),
+           "cpu_baseline": {"value": value, "unit": "SFTs/s", "cores": 1, "kind": "oracle",
+                            "sample": f"one of the {nq} shift iterations of Algorithm 1 per step "
+                                      f"(1/{nq} SFT), numpy FP64 single thread"},
+           "e2e": {"value": value, "unit": "SFTs/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

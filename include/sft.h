@@ -167,6 +167,21 @@ sft_status sft_plan_info(sft_plan_t plan, sft_plan_desc* out);
  */
 sft_status sft_plan_debug_buffer(sft_plan_t plan, int32_t which, void** dev_ptr, size_t* bytes);
 
+/*
+ * Per-stage timing of this plan's executions with CUDA events recorded on the execution stream
+ * between the stages (enable = 1 creates the events, 0 releases them).  Stages: 0 resampling,
+ * 1 chirp-convolution DFTs, 2 residues + CRT, 3 vote + medians, 4 selections, 5 re-estimation.
+ * At most 4096 executions are recorded between two reads; later ones are not timed.
+ */
+sft_status sft_plan_profile(sft_plan_t plan, int32_t enable);
+
+/* After the stream has been synchronised: the summed milliseconds of each stage (stage_ms[0..6))
+ * over the executions recorded since the previous read, and their number; then resets. */
+sft_status sft_plan_profile_read(sft_plan_t plan, double* stage_ms, int32_t* n_executions);
+
+/* Total number of kernels this plan has launched (all executions so far). */
+int64_t sft_plan_launches(sft_plan_t plan);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char* sft_last_error(void);
 

@@ -64,6 +64,10 @@ EXPORTS = {
                                              ctypes.POINTER(ctypes.c_void_p),
                                              ctypes.POINTER(ctypes.c_size_t)]),
     "sft_last_error": (ctypes.c_char_p, []),
+    "sft_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "sft_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_int32)]),
+    "sft_plan_launches": (ctypes.c_int64, [ctypes.c_void_p]),
     "sft_choose_moduli": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_int64),
@@ -181,6 +185,25 @@ def sft_plan_info(plan: Plan) -> dict:
         "L": d.L, "c1": d.c1, "nodes": d.nodes, "fft_size": d.fft_size,
         "precision": d.precision, "input": d.input,
     }
+
+
+STAGES = ("resample", "chirp_dft", "identify", "vote", "select", "refine")
+
+
+def sft_plan_profile(plan: Plan, enable: bool = True):
+    _check(load().sft_plan_profile(plan.handle, 1 if enable else 0))
+
+
+def sft_plan_profile_read(plan: Plan):
+    """Summed per-stage milliseconds since the last read and the number of executions."""
+    arr = (ctypes.c_double * len(STAGES))()
+    n = ctypes.c_int32()
+    _check(load().sft_plan_profile_read(plan.handle, arr, ctypes.byref(n)))
+    return dict(zip(STAGES, list(arr))), n.value
+
+
+def sft_plan_launches(plan: Plan) -> int:
+    return int(load().sft_plan_launches(plan.handle))
 
 
 def sft_plan_debug_buffer(plan: Plan, which: int):

@@ -55,8 +55,18 @@ sft_status sft_plan(sft_plan_t* out, int64_t N, int32_t s, const sft_variant* v,
   return SFT_OK;
 }
 
+namespace {
+void release_events(Plan& P) {
+  for (cudaEvent_t e : P.events) cudaEventDestroy(e);
+  P.events.clear();
+  P.profiling = false;
+  P.recorded = 0;
+}
+}  // namespace
+
 sft_status sft_plan_destroy(sft_plan_t plan) {
   if (!plan) return SFT_OK;
+  release_events(plan->P);
   sft::free_plan(&plan->P);
   delete plan;
   return SFT_OK;
@@ -108,21 +118,77 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
   d.aligned16 = (fa % 16) == 0;
   cudaStream_t st = (cudaStream_t)stream;
   double2* oc = reinterpret_cast<double2*>(out_coefs_dev);
-  cudaError_t e = cudaMemsetAsync(d.counters, 0, (size_t)(d.nq + 4) * 4, st);
-  if (e == cudaSuccess) e = sft::launch_resample(d, f_dev, st);
-  if (e == cudaSuccess) e = sft::launch_bluestein(d, st);
-  if (e == cudaSuccess) e = sft::launch_identify(d, st);
-  if (e == cudaSuccess) e = sft::launch_vote(d, st);
+  Plan& P = plan->P;
+  cudaEvent_t* ev = nullptr;
+  if (P.profiling && P.recorded < sft::kProfileCap)
+    ev = &P.events[(size_t)P.recorded++ * (sft::kStages + 1)];
+  auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], st); };
   const bool fp64 = d.prec == SFT_FP64;
-  if (e == cudaSuccess)
-    e = sft::launch_select(d, fp64 ? out_freqs_dev : nullptr, fp64 ? oc : nullptr, out_count_dev, st);
-  if (e == cudaSuccess && !fp64) e = sft::launch_refine(d, out_freqs_dev, oc, out_count_dev, st);
+  cudaError_t e = cudaMemsetAsync(d.counters, 0, (size_t)(d.nq + 4) * 4, st);
+  mark(0);
+  if (e == cudaSuccess) e = sft::launch_resample(d, f_dev, st);
+  mark(1);
+  if (e == cudaSuccess) e = sft::launch_bluestein(d, st);
+  mark(2);
+  if (e == cudaSuccess) e = sft::launch_identify(d, st);
+  mark(3);
+  if (e == cudaSuccess) e = sft::launch_vote(d, st);
+  mark(4);
+  if (e == cudaSuccess) e = sft::launch_select(d, out_count_dev, st);
+  mark(5);
+  if (e == cudaSuccess && !fp64) e = sft::launch_refine(d, st);
+  if (e == cudaSuccess) e = sft::launch_finalize(d, out_freqs_dev, oc, st);
+  mark(6);
+  P.launches += 4 + sft::select_launches(d) + (fp64 ? 0 : sft::refine_launches(d)) +
+                (out_freqs_dev ? sft::finalize_launches(d) : 0);
   if (e != cudaSuccess) {
     sft::set_error(std::string("CUDA launch failed: ") + cudaGetErrorString(e));
     return SFT_ECUDA;
   }
   return SFT_OK;
 }
+
+sft_status sft_plan_profile(sft_plan_t plan, int32_t enable) {
+  if (!plan) { sft::set_error("plan is NULL"); return SFT_EINVAL; }
+  Plan& P = plan->P;
+  release_events(P);
+  if (!enable) return SFT_OK;
+  const size_t n = (size_t)sft::kProfileCap * (sft::kStages + 1);
+  P.events.resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (cudaEventCreate(&P.events[i]) != cudaSuccess) {
+      P.events.resize(i);
+      release_events(P);
+      sft::set_error("cudaEventCreate failed");
+      return SFT_ECUDA;
+    }
+  }
+  P.profiling = true;
+  return SFT_OK;
+}
+
+sft_status sft_plan_profile_read(sft_plan_t plan, double* stage_ms, int32_t* n_executions) {
+  if (!plan || !stage_ms || !n_executions) { sft::set_error("NULL argument"); return SFT_EINVAL; }
+  Plan& P = plan->P;
+  for (int k = 0; k < sft::kStages; ++k) stage_ms[k] = 0.0;
+  *n_executions = P.recorded;
+  for (int r = 0; r < P.recorded; ++r) {
+    cudaEvent_t* ev = &P.events[(size_t)r * (sft::kStages + 1)];
+    for (int k = 0; k < sft::kStages; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        sft::set_error("profile events not complete (synchronise the stream first)");
+        return SFT_ECUDA;
+      }
+      stage_ms[k] += ms;
+    }
+  }
+  P.recorded = 0;
+  return SFT_OK;
+}
+
+int64_t sft_plan_launches(sft_plan_t plan) { return plan ? plan->P.launches : 0; }
 
 sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                              int64_t* primes_out, int32_t* small_out, int32_t* n_small_out) {

@@ -8,13 +8,18 @@
 // V = FFT(conj(w) wrapped) / (M p) precomputed per prime in FP64 on the host (the inverse FFT is the
 // forward one between two conjugations).  One transform lives in shared memory; the FFT is an
 // in-place Stockham schedule whose passes hold 16 complex values per thread in registers (radix 16
-// passes, then one radix 2/4/8 pass), with twiddles read from an exactly rounded table.
+// passes, then one radix 2/4/8 pass), with twiddles read from an exactly rounded table.  The
+// shared-memory layout inserts one pad element after every 16 (index n -> n + n/16), so the
+// strided stores of the first two passes hit distinct banks.
 #include "cplx.cuh"
 #include "sft_internal.h"
 
 namespace sft {
 
 namespace {
+
+__device__ __forceinline__ int pad16(int n) { return n + (n >> 4); }
+template <int M> constexpr int padded_len() { return M + M / 16; }
 
 // e^{-2 pi i k / 16}, k = 0..15 (mathematical constants, correctly rounded).
 __device__ __constant__ double kW16re[16] = {
@@ -28,9 +33,20 @@ __device__ __constant__ double kW16im[16] = {
     0.0, 0.38268343236508977, 0.70710678118654752, 0.92387953251128674,
     1.0, 0.92387953251128674, 0.70710678118654752, 0.38268343236508977};
 
+__device__ __constant__ float kW16reF[16] = {
+    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+__device__ __constant__ float kW16imF[16] = {
+    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
+
 template <typename C> __device__ __forceinline__ C w16(int k);
 template <> __device__ __forceinline__ float2 w16<float2>(int k) {
-  return make_float2((float)kW16re[k], (float)kW16im[k]);
+  return make_float2(kW16reF[k], kW16imF[k]);
 }
 template <> __device__ __forceinline__ double2 w16<double2>(int k) {
   return make_double2(kW16re[k], kW16im[k]);
@@ -95,7 +111,7 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
     const int i = lt + it * TPT;
     const int k = i & (SPAN - 1);
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[it * RAD + r] = s[i + r * (M / RAD)];
+    for (int r = 0; r < RAD; ++r) v[it * RAD + r] = s[pad16(i + r * (M / RAD))];
     if (SPAN > 1) {
 #pragma unroll
       for (int r = 1; r < RAD; ++r)
@@ -110,7 +126,7 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
     const int k = i & (SPAN - 1);
     const int j0 = (i - k) * RAD + k;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) s[j0 + r * SPAN] = v[it * RAD + r];
+    for (int r = 0; r < RAD; ++r) s[pad16(j0 + r * SPAN)] = v[it * RAD + r];
   }
   __syncthreads();
 }
@@ -128,8 +144,10 @@ struct FFTPasses<C, M, M, TPT> {
   __device__ static __forceinline__ void run(C*, int, const C*) {}
 };
 
+// FP32 transforms up to M = 8192 are limited to 64 registers so that two CTAs share an SM.
 template <typename R, int M>
-__global__ void __launch_bounds__((M / 16) > 256 ? (M / 16) : 256)
+__global__ void __launch_bounds__((M / 16) > 256 ? (M / 16) : 256,
+                                  (sizeof(R) == 4 && M <= 8192) ? 2 : 1)
 bluestein_kernel(DevPlan d) {
   using C = typename Cx<R>::T;
   constexpr int TPT = M / 16;                      // threads per transform
@@ -156,17 +174,17 @@ bluestein_kernel(DevPlan d) {
   const C* chirp = reinterpret_cast<const C*>(d.chirp) + (int64_t)j * d.pmax;
   const C* vhat = reinterpret_cast<const C*>(d.vhat) + (int64_t)j * M;
   const C* W = reinterpret_cast<const C*>(d.fftw);
-  C* s = buf + g * M;
+  C* s = buf + g * padded_len<M>();
 
   for (int n = lt; n < M; n += TPT)
-    s[n] = (active && n < p) ? cmul(in[n], __ldg(chirp + n)) : czero<C>();
+    s[pad16(n)] = (active && n < p) ? cmul(in[n], __ldg(chirp + n)) : czero<C>();
   __syncthreads();
   FFTPasses<C, M, 1, TPT>::run(s, lt, W);
-  for (int n = lt; n < M; n += TPT) s[n] = cconj(cmul(s[n], __ldg(vhat + n)));
+  for (int n = lt; n < M; n += TPT) s[pad16(n)] = cconj(cmul(s[pad16(n)], __ldg(vhat + n)));
   __syncthreads();
   FFTPasses<C, M, 1, TPT>::run(s, lt, W);
   if (active)
-    for (int c = lt; c < p; c += TPT) out[c] = cmul(cconj(s[c]), __ldg(chirp + c));
+    for (int c = lt; c < p; c += TPT) out[c] = cmul(cconj(s[pad16(c)]), __ldg(chirp + c));
 }
 
 template <typename R, int M>
@@ -174,7 +192,7 @@ cudaError_t launch_M(const DevPlan& d, cudaStream_t st) {
   using C = typename Cx<R>::T;
   constexpr int G = (M >= 4096) ? 1 : 4096 / M;
   constexpr int threads = (M / 16) * G;
-  const size_t smem = (size_t)G * M * sizeof(C);
+  const size_t smem = (size_t)G * padded_len<M>() * sizeof(C);
   cudaError_t e = cudaFuncSetAttribute(bluestein_kernel<R, M>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -15,11 +15,27 @@
 // once, by the smallest such j'.  Its estimate is (-1)^w times the componentwise medians of
 // Z_0[w mod p_j'] over all K primes (eq. GSFT_Estimate).
 #include "cplx.cuh"
+#include "select_sort.cuh"
 #include "sft_internal.h"
 
 namespace sft {
 
 namespace {
+
+// x mod t for 0 <= x < 2^63 and 2 <= t <= 64 in 32-bit arithmetic (a 64-bit '%' would run the
+// FP64-based division routine).
+__device__ __forceinline__ int mod_small(int64_t x, int t) {
+  const uint64_t u = (uint64_t)x;
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const uint32_t r32 = (0xFFFFFFFFu % (uint32_t)t + 1u) % (uint32_t)t;   // 2^32 mod t
+  return (int)(((hi % (uint32_t)t) * r32 + lo % (uint32_t)t) % (uint32_t)t);
+}
+
+// w mod p (floor) for |w| < 2^31
+__device__ __forceinline__ int mod_p(int64_t w, int p) {
+  const int r = (int)w % p;
+  return r < 0 ? r + p : r;
+}
 
 __device__ __forceinline__ void decode_bin(const DevPlan& d, int64_t gid, int& qi, int& j, int& b) {
   qi = (int)(gid / d.Ptot);
@@ -27,6 +43,58 @@ __device__ __forceinline__ void decode_bin(const DevPlan& d, int64_t gid, int& q
   j = 0;
   while (j + 1 < d.K && bin >= d.poff[j + 1]) ++j;
   b = bin - d.poff[j];
+}
+
+// Residue of bin b modulo a small modulus T: argmax over r of |X_r|^2 with
+// X_r = sum_{k2 < T} Z_{k2}[b] e^{-2 pi i k2 r / T} (the 1/T factor does not change the argmax);
+// exact ties go to the smaller sub-bin index u = (r - b) p^{-1} mod T.
+template <int T, typename C, typename R>
+__device__ __forceinline__ int residue_t(C z0, const C* Zl, int64_t p, const C* twl, int bt, int pinv) {
+  C z[T], tw[T];
+  z[0] = z0;
+#pragma unroll
+  for (int k2 = 1; k2 < T; ++k2) z[k2] = Zl[(int64_t)k2 * p];
+#pragma unroll
+  for (int k = 0; k < T; ++k) tw[k] = __ldg(twl + k);
+  R best = (R)-1;
+  int bestu = 1 << 30, bestr = 0;
+#pragma unroll
+  for (int r = 0; r < T; ++r) {
+    C X = z[0];
+#pragma unroll
+    for (int k2 = 1; k2 < T; ++k2) X = cadd(X, cmul(z[k2], tw[(k2 * r) % T]));
+    const R m2 = X.x * X.x + X.y * X.y;
+    const int u = (((r - bt) % T + T) % T) * pinv % T;
+    if (m2 > best || (m2 == best && u < bestu)) {
+      best = m2;
+      bestu = u;
+      bestr = r;
+    }
+  }
+  return bestr;
+}
+
+template <typename C, typename R>
+__device__ int residue_any(int t, C z0, const C* Zl, int64_t p, const C* twl, int bt, int pinv) {
+  R best = (R)-1;
+  int bestu = 1 << 30, bestr = 0;
+  for (int r = 0; r < t; ++r) {
+    C X = z0;
+    int idx = 0;
+    for (int k2 = 1; k2 < t; ++k2) {
+      idx += r;
+      if (idx >= t) idx -= t;
+      X = cadd(X, cmul(Zl[(int64_t)k2 * p], __ldg(twl + idx)));
+    }
+    const R m2 = X.x * X.x + X.y * X.y;
+    const int u = (((r - bt) % t + t) % t) * pinv % t;
+    if (m2 > best || (m2 == best && u < bestu)) {
+      best = m2;
+      bestu = u;
+      bestr = r;
+    }
+  }
+  return bestr;
 }
 
 template <typename R>
@@ -47,49 +115,26 @@ __global__ void __launch_bounds__(256) identify_kernel(DevPlan d) {
     const C* twl = tw + d.twoff[l];
     const int pinv = d.pinv[j * d.nT + l];
     const int bt = b % t;
-    R best = (R)-1;
-    int bestu = 1 << 30, bestr = 0;
-    for (int r = 0; r < t; ++r) {
-      C X = z0;
-      int idx = 0;
-      for (int k2 = 1; k2 < t; ++k2) {
-        idx += r;
-        if (idx >= t) idx -= t;                              // idx = k2 r mod t
-        X = cadd(X, cmul(Zl[(int64_t)k2 * p], __ldg(twl + idx)));
-      }
-      const R m2 = X.x * X.x + X.y * X.y;
-      const int u = (((r - bt) % t + t) % t) * pinv % t;
-      if (m2 > best || (m2 == best && u < bestu)) {
-        best = m2;
-        bestu = u;
-        bestr = r;
-      }
+    int r;
+    switch (t) {
+      case 2: r = residue_t<2, C, R>(z0, Zl, p, twl, bt, pinv); break;
+      case 3: r = residue_t<3, C, R>(z0, Zl, p, twl, bt, pinv); break;
+      case 5: r = residue_t<5, C, R>(z0, Zl, p, twl, bt, pinv); break;
+      case 7: r = residue_t<7, C, R>(z0, Zl, p, twl, bt, pinv); break;
+      case 11: r = residue_t<11, C, R>(z0, Zl, p, twl, bt, pinv); break;
+      case 13: r = residue_t<13, C, R>(z0, Zl, p, twl, bt, pinv); break;
+      default: r = residue_any<C, R>(t, z0, Zl, p, twl, bt, pinv); break;
     }
-    d.resid[gid * d.nT + l] = (uint8_t)bestr;
+    d.resid[gid * d.nT + l] = (uint8_t)r;
     const int g = d.garner[j * d.nT + l];
-    const int xm = (int)(x % t);
-    const int v = (((bestr - xm) % t + t) % t) * g % t;
+    const int xm = mod_small(x, t);
+    const int v = (((r - xm) % t + t) % t) * g % t;
     x += Mx * v;
     Mx *= t;
   }
   const int64_t N = d.N;
   int64_t w = (x <= N / 2) ? x : x - d.Mj[j];
   d.cand[gid] = (w > -((N + 1) / 2)) ? w : kNoFreq;
-}
-
-template <typename T>
-__device__ __forceinline__ void sort_small(T* a, int n) {
-  for (int i = 1; i < n; ++i) {
-    T v = a[i];
-    int k = i - 1;
-    while (k >= 0 && a[k] > v) { a[k + 1] = a[k]; --k; }
-    a[k + 1] = v;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ double median_sorted(const T* a, int n) {
-  return (n & 1) ? (double)a[n / 2] : 0.5 * ((double)a[n / 2 - 1] + (double)a[n / 2]);
 }
 
 template <typename R>
@@ -105,7 +150,7 @@ __global__ void __launch_bounds__(256) vote_kernel(DevPlan d) {
   int cnt = 0, jmin = d.K;
   int bb[kMaxK];
   for (int jj = 0; jj < d.K; ++jj) {
-    bb[jj] = (int)fmod64(w, d.p[jj]);
+    bb[jj] = mod_p(w, d.p[jj]);
     if (cq[d.poff[jj] + bb[jj]] == w) {
       ++cnt;
       if (jj < jmin) jmin = jj;
@@ -119,13 +164,11 @@ __global__ void __launch_bounds__(256) vote_kernel(DevPlan d) {
     re[jj] = y.x;
     im[jj] = y.y;
   }
-  sort_small(re, d.K);
-  sort_small(im, d.K);
   const double sg = (w & 1) ? -1.0 : 1.0;
   Voted rec;
   rec.w = w;
-  rec.zre = sg * median_sorted(re, d.K);
-  rec.zim = sg * median_sorted(im, d.K);
+  rec.zre = sg * median_of<kMaxK>(re, d.K);
+  rec.zim = sg * median_of<kMaxK>(im, d.K);
   rec.votes = cnt;
   rec.jmin = jmin;
   const int slot = atomicAdd(d.counters + qi, 1);

@@ -253,6 +253,19 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   d.G0 = 1.0 / ((double)N * c1);
   d.gamma = 2.0 * kPi * kPi / (((double)N * c1) * ((double)N * c1));
   d.vcap = (int32_t)sump;
+  d.gamma32 = (float)d.gamma;
+  d.G032 = (float)d.G0;
+  d.c1f = (float)c1;
+  for (int i = 0; i < nq; ++i) d.qN32[i] = (float)((double)shifts[i] / (double)N);
+  for (int j = 0; j < K; ++j) {
+    d.Nqp[j] = (int32_t)(N / primes[j]);
+    d.Nrp[j] = (int32_t)(N % primes[j]);
+  }
+  for (int l = 0; l < nT; ++l) {
+    d.Nqt[l] = (int32_t)(N / small[l]);
+    d.Nrt[l] = (int32_t)(N % small[l]);
+  }
+  d.nchunk = (pmax + kReChunk - 1) / kReChunk;
   {
     const double far = (double)N - v->kappa - 0.5;
     if (d.gamma * far * far < 40.0) {
@@ -331,7 +344,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   const size_t o_voted = soff;   soff = align256(soff + (size_t)nq * d.vcap * sizeof(Voted));
   const size_t o_pool = soff;    soff = align256(soff + (size_t)nq * s * sizeof(Pooled));
   const size_t o_win = soff;     soff = align256(soff + (size_t)s * sizeof(Pooled));
-  const size_t o_ybuf = soff;    soff = align256(soff + (size_t)s * K * sizeof(double2));
+  const size_t o_ybuf = soff;    soff = align256(soff + (size_t)d.nchunk * s * K * sizeof(double2));
   const size_t total = soff;
 
   char* base = nullptr;

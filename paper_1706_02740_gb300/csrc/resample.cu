@@ -10,8 +10,10 @@
 // (G0 = 1/(N c1), gamma = 2 pi^2 / (N c1)^2).  Only the n = 0 image of the periodic Gaussian is
 // kept: the plan requires gamma (N - kappa - 1/2)^2 >= 40, so every other image is below e^{-40} of
 // the window's central weight.  The table
-// e^{-2 pi i (q i mod N) / N} is reduced exactly on the host; the node phase q d0 is an exact
-// integer with |q d0| <= P N / 4, so no reduction is needed before the sincos.
+// e^{-2 pi i (q i mod N) / N} is reduced exactly on the host; the node phase has
+// |q d0 / (P N)| <= 1/4 and needs no reduction: the FP32 path forms it as the product of the two
+// correctly rounded ratios d0/P and q/N, the FP64 path from the exact integer q d0.  The FP32
+// path keeps FP64 and 64-bit integer division entirely off its instruction stream.
 #include "cplx.cuh"
 #include "sft_internal.h"
 
@@ -25,6 +27,13 @@ struct NodeGeom {
   int32_t PP;   // node modulus P (p_j or p_j t_l)
 };
 
+// Node k of modulus P sits at x = -pi + 2 pi k / P.  For the subset (l, k2) of prime p_j the node
+// is -pi + 2 pi (k1/p + k2/t), i.e. k = (k1 t + k2 p) mod P, P = p t.  With N = Nq p + Nr and
+// N = Nq' t + Nr',
+//     kN / P = I + G / P (mod N),  I = k1 Nq + (k1 Nr) div p + k2 Nq' + (k2 Nr') div t,
+//     G = ((k1 Nr) mod p) t + ((k2 Nr') mod t) p  in [0, 2P),
+// so the nearest grid index (ties up) is j' = I + round(G / P) and d0 = kN - j'P = G - round(G/P) P,
+// all in 32-bit integer arithmetic (no 64-bit division).
 __device__ __forceinline__ void decode_node(const DevPlan& d, int64_t node, int& j, int& k1, NodeGeom& g) {
   j = 0;
   while (j + 1 < d.K && node >= d.nodeoff[j + 1]) ++j;
@@ -32,23 +41,48 @@ __device__ __forceinline__ void decode_node(const DevPlan& d, int64_t node, int&
   const int local = (int)(node - d.nodeoff[j]);
   const int sub = local / p;
   k1 = local - sub * p;
-  int64_t k, PP;
+  const int a1 = k1 * d.Nrp[j];                 // < p^2
+  const int q1 = a1 / p;
+  const int F1 = a1 - q1 * p;
+  int64_t I = (int64_t)k1 * d.Nqp[j] + q1;
+  int G, PP;
   if (sub == 0) {
     PP = p;
-    k = k1;
+    G = F1;
   } else {
-    const int t = d.t[d.sub_l[sub]];
+    const int l = d.sub_l[sub];
+    const int t = d.t[l];
     const int k2 = d.sub_k2[sub];
-    PP = (int64_t)p * t;
-    k = ((int64_t)k1 * t + (int64_t)k2 * p) % PP;   // node -pi + 2 pi (k1/p + k2/t)
+    const int a2 = k2 * d.Nrt[l];
+    const int q2 = a2 / t;
+    const int F2 = a2 - q2 * t;
+    I += (int64_t)k2 * d.Nqt[l] + q2;
+    PP = p * t;
+    G = F1 * t + F2 * p;
   }
-  const int64_t kN = k * d.N;
-  int64_t jp = (2 * kN + PP) / (2 * PP);            // round(kN/P), ties up
-  g.d0 = (int32_t)(kN - jp * PP);
-  if (jp >= d.N) jp -= d.N;
+  const int rnd = (2 * G >= 3 * PP) ? 2 : ((2 * G >= PP) ? 1 : 0);
+  g.d0 = G - rnd * PP;
+  int64_t jp = I + rnd;
+  while (jp >= d.N) jp -= d.N;
   g.jp = jp;
-  g.PP = (int32_t)PP;
+  g.PP = PP;
 }
+
+// Node phase exp(2 pi i q d0 / (P N)) of shift qi (|q d0 / (P N)| <= 1/4, so it needs no reduction).
+__device__ __forceinline__ float2 node_phase(const DevPlan& d, int qi, float v0, const NodeGeom&) {
+  return expi_turns(v0 * d.qN32[qi]);
+}
+__device__ __forceinline__ double2 node_phase(const DevPlan& d, int qi, double, const NodeGeom& g) {
+  const int64_t num = d.q[qi] * (int64_t)g.d0;           // exact
+  return expi_turns((double)num / ((double)g.PP * (double)d.N));
+}
+
+template <typename R> __device__ __forceinline__ R gamma_of(const DevPlan& d);
+template <> __device__ __forceinline__ float gamma_of<float>(const DevPlan& d) { return d.gamma32; }
+template <> __device__ __forceinline__ double gamma_of<double>(const DevPlan& d) { return d.gamma; }
+template <typename R> __device__ __forceinline__ R g0_of(const DevPlan& d);
+template <> __device__ __forceinline__ float g0_of<float>(const DevPlan& d) { return d.G032; }
+template <> __device__ __forceinline__ double g0_of<double>(const DevPlan& d) { return d.G0; }
 
 template <typename IN> struct InLoad;
 template <> struct InLoad<float2> {
@@ -122,7 +156,7 @@ __global__ void __launch_bounds__(256) resample_kernel(DevPlan d, const IN* __re
 
   // Gaussian weights G0 exp(-gamma (v0 - i)^2), v0 = d0 / P
   const R v0 = (R)g.d0 / (R)g.PP;
-  const R gam = (R)d.gamma, G0 = (R)d.G0;
+  const R gam = gamma_of<R>(d), G0 = g0_of<R>(d);
 #pragma unroll
   for (int i = 0; i < W; ++i) {
     const R v = v0 - (R)(i - KAPPA);
@@ -131,15 +165,12 @@ __global__ void __launch_bounds__(256) resample_kernel(DevPlan d, const IN* __re
 
   const C* T = reinterpret_cast<const C*>(d.Ttab);
   C* out = reinterpret_cast<C*>(d.samples);
-  const R inv_PN = (R)1 / ((R)g.PP * (R)d.N);
   for (int qi = 0; qi < d.nq; ++qi) {
     C acc = czero<C>();
     const C* Tq = T + qi * W;
 #pragma unroll
     for (int i = 0; i < W; ++i) acc = cadd(acc, cmul(win[i], __ldg(Tq + i)));
-    const int64_t num = d.q[qi] * (int64_t)g.d0;           // exact, |num| <= P N / 4
-    const C ph = expi_turns((R)num * inv_PN);
-    out[(int64_t)qi * d.m + node] = cmul(acc, ph);
+    out[(int64_t)qi * d.m + node] = cmul(acc, node_phase(d, qi, v0, g));
   }
 }
 
@@ -154,10 +185,9 @@ __global__ void __launch_bounds__(128) resample_kernel_generic(DevPlan d, const 
   decode_node(d, node, j, k1, g);
   const int KAPPA = d.kappa, W = 2 * KAPPA + 1;
   const R v0 = (R)g.d0 / (R)g.PP;
-  const R gam = (R)d.gamma, G0 = (R)d.G0;
+  const R gam = gamma_of<R>(d), G0 = g0_of<R>(d);
   const C* T = reinterpret_cast<const C*>(d.Ttab);
   C* out = reinterpret_cast<C*>(d.samples);
-  const R inv_PN = (R)1 / ((R)g.PP * (R)d.N);
   C acc[kMaxQ];
   for (int qi = 0; qi < d.nq; ++qi) acc[qi] = czero<C>();
   for (int i = 0; i < W; ++i) {
@@ -168,10 +198,8 @@ __global__ void __launch_bounds__(128) resample_kernel_generic(DevPlan d, const 
     const C fw = cscale(widen<R, C, IN>(InLoad<IN>::one(f, idx)), G0 * r_exp(-gam * v * v));
     for (int qi = 0; qi < d.nq; ++qi) acc[qi] = cadd(acc[qi], cmul(fw, __ldg(T + qi * W + i)));
   }
-  for (int qi = 0; qi < d.nq; ++qi) {
-    const int64_t num = d.q[qi] * (int64_t)g.d0;
-    out[(int64_t)qi * d.m + node] = cmul(acc[qi], expi_turns((R)num * inv_PN));
-  }
+  for (int qi = 0; qi < d.nq; ++qi)
+    out[(int64_t)qi * d.m + node] = cmul(acc[qi], node_phase(d, qi, v0, g));
 }
 
 template <typename R, typename IN>

@@ -3,136 +3,299 @@
 // shift_select: per shift q, R_temp = the s voted frequencies of largest |z| (ties: smaller w);
 // those inside [q - L, q + L) and B are divided by the modulated filter's Fourier coefficient
 // g_hat_{w - q} = e^{-c1^2 (w - q)^2 / 2} / sqrt(2 pi) (Lemma Periodic_Gaussian_FC) and pooled.
-// global_select: the s pooled pairs of largest |c| (ties: smaller w), in rank order.
+// global_select: the s pooled pairs of largest |c| (ties: smaller w) become the winners.
+// finalize: the winners in order, |c| descending, ties by the smaller frequency.
 //
-// Lists are short (about s entries per shift), so each element's rank is counted directly against
-// every other element of its list (keys are distinct: frequencies are distinct within a list),
-// with the list staged through shared memory in tiles.  Ranks are exact and deterministic whatever
-// order the atomics of the vote kernel produced.
+// Only membership matters at the first two points (the winners are put in order once, at the end),
+// so a list of at most s entries is taken whole without sorting.  A longer list of up to kSortCap
+// entries is sorted by one CTA (register/shuffle bitonic network on integer keys); a longer one
+// still falls back to counting each element's rank against the whole list.  The kernels of both
+// branches are launched and each checks the list length on the device.
 #include <algorithm>
 
 #include "cplx.cuh"
+#include "select_sort.cuh"
 #include "sft_internal.h"
 
 namespace sft {
 
 namespace {
 
-constexpr int kTile = 256;
-constexpr double kSqrt2Pi = 2.5066282746310002;  // sqrt(2 pi)
-
-// a precedes b: larger magnitude first, then the smaller frequency
-__device__ __forceinline__ bool precedes(double ma, int64_t wa, double mb, int64_t wb) {
-  return ma > mb || (ma == mb && wa < wb);
+__device__ __forceinline__ bool in_band(const DevPlan& d, int64_t w, int64_t q) {
+  const int64_t lo = -((d.N + 1) / 2) + 1, hi = d.N / 2;
+  return w >= q - d.L && w < q + d.L && w >= lo && w <= hi;
 }
 
-__global__ void __launch_bounds__(kTile) shift_select_kernel(DevPlan d) {
-  __shared__ double sm[kTile];
-  __shared__ int64_t sw[kTile];
-  const int qi = blockIdx.y;
+// 1 / g_hat_{w - q} = sqrt(2 pi) e^{c1^2 (w - q)^2 / 2}; FP32 on the FP32 path (the winners are
+// re-estimated and divided again in FP64 later), FP64 on the FP64 path.
+__device__ __forceinline__ void pool_append(const DevPlan& d, const Voted& v, int qi) {
+  const int64_t q = d.q[qi];
+  if (!in_band(d, v.w, q)) return;
+  Pooled pr;
+  if (d.prec == SFT_FP32) {
+    const float x = d.c1f * (float)(v.w - q);
+    const float inv_ghat = 2.50662827463f * expf(0.5f * x * x);
+    pr.cre = (double)((float)v.zre * inv_ghat);
+    pr.cim = (double)((float)v.zim * inv_ghat);
+  } else {
+    const double x = d.c1 * (double)(v.w - q);
+    const double inv_ghat = 2.5066282746310002 * exp(0.5 * x * x);
+    pr.cre = v.zre * inv_ghat;
+    pr.cim = v.zim * inv_ghat;
+  }
+  pr.w = v.w;
+  pr.qi = qi;
+  pr.pad = 0;
+  const int slot = atomicAdd(d.counters + d.nq, 1);
+  if (slot < d.nq * d.s) d.pool[slot] = pr;
+}
+
+__device__ __forceinline__ uint64_t vkey(const Voted& v) {
+  return mag_key(v.zre * v.zre + v.zim * v.zim);
+}
+__device__ __forceinline__ uint64_t pkey(const Pooled& p) {
+  return mag_key(p.cre * p.cre + p.cim * p.cim);
+}
+
+__global__ void __launch_bounds__(kSortThreads) shift_select(DevPlan d) {
+  const int qi = blockIdx.x;
   const int n = min(d.counters[qi], d.vcap);
   const Voted* V = d.voted + (int64_t)qi * d.vcap;
-  const int64_t q = d.q[qi];
-  for (int base = blockIdx.x * kTile; base < n; base += gridDim.x * kTile) {
+  if (n <= d.s) {
+    for (int i = threadIdx.x; i < n; i += kSortThreads) pool_append(d, V[i], qi);
+    return;
+  }
+  if (n > kSortCap) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Rec* S = reinterpret_cast<Rec*>(smem_raw);
+  const int slots = sort_slots(n);
+  for (int i = threadIdx.x; i < slots; i += kSortThreads) {
+    if (i < n) {
+      const Voted v = V[i];
+      S[i].m = vkey(v);
+      S[i].w = v.w;
+      S[i].ix = i;
+      S[i].pad = 0;
+    } else {
+      S[i] = pad_rec(i);
+    }
+  }
+  __syncthreads();
+  sort_smem(S, n);
+  for (int i = threadIdx.x; i < d.s; i += kSortThreads) pool_append(d, V[S[i].ix], qi);
+}
+
+__global__ void __launch_bounds__(kRankThreads) shift_select_rank(DevPlan d) {
+  __shared__ uint64_t sm[kRankThreads];
+  __shared__ int64_t sw[kRankThreads];
+  const int qi = blockIdx.y;
+  const int n = min(d.counters[qi], d.vcap);
+  if (n <= kSortCap || n <= d.s) return;
+  const Voted* V = d.voted + (int64_t)qi * d.vcap;
+  for (int base = blockIdx.x * kRankThreads; base < n; base += gridDim.x * kRankThreads) {
     const int i = base + threadIdx.x;
-    double mi = 0;
-    int64_t wi = 0;
     Voted vi;
+    uint64_t mi = 0;
+    int64_t wi = 0;
     if (i < n) {
       vi = V[i];
-      mi = vi.zre * vi.zre + vi.zim * vi.zim;
+      mi = vkey(vi);
       wi = vi.w;
     }
     int rank = 0;
-    for (int t0 = 0; t0 < n; t0 += kTile) {
+    for (int t0 = 0; t0 < n; t0 += kRankThreads) {
       __syncthreads();
       if (t0 + threadIdx.x < n) {
         const Voted vt = V[t0 + threadIdx.x];
-        sm[threadIdx.x] = vt.zre * vt.zre + vt.zim * vt.zim;
+        sm[threadIdx.x] = vkey(vt);
         sw[threadIdx.x] = vt.w;
       }
       __syncthreads();
-      const int lim = min(kTile, n - t0);
+      const int lim = min(kRankThreads, n - t0);
       if (i < n)
         for (int k = 0; k < lim; ++k) rank += precedes(sm[k], sw[k], mi, wi) ? 1 : 0;
     }
-    if (i < n && rank < d.s) {
-      const int64_t lo = -((d.N + 1) / 2) + 1, hi = d.N / 2;
-      if (wi >= q - d.L && wi < q + d.L && wi >= lo && wi <= hi) {
-        const double x = d.c1 * (double)(wi - q);
-        const double inv_ghat = kSqrt2Pi * exp(0.5 * x * x);
-        Pooled pr;
-        pr.w = wi;
-        pr.cre = vi.zre * inv_ghat;
-        pr.cim = vi.zim * inv_ghat;
-        pr.qi = qi;
-        pr.pad = 0;
-        const int slot = atomicAdd(d.counters + d.nq, 1);
-        if (slot < d.nq * d.s) d.pool[slot] = pr;
-      }
-    }
+    if (i < n && rank < d.s) pool_append(d, vi, qi);
   }
 }
 
-// Rank the pool; write winners[rank] and, when out_w is given, the final output directly.
-__global__ void __launch_bounds__(kTile) global_select_kernel(DevPlan d, int64_t* out_w,
-                                                              double2* out_c, int32_t* out_n) {
-  __shared__ double sm[kTile];
-  __shared__ int64_t sw[kTile];
-  const int n = min(d.counters[d.nq], d.nq * d.s);
-  const int limit = max(n, d.s);
+__device__ __forceinline__ void set_count(const DevPlan& d, int n, int32_t* out_n) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     d.counters[d.nq + 2] = min(n, d.s);
     if (out_n) *out_n = min(n, d.s);
   }
-  for (int base = blockIdx.x * kTile; base < limit; base += gridDim.x * kTile) {
+}
+
+__global__ void __launch_bounds__(kSortThreads) global_select(DevPlan d, int32_t* out_n) {
+  const int n = min(d.counters[d.nq], d.nq * d.s);
+  if (n <= d.s) {
+    set_count(d, n, out_n);
+    for (int i = threadIdx.x; i < n; i += kSortThreads) d.winners[i] = d.pool[i];
+    return;
+  }
+  if (n > kSortCap) return;
+  set_count(d, n, out_n);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Rec* S = reinterpret_cast<Rec*>(smem_raw);
+  const int slots = sort_slots(n);
+  for (int i = threadIdx.x; i < slots; i += kSortThreads) {
+    if (i < n) {
+      const Pooled p = d.pool[i];
+      S[i].m = pkey(p);
+      S[i].w = p.w;
+      S[i].ix = i;
+      S[i].pad = 0;
+    } else {
+      S[i] = pad_rec(i);
+    }
+  }
+  __syncthreads();
+  sort_smem(S, n);
+  for (int i = threadIdx.x; i < d.s; i += kSortThreads) d.winners[i] = d.pool[S[i].ix];
+}
+
+__global__ void __launch_bounds__(kRankThreads) global_select_rank(DevPlan d, int32_t* out_n) {
+  __shared__ uint64_t sm[kRankThreads];
+  __shared__ int64_t sw[kRankThreads];
+  const int n = min(d.counters[d.nq], d.nq * d.s);
+  if (n <= kSortCap || n <= d.s) return;
+  set_count(d, n, out_n);
+  for (int base = blockIdx.x * kRankThreads; base < n; base += gridDim.x * kRankThreads) {
     const int i = base + threadIdx.x;
-    double mi = 0;
-    int64_t wi = 0;
     Pooled pi;
+    uint64_t mi = 0;
+    int64_t wi = 0;
     if (i < n) {
       pi = d.pool[i];
-      mi = pi.cre * pi.cre + pi.cim * pi.cim;
+      mi = pkey(pi);
       wi = pi.w;
     }
     int rank = 0;
-    for (int t0 = 0; t0 < n; t0 += kTile) {
+    for (int t0 = 0; t0 < n; t0 += kRankThreads) {
       __syncthreads();
       if (t0 + threadIdx.x < n) {
         const Pooled pt = d.pool[t0 + threadIdx.x];
-        sm[threadIdx.x] = pt.cre * pt.cre + pt.cim * pt.cim;
+        sm[threadIdx.x] = pkey(pt);
         sw[threadIdx.x] = pt.w;
       }
       __syncthreads();
-      const int lim = min(kTile, n - t0);
+      const int lim = min(kRankThreads, n - t0);
       if (i < n)
         for (int k = 0; k < lim; ++k) rank += precedes(sm[k], sw[k], mi, wi) ? 1 : 0;
     }
-    if (i < n && rank < d.s) {
-      d.winners[rank] = pi;
-      if (out_w) {
-        out_w[rank] = pi.w;
-        out_c[rank] = make_double2(pi.cre, pi.cim);
-      }
+    if (i < n && rank < d.s) d.winners[rank] = pi;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) finalize_sorted(DevPlan d, int64_t* out_w,
+                                                                double2* out_c) {
+  const int n = d.counters[d.nq + 2];
+  if (n > kSortCap || !out_w) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Rec* S = reinterpret_cast<Rec*>(smem_raw);
+  const int slots = sort_slots(n);
+  for (int i = threadIdx.x; i < slots; i += kSortThreads) {
+    if (i < n) {
+      const Pooled p = d.winners[i];
+      S[i].m = pkey(p);
+      S[i].w = p.w;
+      S[i].ix = i;
+      S[i].pad = 0;
+    } else {
+      S[i] = pad_rec(i);
     }
-    if (out_w && i >= n && i < d.s) {
+  }
+  __syncthreads();
+  sort_smem(S, n);
+  for (int i = threadIdx.x; i < n; i += kSortThreads) {
+    const Pooled p = d.winners[S[i].ix];
+    out_w[i] = p.w;
+    out_c[i] = make_double2(p.cre, p.cim);
+  }
+  for (int i = n + threadIdx.x; i < d.s; i += kSortThreads) {
+    out_w[i] = 0;
+    out_c[i] = make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void __launch_bounds__(kRankThreads) finalize_rank(DevPlan d, int64_t* out_w,
+                                                              double2* out_c) {
+  __shared__ uint64_t sm[kRankThreads];
+  __shared__ int64_t sw[kRankThreads];
+  const int n = d.counters[d.nq + 2];
+  if (n <= kSortCap || !out_w) return;
+  const int limit = max(n, d.s);
+  for (int base = blockIdx.x * kRankThreads; base < limit; base += gridDim.x * kRankThreads) {
+    const int i = base + threadIdx.x;
+    Pooled pi;
+    uint64_t mi = 0;
+    int64_t wi = 0;
+    if (i < n) {
+      pi = d.winners[i];
+      mi = pkey(pi);
+      wi = pi.w;
+    }
+    int rank = 0;
+    for (int t0 = 0; t0 < n; t0 += kRankThreads) {
+      __syncthreads();
+      if (t0 + threadIdx.x < n) {
+        const Pooled pt = d.winners[t0 + threadIdx.x];
+        sm[threadIdx.x] = pkey(pt);
+        sw[threadIdx.x] = pt.w;
+      }
+      __syncthreads();
+      const int lim = min(kRankThreads, n - t0);
+      if (i < n)
+        for (int k = 0; k < lim; ++k) rank += precedes(sm[k], sw[k], mi, wi) ? 1 : 0;
+    }
+    if (i < n) {
+      out_w[rank] = pi.w;
+      out_c[rank] = make_double2(pi.cre, pi.cim);
+    } else if (i < d.s) {
       out_w[i] = 0;
       out_c[i] = make_double2(0.0, 0.0);
     }
   }
 }
 
+cudaError_t set_smem(const void* fn) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+}
+
 }  // namespace
 
-cudaError_t launch_select(const DevPlan& d, int64_t* out_w, double2* out_c, int32_t* out_n,
-                          cudaStream_t st) {
-  const int chunks = (int)std::min<int64_t>((d.vcap + kTile - 1) / kTile, 64);
-  shift_select_kernel<<<dim3(chunks, d.nq), kTile, 0, st>>>(d);
-  cudaError_t e = cudaGetLastError();
+int select_launches(const DevPlan& d) {
+  return 2 + (d.vcap > kSortCap ? 1 : 0) + ((int64_t)d.nq * d.s > kSortCap ? 1 : 0);
+}
+
+int finalize_launches(const DevPlan& d) { return 1 + (d.s > kSortCap ? 1 : 0); }
+
+cudaError_t launch_select(const DevPlan& d, int32_t* out_n, cudaStream_t st) {
+  cudaError_t e = set_smem((const void*)shift_select);
+  if (e == cudaSuccess) e = set_smem((const void*)global_select);
   if (e != cudaSuccess) return e;
-  const int64_t lim = std::max<int64_t>((int64_t)d.nq * d.s, d.s);
-  const int g2 = (int)std::min<int64_t>((lim + kTile - 1) / kTile, 256);
-  global_select_kernel<<<g2, kTile, 0, st>>>(d, out_w, out_c, out_n);
+  shift_select<<<d.nq, kSortThreads, kSortSmem, st>>>(d);
+  if (d.vcap > kSortCap) {
+    const int chunks = (int)std::min<int64_t>((d.vcap + kRankThreads - 1) / kRankThreads, 64);
+    shift_select_rank<<<dim3(chunks, d.nq), kRankThreads, 0, st>>>(d);
+  }
+  global_select<<<1, kSortThreads, kSortSmem, st>>>(d, out_n);
+  if ((int64_t)d.nq * d.s > kSortCap) {
+    const int64_t lim = (int64_t)d.nq * d.s;
+    const int g2 = (int)std::min<int64_t>((lim + kRankThreads - 1) / kRankThreads, 256);
+    global_select_rank<<<g2, kRankThreads, 0, st>>>(d, out_n);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const DevPlan& d, int64_t* out_w, double2* out_c, cudaStream_t st) {
+  cudaError_t e = set_smem((const void*)finalize_sorted);
+  if (e != cudaSuccess) return e;
+  finalize_sorted<<<1, kSortThreads, kSortSmem, st>>>(d, out_w, out_c);
+  if (d.s > kSortCap) {
+    const int g = (int)std::min<int64_t>((d.s + kRankThreads - 1) / kRankThreads, 256);
+    finalize_rank<<<g, kRankThreads, 0, st>>>(d, out_w, out_c);
+  }
   return cudaGetLastError();
 }
 

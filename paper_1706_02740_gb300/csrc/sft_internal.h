@@ -58,6 +58,12 @@ struct DevPlan {
   double c1;
   double gamma;               // 2 pi^2 / (N c1)^2: Gaussian exponent per squared grid offset
   double G0;                  // 1 / (N c1): weight prefactor
+  float gamma32, G032, c1f;   // the same, rounded once to FP32
+  float qN32[kMaxQ];          // q / N rounded to FP32 (node phase of the FP32 path)
+  // N = Nq p_j + Nr and N = Nq t_l + Nr: 32-bit pieces of the window-centre computation
+  int32_t Nqp[kMaxK], Nrp[kMaxK];
+  int32_t Nqt[kMaxT], Nrt[kMaxT];
+  int32_t nchunk;             // sample chunks of the re-estimation (ceil(pmax / kReChunk))
   int32_t vcap;               // capacity of each shift's voted list
   int32_t aligned16;          // f is 16-byte aligned (set per execution)
   // device tables
@@ -79,11 +85,21 @@ struct DevPlan {
   Voted* voted;               // [nq][vcap]
   Pooled* pool;               // [nq * s]
   Pooled* winners;            // [s]
-  double2* ybuf;              // [s][K] re-estimated bins
+  double2* ybuf;              // [nchunk][s][K] partial sums of the re-estimated bins
 };
+
+constexpr int kReChunk = 256;   // samples per re-estimation CTA
+
+constexpr int kStages = 6;
+constexpr int kProfileCap = 4096;
 
 struct Plan {
   DevPlan d;
+  // per-stage timing (sft_plan_profile): kStages + 1 events per recorded execution
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  int recorded = 0;
+  int64_t launches = 0;
   double alpha = 0, beta = 0;
   uint64_t seed = 0;
   std::vector<int64_t> shifts;
@@ -98,10 +114,13 @@ cudaError_t launch_resample(const DevPlan& d, const void* f, cudaStream_t st);
 cudaError_t launch_bluestein(const DevPlan& d, cudaStream_t st);
 cudaError_t launch_identify(const DevPlan& d, cudaStream_t st);
 cudaError_t launch_vote(const DevPlan& d, cudaStream_t st);
-cudaError_t launch_select(const DevPlan& d, int64_t* out_w, double2* out_c, int32_t* out_n,
-                          cudaStream_t st);
-cudaError_t launch_refine(const DevPlan& d, int64_t* out_w, double2* out_c, int32_t* out_n,
-                          cudaStream_t st);
+cudaError_t launch_select(const DevPlan& d, int32_t* out_n, cudaStream_t st);
+cudaError_t launch_refine(const DevPlan& d, cudaStream_t st);
+cudaError_t launch_finalize(const DevPlan& d, int64_t* out_w, double2* out_c, cudaStream_t st);
+// kernels each stage launches for this plan (host-side count, matches the launch wrappers)
+int select_launches(const DevPlan& d);
+int refine_launches(const DevPlan& d);
+int finalize_launches(const DevPlan& d);
 
 // Host plan construction (plan.cpp).
 sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,

@@ -1,0 +1,31 @@
+"""Seeded synthetic signals generated directly in device memory (for large N, where building the
+input on the host would dominate a benchmark's set-up time).  Same recipe as synth.signals:
+s distinct frequencies uniform over B, random phase, unit or log-uniform magnitude, f = F^{-1} c
+by one inverse FFT, plus i.i.d. complex Gaussian noise rescaled to an exact SNR.  Contains none of
+the sparse Fourier transform's arithmetic."""
+from __future__ import annotations
+
+import numpy as np
+
+from synth.signals import draw_spectrum
+
+
+def make_device_signal(N: int, s: int, seed: int, magnitude: str = "loguniform",
+                       snr_db: float | None = 30.0, device="cuda", dtype=None):
+    import torch
+    dtype = dtype or torch.complex64
+    omega, coef = draw_spectrum(N, s, seed, magnitude)
+    a = torch.zeros(N, dtype=torch.complex128, device=device)
+    sign = np.where(omega % 2 == 0, 1.0, -1.0)
+    a[torch.from_numpy(np.mod(omega, N)).to(device)] = torch.from_numpy(coef * sign).to(device)
+    f = torch.fft.ifft(a) * N
+    del a
+    if snr_db is not None:
+        g = torch.Generator(device=device)
+        g.manual_seed(seed ^ 0x5EED5EED)
+        n = torch.complex(torch.randn(N, generator=g, device=device, dtype=torch.float64),
+                          torch.randn(N, generator=g, device=device, dtype=torch.float64))
+        target = torch.linalg.vector_norm(f) * 10.0 ** (-snr_db / 20.0)
+        f = f + n * (target / torch.linalg.vector_norm(n))
+        del n
+    return f.to(dtype).contiguous(), omega, coef
