@@ -182,6 +182,29 @@ sft_status sft_plan_profile_read(sft_plan_t plan, double* stage_ms, int32_t* n_e
 /* Total number of kernels this plan has launched (all executions so far). */
 int64_t sft_plan_launches(sft_plan_t plan);
 
+/*
+ * Batched DFT that allocates no device memory, for callers that cannot call cudaMalloc: code that
+ * runs while another component owns the device's memory (a host framework's caching allocator, a
+ * plug-in with a fixed memory budget, or a phase where allocating would stall or fragment the
+ * heap).  The paper has no counterpart: it is a stand-alone use of this library's prime-length DFT
+ * (the chirp-convolution kernel of the measurements).
+ *
+ * Computes, for b = 0..batch-1 and c = 0..n-1,
+ *     out[b n + c] = (1/n) sum_{k=0}^{n-1} in[b n + k] e^{-2 pi i k c / n}
+ * on complex64 vectors (interleaved float re,im, 8-byte aligned, caller-owned), any length
+ * 2 <= n <= 8191 (prime or not), in FP32, on `stream`.
+ *
+ * The kernel's tables (chirp, filter spectrum, FFT twiddles) live in one fixed 320 KiB array in
+ * device memory that the library declares statically: every GPU that loads the library holds it
+ * until the process exits, and nothing is allocated at any call.  The first call on a device looks
+ * up that array's address and builds the tables for n on `stream`; a later call with another n
+ * rebuilds them.  Make that first call on each device before any stream capture.  All calls share
+ * the array, so calls that overlap on the GPU (different streams, or different n in flight) race;
+ * serialise them.  Returns SFT_EINVAL for n outside 2..8191, batch < 1 or NULL/misaligned buffers.
+ */
+sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_dev, void* out_dev,
+                           void* stream);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char* sft_last_error(void);
 

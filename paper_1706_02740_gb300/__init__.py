@@ -68,6 +68,8 @@ EXPORTS = {
     "sft_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int32)]),
     "sft_plan_launches": (ctypes.c_int64, [ctypes.c_void_p]),
+    "sft_dft_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "sft_choose_moduli": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_int64),
@@ -200,6 +202,12 @@ def sft_plan_profile_read(plan: Plan):
     n = ctypes.c_int32()
     _check(load().sft_plan_profile_read(plan.handle, arr, ctypes.byref(n)))
     return dict(zip(STAGES, list(arr))), n.value
+
+
+def sft_dft_noalloc(n: int, batch: int, in_dev: int, out_dev: int, stream: int = 0):
+    """Batched length-n DFT (1/n normalised) of complex64 vectors; allocates no device memory
+    (its tables live in a fixed static device array of the library)."""
+    _check(load().sft_dft_noalloc(int(n), int(batch), in_dev, out_dev, stream))
 
 
 def sft_plan_launches(plan: Plan) -> int:

@@ -11,6 +11,12 @@
 // passes, then one radix 2/4/8 pass), with twiddles read from an exactly rounded table.  The
 // shared-memory layout inserts one pad element after every 16 (index n -> n + n/16), so the
 // strided stores of the first two passes hit distinct banks.
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
 #include "cplx.cuh"
 #include "sft_internal.h"
 
@@ -226,4 +232,159 @@ cudaError_t launch_bluestein(const DevPlan& d, cudaStream_t st) {
   return d.prec == SFT_FP32 ? launch_prec<float>(d, st) : launch_prec<double>(d, st);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Batched DFT that allocates nothing (sft_dft_noalloc).
+//
+// Its tables (the chirp, the transformed filter and the FFT twiddles) live in one file-scope
+// device array of a fixed size; every GPU that loads the library holds it until the process
+// exits.  They are built on the device by the two kernels below the first time a length is used
+// on a device, and rebuilt when the length changes; the transforms themselves run through the
+// same chirp-convolution kernel as the sparse transform.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxN = 8191;           // longest transform: 2n - 1 <= 16384
+constexpr int kNoAllocMaxM = 16384;
+constexpr int kNoAllocChirp = 8192;
+constexpr size_t kNoAllocElems = (size_t)kNoAllocChirp + 2 * (size_t)kNoAllocMaxM;
+constexpr int kMaxDevices = 64;
+
+// chirp [8192] | filter spectrum [16384] | twiddles [16384], complex64: 320 KiB in all
+static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocElems];
+
+std::mutex g_noalloc_mu;
+float2* g_noalloc_ptr[kMaxDevices];     // device address of g_noalloc_scratch, per device
+int g_noalloc_n[kMaxDevices];           // length the tables currently hold (0 = none)
+
+// Twiddles e^{-2 pi i m / M}, the chirp w_k = e^{-pi i (k^2 mod 2n) / n} (k < n) and the wrapped
+// conjugate chirp V (V[k] = V[M - k] = conj(w_k), zero elsewhere), in FP64 then rounded.
+__global__ void noalloc_tables_kernel(int n, int M, float2* chirp, float2* V, float2* W) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)i / (double)M, &s, &c);
+    W[i] = make_float2((float)c, (float)s);
+    int k = -1;
+    if (i < n) k = i;
+    else if (i > M - n) k = M - i;
+    float2 v = make_float2(0.f, 0.f);
+    if (k >= 0) {
+      const int r = (k * k) % (2 * n);                 // k < 8192: k^2 < 2^26
+      sincospi(-(double)r / (double)n, &s, &c);
+      v = make_float2((float)c, -(float)s);
+      if (i < n) chirp[i] = make_float2((float)c, (float)s);
+    }
+    V[i] = v;
+  }
+}
+
+// Filter spectrum: FFT_M(V) / (M n), one CTA, the same shared-memory Stockham passes.
+template <int M>
+__global__ void __launch_bounds__(M / 16) noalloc_filter_kernel(int n, float2* V, const float2* W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* s = reinterpret_cast<float2*>(smem_raw);
+  constexpr int TPT = M / 16;
+  const int lt = threadIdx.x;
+  for (int i = lt; i < M; i += TPT) s[pad16(i)] = V[i];
+  __syncthreads();
+  FFTPasses<float2, M, 1, TPT>::run(s, lt, W);
+  const float scale = (float)(1.0 / ((double)M * (double)n));
+  for (int i = lt; i < M; i += TPT) V[i] = cscale(s[pad16(i)], scale);
+}
+
+template <int M>
+cudaError_t noalloc_build(int n, float2* base, cudaStream_t st) {
+  float2* chirp = base;
+  float2* V = base + kNoAllocChirp;
+  float2* W = V + kNoAllocMaxM;
+  noalloc_tables_kernel<<<(M + 255) / 256, 256, 0, st>>>(n, M, chirp, V, W);
+  const size_t smem = (size_t)padded_len<M>() * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(noalloc_filter_kernel<M>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  noalloc_filter_kernel<M><<<1, M / 16, smem, st>>>(n, V, W);
+  return cudaGetLastError();
+}
+
+cudaError_t noalloc_build_any(int n, int M, float2* base, cudaStream_t st) {
+  switch (M) {
+    case 64: return noalloc_build<64>(n, base, st);
+    case 128: return noalloc_build<128>(n, base, st);
+    case 256: return noalloc_build<256>(n, base, st);
+    case 512: return noalloc_build<512>(n, base, st);
+    case 1024: return noalloc_build<1024>(n, base, st);
+    case 2048: return noalloc_build<2048>(n, base, st);
+    case 4096: return noalloc_build<4096>(n, base, st);
+    case 8192: return noalloc_build<8192>(n, base, st);
+    case 16384: return noalloc_build<16384>(n, base, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
 }  // namespace sft
+
+extern "C" sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_dev, void* out_dev,
+                                      void* stream) {
+  using namespace sft;
+  if (n < 2 || n > kNoAllocMaxN) {
+    set_error("sft_dft_noalloc: length must be in 2..8191 (the static table holds at most 8191)");
+    return SFT_EINVAL;
+  }
+  if (batch < 1 || !in_dev || !out_dev || ((uintptr_t)in_dev % 8) || ((uintptr_t)out_dev % 8)) {
+    set_error("sft_dft_noalloc: need batch >= 1 and non-NULL 8-byte aligned buffers");
+    return SFT_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_error("sft_dft_noalloc: no usable current device");
+    return SFT_ECUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int M = 64;
+  while (M < 2 * n - 1) M <<= 1;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("sft_dft_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      return SFT_ECUDA;
+    }
+    g_noalloc_ptr[dev] = reinterpret_cast<float2*>(p);
+  }
+  float2* base = g_noalloc_ptr[dev];
+  if (g_noalloc_n[dev] != n) {
+    e = noalloc_build_any(n, M, base, st);
+    if (e != cudaSuccess) {
+      g_noalloc_n[dev] = 0;
+      set_error(std::string("sft_dft_noalloc: table build failed: ") + cudaGetErrorString(e));
+      return SFT_ECUDA;
+    }
+    g_noalloc_n[dev] = n;
+  }
+  DevPlan d;
+  memset(&d, 0, sizeof(d));
+  d.prec = SFT_FP32;
+  d.K = 1;
+  d.nsub = 1;
+  d.nq = batch;
+  d.p[0] = n;
+  d.nodeoff[0] = 0;
+  d.nodeoff[1] = n;
+  d.m = n;
+  d.pmax = n;
+  d.fftM = M;
+  d.samples = const_cast<void*>(in_dev);
+  d.bins = out_dev;
+  d.chirp = base;
+  d.vhat = base + kNoAllocChirp;
+  d.fftw = base + kNoAllocChirp + kNoAllocMaxM;
+  e = launch_prec<float>(d, st);
+  if (e != cudaSuccess) {
+    set_error(std::string("sft_dft_noalloc: launch failed: ") + cudaGetErrorString(e));
+    return SFT_ECUDA;
+  }
+  return SFT_OK;
+}
