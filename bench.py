@@ -161,6 +161,21 @@ def dft_flops(info):
 
 
 # ------------------------------------------------------------------------------------------
+# replicas: one process per GPU, independent SFTs, timing aggregated over ranks
+# ------------------------------------------------------------------------------------------
+def aggregate_ranks(elapsed_ms, sfts_per_rank, world, device=None):
+    """Whole-job throughput of independent replicas: every rank ran sfts_per_rank SFTs; the job
+    took the slowest rank's time.  Returns (max elapsed ms over ranks, SFTs/s of all ranks)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, sfts_per_rank * world / (elapsed_ms / 1e3)
+
+
+# ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
@@ -241,12 +256,7 @@ def run_ours(args, rank, world, local_rank):
     lat = sorted(a.elapsed_time(b) for a, b in zip(starts, ends))
     stage_ms, n_rec = sft.sft_plan_profile_read(plan)
     sft.sft_plan_profile(plan, False)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_sfts = K * batch * world
-    value = total_sfts / (elapsed_ms / 1e3)
+    elapsed_ms, value = aggregate_ranks(elapsed_ms, K * batch, world, dev)
 
     # roofline of the gather (resampling) and of the dominant stage
     peaks, peak_kind = measured_peaks()
