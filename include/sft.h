@@ -142,6 +142,36 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
 sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                              int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);
 
+/*
+ * Batches: the transforms of n signals, each with its own plan, with one kernel launch per stage
+ * for the whole batch (SURVEY's batched pattern; Algorithm 1 is unchanged per signal).  Plans may
+ * differ in N, s and moduli but must share precision, input type and kappa, and each plan may
+ * appear once (its scratch serves one signal).  The batch keeps device copies of the plans'
+ * records, so plans must outlive the batch and must not be executed on their own while an
+ * execution of the batch is in flight.
+ */
+typedef struct sft_batch_s* sft_batch_t;
+
+sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n);
+
+/*
+ * One execution: f_devs[i] is signal i's input (N_i elements of the shared input type); its
+ * results go to out_freqs_devs[i][0..s_i), out_coefs_devs[i][0..s_i) (complex128) and
+ * out_count_devs[i][0], as for sft_execute.  All five arrays are host arrays of n device pointers;
+ * they are copied at the call.  Executions of one batch must not overlap on the GPU.
+ */
+sft_status sft_batch_execute(sft_batch_t batch, const void* const* f_devs,
+                             int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
+                             int32_t* const* out_count_devs, void* stream);
+
+sft_status sft_batch_destroy(sft_batch_t batch);
+
+/* Per-stage timing and launch count of a batch, as sft_plan_profile / _read / _launches. */
+sft_status sft_batch_profile(sft_batch_t batch, int32_t enable);
+sft_status sft_batch_profile_read(sft_batch_t batch, double* stage_ms, int32_t* n_executions);
+int64_t sft_batch_launches(sft_batch_t batch);
+size_t sft_batch_device_bytes(sft_batch_t batch);
+
 /* Release every device and host resource of the plan (NULL is a no-op).  The caller must ensure
  * no execution of the plan is still running on the GPU. */
 sft_status sft_plan_destroy(sft_plan_t plan);
@@ -194,7 +224,8 @@ int64_t sft_plan_launches(sft_plan_t plan);
  * on complex64 vectors (interleaved float re,im, 8-byte aligned, caller-owned), any length
  * 2 <= n <= 8191 (prime or not), in FP32, on `stream`.
  *
- * The kernel's tables (chirp, filter spectrum, FFT twiddles) live in one fixed 320 KiB array in
+ * The kernel's tables (chirp, filter spectrum, FFT twiddles) and its launch record live in one
+ * fixed 324 KiB array in
  * device memory that the library declares statically: every GPU that loads the library holds it
  * until the process exits, and nothing is allocated at any call.  The first call on a device looks
  * up that array's address and builds the tables for n on `stream`; a later call with another n

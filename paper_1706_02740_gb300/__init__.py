@@ -70,6 +70,16 @@ EXPORTS = {
     "sft_plan_launches": (ctypes.c_int64, [ctypes.c_void_p]),
     "sft_dft_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "sft_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32]),
+    "sft_batch_execute": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_void_p)] * 4
+                          + [ctypes.c_void_p]),
+    "sft_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sft_batch_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "sft_batch_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int32)]),
+    "sft_batch_launches": (ctypes.c_int64, [ctypes.c_void_p]),
+    "sft_batch_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "sft_choose_moduli": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_int64),
@@ -208,6 +218,67 @@ def sft_dft_noalloc(n: int, batch: int, in_dev: int, out_dev: int, stream: int =
     """Batched length-n DFT (1/n normalised) of complex64 vectors; allocates no device memory
     (its tables live in a fixed static device array of the library)."""
     _check(load().sft_dft_noalloc(int(n), int(batch), in_dev, out_dev, stream))
+
+
+class Batch:
+    """Owns an sft_batch_t over a list of Plans (kept alive by this object)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(load().sft_batch_create(ctypes.byref(h), arr, len(self.plans)))
+        self.handle = h.value
+
+    def destroy(self):
+        if self.handle:
+            load().sft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def execute(self, f_ptrs, w_ptrs, c_ptrs, n_ptrs, stream: int = 0):
+        n = len(self.plans)
+        arrs = [(ctypes.c_void_p * n)(*[int(x) for x in ptrs])
+                for ptrs in (f_ptrs, w_ptrs, c_ptrs, n_ptrs)]
+        _check(load().sft_batch_execute(self.handle, *arrs, stream))
+
+    def profile(self, enable: bool = True):
+        _check(load().sft_batch_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        arr = (ctypes.c_double * len(STAGES))()
+        n = ctypes.c_int32()
+        _check(load().sft_batch_profile_read(self.handle, arr, ctypes.byref(n)))
+        return dict(zip(STAGES, list(arr))), n.value
+
+    @property
+    def launches(self) -> int:
+        return int(load().sft_batch_launches(self.handle))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().sft_batch_device_bytes(self.handle))
+
+
+def execute_batch_torch(batch: Batch, fs, stream=None):
+    """Run a batch on CUDA tensors fs (one per plan); returns lists of device result tensors."""
+    import torch
+    outs = []
+    for p, f in zip(batch.plans, fs):
+        s = p.info()["s"]
+        outs.append((torch.empty(s, dtype=torch.int64, device=f.device),
+                     torch.empty(s, dtype=torch.complex128, device=f.device),
+                     torch.empty(1, dtype=torch.int32, device=f.device)))
+    st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
+    batch.execute([f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs],
+                  [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs],
+                  st.cuda_stream)
+    return outs
 
 
 def sft_plan_launches(plan: Plan) -> int:

@@ -15,6 +15,110 @@ thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// Blocks of each stage for one signal (matches the kernels' block shapes).
+int signal_blocks(const DevPlan& d, int kind) {
+  switch (kind) {
+    case kStOne: return 1;
+    case kStResample: {
+      const int t = (d.kappa == 4 || d.kappa == 6) ? kResampleThreads : kResampleGenericThreads;
+      return (int)((d.m + t - 1) / t);
+    }
+    case kStBins: return (int)(((int64_t)d.nq * d.Ptot + kBinThreads - 1) / kBinThreads);
+    case kStShift: return d.nq;
+    case kStShiftRank:
+    case kStGlobalRank:
+    case kStFinalRank: return rank_blocks(d, kind);
+    case kStReest: return d.prec == SFT_FP32 ? d.nq * d.K * d.nchunk : 0;
+    case kStRefine: return d.prec == SFT_FP32 ? (d.s + kRefineThreads - 1) / kRefineThreads : 0;
+    default:
+      if (kind >= kStBluestein0 && kind < kStCount)
+        return bluestein_blocks(d, 64 << (kind - kStBluestein0));
+      return 0;
+  }
+}
+
+LaunchSet single_launch_set(const DevPlan& d) {
+  LaunchSet ls;
+  for (int k = 0; k < kStCount; ++k) {
+    ls.blocks[k] = signal_blocks(d, k);
+    ls.blk[k] = nullptr;
+  }
+  return ls;
+}
+
+cudaEvent_t* profile_slot(Profiler& pr) {
+  if (pr.on && pr.recorded < kProfileCap) return &pr.events[(size_t)pr.recorded++ * (kStages + 1)];
+  return nullptr;
+}
+
+void profile_release(Profiler& pr) {
+  for (cudaEvent_t e : pr.events) cudaEventDestroy(e);
+  pr.events.clear();
+  pr.on = false;
+  pr.recorded = 0;
+}
+
+sft_status profile_enable(Profiler& pr, int enable) {
+  profile_release(pr);
+  if (!enable) return SFT_OK;
+  const size_t n = (size_t)kProfileCap * (kStages + 1);
+  pr.events.resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (cudaEventCreate(&pr.events[i]) != cudaSuccess) {
+      pr.events.resize(i);
+      profile_release(pr);
+      set_error("cudaEventCreate failed");
+      return SFT_ECUDA;
+    }
+  }
+  pr.on = true;
+  return SFT_OK;
+}
+
+sft_status profile_read(Profiler& pr, double* stage_ms, int32_t* n_executions) {
+  for (int k = 0; k < kStages; ++k) stage_ms[k] = 0.0;
+  *n_executions = pr.recorded;
+  for (int r = 0; r < pr.recorded; ++r) {
+    cudaEvent_t* ev = &pr.events[(size_t)r * (kStages + 1)];
+    for (int k = 0; k < kStages; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("profile events not complete (synchronise the stream first)");
+        return SFT_ECUDA;
+      }
+      stage_ms[k] += ms;
+    }
+  }
+  pr.recorded = 0;
+  return SFT_OK;
+}
+
+// The stages of Algorithm 1 for every signal of bv, in stream order.  ev (optional) receives
+// kStages + 1 events recorded between the stages.
+cudaError_t run_stages(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                       cudaStream_t st, cudaEvent_t* ev, int* launched) {
+  auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], st); };
+  const bool fp64 = d0.prec == SFT_FP64;
+  cudaError_t e = launch_zero(bv, ls, st);
+  ++*launched;
+  mark(0);
+  if (e == cudaSuccess) { e = launch_resample(d0, bv, ls, st); ++*launched; }
+  mark(1);
+  if (e == cudaSuccess) e = launch_bluestein(d0, bv, ls, st, launched);
+  mark(2);
+  if (e == cudaSuccess) { e = launch_identify(d0, bv, ls, st); ++*launched; }
+  mark(3);
+  if (e == cudaSuccess) { e = launch_vote(d0, bv, ls, st); ++*launched; }
+  mark(4);
+  if (e == cudaSuccess) e = launch_select(bv, ls, st, launched);
+  mark(5);
+  if (e == cudaSuccess && !fp64) { e = launch_refine(bv, ls, st); *launched += 2; }
+  if (e == cudaSuccess) e = launch_finalize(bv, ls, st, launched);
+  mark(6);
+  return e;
+}
+
 }  // namespace sft
 
 using sft::Plan;
@@ -22,6 +126,10 @@ using sft::Plan;
 struct sft_plan_s {
   Plan P;
 };
+
+namespace sft {
+Plan* sft_plan_internal(sft_plan_t plan) { return &plan->P; }
+}  // namespace sft
 
 extern "C" {
 
@@ -55,18 +163,9 @@ sft_status sft_plan(sft_plan_t* out, int64_t N, int32_t s, const sft_variant* v,
   return SFT_OK;
 }
 
-namespace {
-void release_events(Plan& P) {
-  for (cudaEvent_t e : P.events) cudaEventDestroy(e);
-  P.events.clear();
-  P.profiling = false;
-  P.recorded = 0;
-}
-}  // namespace
-
 sft_status sft_plan_destroy(sft_plan_t plan) {
   if (!plan) return SFT_OK;
-  release_events(plan->P);
+  sft::profile_release(plan->P.prof);
   sft::free_plan(&plan->P);
   delete plan;
   return SFT_OK;
@@ -109,38 +208,26 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
   const bool any = out_freqs_dev || out_coefs_dev || out_count_dev;
   const bool all = out_freqs_dev && out_coefs_dev && out_count_dev;
   if (any && !all) { sft::set_error("outputs must be all NULL or all non-NULL"); return SFT_EINVAL; }
-  sft::DevPlan d = plan->P.d;
+  Plan& P = plan->P;
+  const sft::DevPlan& d = P.d;
   const uintptr_t fa = (uintptr_t)f_dev;
   if (fa % (d.input == SFT_IN_C64 ? 8 : 16) != 0) {
     sft::set_error("f is not aligned to its element size");
     return SFT_EINVAL;
   }
-  d.aligned16 = (fa % 16) == 0;
-  cudaStream_t st = (cudaStream_t)stream;
-  double2* oc = reinterpret_cast<double2*>(out_coefs_dev);
-  Plan& P = plan->P;
-  cudaEvent_t* ev = nullptr;
-  if (P.profiling && P.recorded < sft::kProfileCap)
-    ev = &P.events[(size_t)P.recorded++ * (sft::kStages + 1)];
-  auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], st); };
-  const bool fp64 = d.prec == SFT_FP64;
-  cudaError_t e = cudaMemsetAsync(d.counters, 0, (size_t)(d.nq + 4) * 4, st);
-  mark(0);
-  if (e == cudaSuccess) e = sft::launch_resample(d, f_dev, st);
-  mark(1);
-  if (e == cudaSuccess) e = sft::launch_bluestein(d, st);
-  mark(2);
-  if (e == cudaSuccess) e = sft::launch_identify(d, st);
-  mark(3);
-  if (e == cudaSuccess) e = sft::launch_vote(d, st);
-  mark(4);
-  if (e == cudaSuccess) e = sft::launch_select(d, out_count_dev, st);
-  mark(5);
-  if (e == cudaSuccess && !fp64) e = sft::launch_refine(d, st);
-  if (e == cudaSuccess) e = sft::launch_finalize(d, out_freqs_dev, oc, st);
-  mark(6);
-  P.launches += 4 + sft::select_launches(d) + (fp64 ? 0 : sft::refine_launches(d)) +
-                (out_freqs_dev ? sft::finalize_launches(d) : 0);
+  sft::BatchView bv;
+  memset(&bv, 0, sizeof(bv));
+  bv.plans = P.d_dev;
+  bv.n = 1;
+  bv.f0 = f_dev;
+  bv.out_w0 = out_freqs_dev;
+  bv.out_c0 = reinterpret_cast<double2*>(out_coefs_dev);
+  bv.out_n0 = out_count_dev;
+  sft::LaunchSet ls = sft::single_launch_set(d);
+  int launched = 0;
+  cudaError_t e = sft::run_stages(d, bv, ls, (cudaStream_t)stream, sft::profile_slot(P.prof),
+                                  &launched);
+  P.launches += launched;
   if (e != cudaSuccess) {
     sft::set_error(std::string("CUDA launch failed: ") + cudaGetErrorString(e));
     return SFT_ECUDA;
@@ -150,42 +237,12 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
 
 sft_status sft_plan_profile(sft_plan_t plan, int32_t enable) {
   if (!plan) { sft::set_error("plan is NULL"); return SFT_EINVAL; }
-  Plan& P = plan->P;
-  release_events(P);
-  if (!enable) return SFT_OK;
-  const size_t n = (size_t)sft::kProfileCap * (sft::kStages + 1);
-  P.events.resize(n);
-  for (size_t i = 0; i < n; ++i) {
-    if (cudaEventCreate(&P.events[i]) != cudaSuccess) {
-      P.events.resize(i);
-      release_events(P);
-      sft::set_error("cudaEventCreate failed");
-      return SFT_ECUDA;
-    }
-  }
-  P.profiling = true;
-  return SFT_OK;
+  return sft::profile_enable(plan->P.prof, enable);
 }
 
 sft_status sft_plan_profile_read(sft_plan_t plan, double* stage_ms, int32_t* n_executions) {
   if (!plan || !stage_ms || !n_executions) { sft::set_error("NULL argument"); return SFT_EINVAL; }
-  Plan& P = plan->P;
-  for (int k = 0; k < sft::kStages; ++k) stage_ms[k] = 0.0;
-  *n_executions = P.recorded;
-  for (int r = 0; r < P.recorded; ++r) {
-    cudaEvent_t* ev = &P.events[(size_t)r * (sft::kStages + 1)];
-    for (int k = 0; k < sft::kStages; ++k) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) {
-        cudaGetLastError();
-        sft::set_error("profile events not complete (synchronise the stream first)");
-        return SFT_ECUDA;
-      }
-      stage_ms[k] += ms;
-    }
-  }
-  P.recorded = 0;
-  return SFT_OK;
+  return sft::profile_read(plan->P.prof, stage_ms, n_executions);
 }
 
 int64_t sft_plan_launches(sft_plan_t plan) { return plan ? plan->P.launches : 0; }

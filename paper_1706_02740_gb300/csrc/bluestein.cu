@@ -154,22 +154,24 @@ struct FFTPasses<C, M, M, TPT> {
 template <typename R, int M>
 __global__ void __launch_bounds__((M / 16) > 256 ? (M / 16) : 256,
                                   (sizeof(R) == 4 && M <= 8192) ? 2 : 1)
-bluestein_kernel(DevPlan d) {
+bluestein_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   constexpr int TPT = M / 16;                      // threads per transform
   constexpr int G = (M >= 4096) ? 1 : 4096 / M;    // transforms per CTA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int g = threadIdx.x / TPT;
   const int lt = threadIdx.x - g * TPT;
-  const int64_t per_q = (int64_t)d.K * d.nsub;
-  const int64_t total = per_q * d.nq;
-  const int64_t tid = (int64_t)blockIdx.x * G + g;
+  const int per_q = d.K * d.nsub;
+  const int total = per_q * d.nq;
+  const int tid = lb * G + g;
   const bool active = tid < total;
   int qi = 0, j = 0, sub = 0;
   if (active) {
-    qi = (int)(tid / per_q);
-    const int rem = (int)(tid - (int64_t)qi * per_q);
+    qi = tid / per_q;
+    const int rem = tid - qi * per_q;
     j = rem / d.nsub;
     sub = rem - j * d.nsub;
   }
@@ -193,43 +195,55 @@ bluestein_kernel(DevPlan d) {
     for (int c = lt; c < p; c += TPT) out[c] = cmul(cconj(s[pad16(c)]), __ldg(chirp + c));
 }
 
+template <int M> constexpr int log2_of() { return M <= 1 ? 0 : 1 + log2_of<M / 2>(); }
+
 template <typename R, int M>
-cudaError_t launch_M(const DevPlan& d, cudaStream_t st) {
+cudaError_t launch_M(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
   using C = typename Cx<R>::T;
   constexpr int G = (M >= 4096) ? 1 : 4096 / M;
   constexpr int threads = (M / 16) * G;
+  const unsigned grid = (unsigned)ls.blocks[kStBluestein0 + log2_of<M>() - 6];
+  if (grid == 0) return cudaSuccess;
   const size_t smem = (size_t)G * padded_len<M>() * sizeof(C);
   cudaError_t e = cudaFuncSetAttribute(bluestein_kernel<R, M>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t total = (int64_t)d.K * d.nsub * d.nq;
-  const unsigned grid = (unsigned)((total + G - 1) / G);
-  bluestein_kernel<R, M><<<grid, threads, smem, st>>>(d);
+  BatchView v = bv;
+  v.blk = ls.blk[kStBluestein0 + log2_of<M>() - 6];
+  bluestein_kernel<R, M><<<grid, threads, smem, st>>>(v);
+  if (launched) ++*launched;
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_prec(const DevPlan& d, cudaStream_t st) {
-  switch (d.fftM) {
-    case 64: return launch_M<R, 64>(d, st);
-    case 128: return launch_M<R, 128>(d, st);
-    case 256: return launch_M<R, 256>(d, st);
-    case 512: return launch_M<R, 512>(d, st);
-    case 1024: return launch_M<R, 1024>(d, st);
-    case 2048: return launch_M<R, 2048>(d, st);
-    case 4096: return launch_M<R, 4096>(d, st);
-    case 8192: return launch_M<R, 8192>(d, st);
-    case 16384:
-      if constexpr (sizeof(R) == 4) return launch_M<R, 16384>(d, st);
-      return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_prec(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = launch_M<R, 64>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 128>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 256>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 512>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 1024>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 2048>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 4096>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 8192>(bv, ls, st, launched);
+  if constexpr (sizeof(R) == 4)
+    if (e == cudaSuccess) e = launch_M<R, 16384>(bv, ls, st, launched);
+  return e;
 }
 
 }  // namespace
 
-cudaError_t launch_bluestein(const DevPlan& d, cudaStream_t st) {
-  return d.prec == SFT_FP32 ? launch_prec<float>(d, st) : launch_prec<double>(d, st);
+cudaError_t launch_bluestein(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                             cudaStream_t st, int* launched) {
+  return d0.prec == SFT_FP32 ? launch_prec<float>(bv, ls, st, launched)
+                             : launch_prec<double>(bv, ls, st, launched);
+}
+
+int bluestein_blocks(const DevPlan& d, int M) {
+  if (d.fftM != M) return 0;
+  const int G = (M >= 4096) ? 1 : 4096 / M;
+  const int total = d.nq * d.K * d.nsub;
+  return (total + G - 1) / G;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -246,14 +260,18 @@ namespace {
 constexpr int kNoAllocMaxN = 8191;           // longest transform: 2n - 1 <= 16384
 constexpr int kNoAllocMaxM = 16384;
 constexpr int kNoAllocChirp = 8192;
-constexpr size_t kNoAllocElems = (size_t)kNoAllocChirp + 2 * (size_t)kNoAllocMaxM;
+constexpr size_t kNoAllocHead = 4096;        // the launch's plan record
+static_assert(sizeof(DevPlan) <= kNoAllocHead, "plan record must fit the head of the array");
+constexpr size_t kNoAllocBytes =
+    kNoAllocHead + sizeof(float2) * ((size_t)kNoAllocChirp + 2 * (size_t)kNoAllocMaxM);
 constexpr int kMaxDevices = 64;
 
-// chirp [8192] | filter spectrum [16384] | twiddles [16384], complex64: 320 KiB in all
-static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocElems];
+// plan record [4 KiB] | chirp [8192] | filter spectrum [16384] | twiddles [16384] (complex64):
+// 324 KiB in all
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
-float2* g_noalloc_ptr[kMaxDevices];     // device address of g_noalloc_scratch, per device
+unsigned char* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
 int g_noalloc_n[kMaxDevices];           // length the tables currently hold (0 = none)
 
 // Twiddles e^{-2 pi i m / M}, the chirp w_k = e^{-pi i (k^2 mod 2n) / n} (k < n) and the wrapped
@@ -352,9 +370,10 @@ extern "C" sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_d
       set_error(std::string("sft_dft_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
       return SFT_ECUDA;
     }
-    g_noalloc_ptr[dev] = reinterpret_cast<float2*>(p);
+    g_noalloc_ptr[dev] = reinterpret_cast<unsigned char*>(p);
   }
-  float2* base = g_noalloc_ptr[dev];
+  DevPlan* rec = reinterpret_cast<DevPlan*>(g_noalloc_ptr[dev]);
+  float2* base = reinterpret_cast<float2*>(g_noalloc_ptr[dev] + kNoAllocHead);
   if (g_noalloc_n[dev] != n) {
     e = noalloc_build_any(n, M, base, st);
     if (e != cudaSuccess) {
@@ -381,7 +400,22 @@ extern "C" sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_d
   d.chirp = base;
   d.vhat = base + kNoAllocChirp;
   d.fftw = base + kNoAllocChirp + kNoAllocMaxM;
-  e = launch_prec<float>(d, st);
+  // the record travels to the array's head in stream order (a pageable copy: no allocation)
+  e = cudaMemcpyAsync(rec, &d, sizeof(d), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    set_error(std::string("sft_dft_noalloc: record copy failed: ") + cudaGetErrorString(e));
+    return SFT_ECUDA;
+  }
+  BatchView bv;
+  memset(&bv, 0, sizeof(bv));
+  bv.plans = rec;
+  bv.n = 1;
+  LaunchSet ls;
+  memset(&ls, 0, sizeof(ls));
+  int lg = 0;
+  while ((1 << lg) < M) ++lg;
+  ls.blocks[kStBluestein0 + lg - 6] = bluestein_blocks(d, M);
+  e = launch_prec<float>(bv, ls, st, nullptr);
   if (e != cudaSuccess) {
     set_error(std::string("sft_dft_noalloc: launch failed: ") + cudaGetErrorString(e));
     return SFT_ECUDA;

@@ -98,9 +98,11 @@ __device__ int residue_any(int t, C z0, const C* Zl, int64_t p, const C* twl, in
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) identify_kernel(DevPlan d) {
+__global__ void __launch_bounds__(kBinThreads) identify_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
+  const int64_t gid = (int64_t)lb * kBinThreads + threadIdx.x;
   if (gid >= (int64_t)d.nq * d.Ptot) return;
   int qi, j, b;
   decode_bin(d, gid, qi, j, b);
@@ -138,9 +140,11 @@ __global__ void __launch_bounds__(256) identify_kernel(DevPlan d) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) vote_kernel(DevPlan d) {
+__global__ void __launch_bounds__(kBinThreads) vote_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
+  const int64_t gid = (int64_t)lb * kBinThreads + threadIdx.x;
   if (gid >= (int64_t)d.nq * d.Ptot) return;
   const int64_t w = d.cand[gid];
   if (w == kNoFreq) return;
@@ -177,19 +181,25 @@ __global__ void __launch_bounds__(256) vote_kernel(DevPlan d) {
 
 }  // namespace
 
-cudaError_t launch_identify(const DevPlan& d, cudaStream_t st) {
-  const int64_t n = (int64_t)d.nq * d.Ptot;
-  const unsigned grid = (unsigned)((n + 255) / 256);
-  if (d.prec == SFT_FP32) identify_kernel<float><<<grid, 256, 0, st>>>(d);
-  else identify_kernel<double><<<grid, 256, 0, st>>>(d);
+cudaError_t launch_identify(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                            cudaStream_t st) {
+  const unsigned grid = (unsigned)ls.blocks[kStBins];
+  if (grid == 0) return cudaSuccess;
+  BatchView v = bv;
+  v.blk = ls.blk[kStBins];
+  if (d0.prec == SFT_FP32) identify_kernel<float><<<grid, kBinThreads, 0, st>>>(v);
+  else identify_kernel<double><<<grid, kBinThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 
-cudaError_t launch_vote(const DevPlan& d, cudaStream_t st) {
-  const int64_t n = (int64_t)d.nq * d.Ptot;
-  const unsigned grid = (unsigned)((n + 255) / 256);
-  if (d.prec == SFT_FP32) vote_kernel<float><<<grid, 256, 0, st>>>(d);
-  else vote_kernel<double><<<grid, 256, 0, st>>>(d);
+cudaError_t launch_vote(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                        cudaStream_t st) {
+  const unsigned grid = (unsigned)ls.blocks[kStBins];
+  if (grid == 0) return cudaSuccess;
+  BatchView v = bv;
+  v.blk = ls.blk[kStBins];
+  if (d0.prec == SFT_FP32) vote_kernel<float><<<grid, kBinThreads, 0, st>>>(v);
+  else vote_kernel<double><<<grid, kBinThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 

@@ -345,6 +345,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   const size_t o_pool = soff;    soff = align256(soff + (size_t)nq * s * sizeof(Pooled));
   const size_t o_win = soff;     soff = align256(soff + (size_t)s * sizeof(Pooled));
   const size_t o_ybuf = soff;    soff = align256(soff + (size_t)d.nchunk * s * K * sizeof(double2));
+  const size_t o_self = soff;    soff = align256(soff + sizeof(DevPlan));
   const size_t total = soff;
 
   char* base = nullptr;
@@ -373,6 +374,13 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   d.pool = reinterpret_cast<Pooled*>(base + o_pool);
   d.winners = reinterpret_cast<Pooled*>(base + o_win);
   d.ybuf = reinterpret_cast<double2*>(base + o_ybuf);
+  P->d_dev = reinterpret_cast<DevPlan*>(base + o_self);
+  e = cudaMemcpy(P->d_dev, &d, sizeof(DevPlan), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_error(std::string("copy of the plan record failed: ") + cudaGetErrorString(e));
+    free_plan(P);
+    return SFT_ECUDA;
+  }
   P->device_bytes = total;
   P->alpha = v->alpha; P->beta = v->beta; P->seed = v->seed;
   P->shifts = shifts; P->primes = primes; P->small = small;

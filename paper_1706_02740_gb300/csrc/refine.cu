@@ -37,15 +37,18 @@ __device__ __forceinline__ int mod_p32(int64_t w, int p) {
   return r < 0 ? r + p : r;
 }
 
-__global__ void __launch_bounds__(kReChunk) reestimate_kernel(DevPlan d) {
+__global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
   __shared__ float2 S[kReChunk];
   __shared__ int list_r[kReChunk];
   __shared__ int list_b[kReChunk];
   __shared__ int list_n;
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int n = d.counters[d.nq + 2];
-  const int qi = blockIdx.x / d.K;
-  const int jj = blockIdx.x - qi * d.K;
-  const int c = blockIdx.y;
+  const int qk = lb / d.nchunk;
+  const int c = lb - qk * d.nchunk;
+  const int qi = qk / d.K;
+  const int jj = qk - qi * d.K;
   const int p = d.p[jj];
   const int k0 = c * kReChunk;
   const int klen = max(0, min(kReChunk, p - k0));
@@ -94,9 +97,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // Refined coefficient of winner r, written back into winners[r].
-__global__ void __launch_bounds__(64) refine_values_kernel(DevPlan d) {
+__global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView bv) {
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int n = d.counters[d.nq + 2];
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = lb * kRefineThreads + threadIdx.x;
   if (r >= n) return;
   Pooled pw = d.winners[r];
   double re[kMaxK], im[kMaxK];
@@ -132,11 +137,12 @@ __global__ void __launch_bounds__(64) refine_values_kernel(DevPlan d) {
 
 }  // namespace
 
-int refine_launches(const DevPlan&) { return 2; }
-
-cudaError_t launch_refine(const DevPlan& d, cudaStream_t st) {
-  reestimate_kernel<<<dim3(d.nq * d.K, d.nchunk), kReChunk, 0, st>>>(d);
-  refine_values_kernel<<<(unsigned)((d.s + 63) / 64), 64, 0, st>>>(d);
+cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t st) {
+  BatchView v = bv;
+  v.blk = ls.blk[kStReest];
+  reestimate_kernel<<<ls.blocks[kStReest], kReChunk, 0, st>>>(v);
+  v.blk = ls.blk[kStRefine];
+  refine_values_kernel<<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 

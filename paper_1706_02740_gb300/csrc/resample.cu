@@ -105,7 +105,7 @@ __device__ __forceinline__ void fetch_window(const DevPlan& d, const IN* f, int6
   constexpr int W = 2 * KAPPA + 1;
   const int64_t N = d.N;
   if constexpr (sizeof(IN) == 8) {
-    if (d.aligned16 && jp >= KAPPA && jp + KAPPA + 2 <= N) {
+    if ((reinterpret_cast<uintptr_t>(f) & 15) == 0 && jp >= KAPPA && jp + KAPPA + 2 <= N) {
       const int64_t start = jp - KAPPA;
       const int64_t base = start & ~int64_t(1);
       const float4* v = reinterpret_cast<const float4*>(f + base);
@@ -142,11 +142,15 @@ __device__ __forceinline__ void fetch_window(const DevPlan& d, const IN* f, int6
 }
 
 template <int KAPPA, typename R, typename IN>
-__global__ void __launch_bounds__(256) resample_kernel(DevPlan d, const IN* __restrict__ f) {
+__global__ void __launch_bounds__(kResampleThreads) resample_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   constexpr int W = 2 * KAPPA + 1;
-  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lb, nb;
+  const int b = batch_signal(bv, lb, nb);
+  const DevPlan& d = bv.plans[b];
+  const int64_t node = (int64_t)lb * kResampleThreads + threadIdx.x;
   if (node >= d.m) return;
+  const IN* __restrict__ f = reinterpret_cast<const IN*>(batch_f(bv, b));
   int j, k1;
   NodeGeom g;
   decode_node(d, node, j, k1, g);
@@ -165,21 +169,27 @@ __global__ void __launch_bounds__(256) resample_kernel(DevPlan d, const IN* __re
 
   const C* T = reinterpret_cast<const C*>(d.Ttab);
   C* out = reinterpret_cast<C*>(d.samples);
-  for (int qi = 0; qi < d.nq; ++qi) {
+  const int nq = d.nq;
+  const int64_t m = d.m;
+  for (int qi = 0; qi < nq; ++qi) {
     C acc = czero<C>();
     const C* Tq = T + qi * W;
 #pragma unroll
     for (int i = 0; i < W; ++i) acc = cadd(acc, cmul(win[i], __ldg(Tq + i)));
-    out[(int64_t)qi * d.m + node] = cmul(acc, node_phase(d, qi, v0, g));
+    out[(int64_t)qi * m + node] = cmul(acc, node_phase(d, qi, v0, g));
   }
 }
 
 // Any window half-width up to kMaxKappa (theorem-parameter mode): scalar loads, runtime loops.
 template <typename R, typename IN>
-__global__ void __launch_bounds__(128) resample_kernel_generic(DevPlan d, const IN* __restrict__ f) {
+__global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_generic(BatchView bv) {
   using C = typename Cx<R>::T;
-  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lb, nb;
+  const int b = batch_signal(bv, lb, nb);
+  const DevPlan& d = bv.plans[b];
+  const int64_t node = (int64_t)lb * kResampleGenericThreads + threadIdx.x;
   if (node >= d.m) return;
+  const IN* __restrict__ f = reinterpret_cast<const IN*>(batch_f(bv, b));
   int j, k1;
   NodeGeom g;
   decode_node(d, node, j, k1, g);
@@ -203,29 +213,27 @@ __global__ void __launch_bounds__(128) resample_kernel_generic(DevPlan d, const 
 }
 
 template <typename R, typename IN>
-cudaError_t launch_typed(const DevPlan& d, const void* f, cudaStream_t st) {
-  const IN* fin = reinterpret_cast<const IN*>(f);
-  if (d.kappa == 6) {
-    const unsigned grid = (unsigned)((d.m + 255) / 256);
-    resample_kernel<6, R, IN><<<grid, 256, 0, st>>>(d, fin);
-  } else if (d.kappa == 4) {
-    const unsigned grid = (unsigned)((d.m + 255) / 256);
-    resample_kernel<4, R, IN><<<grid, 256, 0, st>>>(d, fin);
-  } else {
-    const unsigned grid = (unsigned)((d.m + 127) / 128);
-    resample_kernel_generic<R, IN><<<grid, 128, 0, st>>>(d, fin);
-  }
+cudaError_t launch_typed(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                         cudaStream_t st) {
+  const unsigned grid = (unsigned)ls.blocks[kStResample];
+  if (grid == 0) return cudaSuccess;
+  BatchView v = bv;
+  v.blk = ls.blk[kStResample];
+  if (d0.kappa == 6) resample_kernel<6, R, IN><<<grid, kResampleThreads, 0, st>>>(v);
+  else if (d0.kappa == 4) resample_kernel<4, R, IN><<<grid, kResampleThreads, 0, st>>>(v);
+  else resample_kernel_generic<R, IN><<<grid, kResampleGenericThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_resample(const DevPlan& d, const void* f, cudaStream_t st) {
-  if (d.prec == SFT_FP32)
-    return d.input == SFT_IN_C64 ? launch_typed<float, float2>(d, f, st)
-                                 : launch_typed<float, double2>(d, f, st);
-  return d.input == SFT_IN_C64 ? launch_typed<double, float2>(d, f, st)
-                               : launch_typed<double, double2>(d, f, st);
+cudaError_t launch_resample(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                            cudaStream_t st) {
+  if (d0.prec == SFT_FP32)
+    return d0.input == SFT_IN_C64 ? launch_typed<float, float2>(d0, bv, ls, st)
+                                  : launch_typed<float, double2>(d0, bv, ls, st);
+  return d0.input == SFT_IN_C64 ? launch_typed<double, float2>(d0, bv, ls, st)
+                                : launch_typed<double, double2>(d0, bv, ls, st);
 }
 
 }  // namespace sft

@@ -57,8 +57,10 @@ __device__ __forceinline__ uint64_t pkey(const Pooled& p) {
   return mag_key(p.cre * p.cre + p.cim * p.cim);
 }
 
-__global__ void __launch_bounds__(kSortThreads) shift_select(DevPlan d) {
-  const int qi = blockIdx.x;
+__global__ void __launch_bounds__(kSortThreads) shift_select(BatchView bv) {
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
+  const int qi = lb;
   const int n = min(d.counters[qi], d.vcap);
   const Voted* V = d.voted + (int64_t)qi * d.vcap;
   if (n <= d.s) {
@@ -85,14 +87,17 @@ __global__ void __launch_bounds__(kSortThreads) shift_select(DevPlan d) {
   for (int i = threadIdx.x; i < d.s; i += kSortThreads) pool_append(d, V[S[i].ix], qi);
 }
 
-__global__ void __launch_bounds__(kRankThreads) shift_select_rank(DevPlan d) {
+__global__ void __launch_bounds__(kRankThreads) shift_select_rank(BatchView bv) {
   __shared__ uint64_t sm[kRankThreads];
   __shared__ int64_t sw[kRankThreads];
-  const int qi = blockIdx.y;
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
+  const int chunks = nb / d.nq;
+  const int qi = lb / chunks, chunk = lb - qi * chunks;
   const int n = min(d.counters[qi], d.vcap);
   if (n <= kSortCap || n <= d.s) return;
   const Voted* V = d.voted + (int64_t)qi * d.vcap;
-  for (int base = blockIdx.x * kRankThreads; base < n; base += gridDim.x * kRankThreads) {
+  for (int base = chunk * kRankThreads; base < n; base += chunks * kRankThreads) {
     const int i = base + threadIdx.x;
     Voted vi;
     uint64_t mi = 0;
@@ -119,22 +124,26 @@ __global__ void __launch_bounds__(kRankThreads) shift_select_rank(DevPlan d) {
   }
 }
 
-__device__ __forceinline__ void set_count(const DevPlan& d, int n, int32_t* out_n) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ void set_count(const DevPlan& d, int n, int32_t* out_n, int lb) {
+  if (lb == 0 && threadIdx.x == 0) {
     d.counters[d.nq + 2] = min(n, d.s);
     if (out_n) *out_n = min(n, d.s);
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) global_select(DevPlan d, int32_t* out_n) {
+__global__ void __launch_bounds__(kSortThreads) global_select(BatchView bv) {
+  int lb, nb;
+  const int b = batch_signal(bv, lb, nb);
+  const DevPlan& d = bv.plans[b];
+  int32_t* out_n = batch_out_n(bv, b);
   const int n = min(d.counters[d.nq], d.nq * d.s);
   if (n <= d.s) {
-    set_count(d, n, out_n);
+    set_count(d, n, out_n, lb);
     for (int i = threadIdx.x; i < n; i += kSortThreads) d.winners[i] = d.pool[i];
     return;
   }
   if (n > kSortCap) return;
-  set_count(d, n, out_n);
+  set_count(d, n, out_n, lb);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Rec* S = reinterpret_cast<Rec*>(smem_raw);
   const int slots = sort_slots(n);
@@ -154,13 +163,16 @@ __global__ void __launch_bounds__(kSortThreads) global_select(DevPlan d, int32_t
   for (int i = threadIdx.x; i < d.s; i += kSortThreads) d.winners[i] = d.pool[S[i].ix];
 }
 
-__global__ void __launch_bounds__(kRankThreads) global_select_rank(DevPlan d, int32_t* out_n) {
+__global__ void __launch_bounds__(kRankThreads) global_select_rank(BatchView bv) {
   __shared__ uint64_t sm[kRankThreads];
   __shared__ int64_t sw[kRankThreads];
+  int lb, nb;
+  const int b = batch_signal(bv, lb, nb);
+  const DevPlan& d = bv.plans[b];
   const int n = min(d.counters[d.nq], d.nq * d.s);
   if (n <= kSortCap || n <= d.s) return;
-  set_count(d, n, out_n);
-  for (int base = blockIdx.x * kRankThreads; base < n; base += gridDim.x * kRankThreads) {
+  set_count(d, n, batch_out_n(bv, b), lb);
+  for (int base = lb * kRankThreads; base < n; base += nb * kRankThreads) {
     const int i = base + threadIdx.x;
     Pooled pi;
     uint64_t mi = 0;
@@ -187,8 +199,12 @@ __global__ void __launch_bounds__(kRankThreads) global_select_rank(DevPlan d, in
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) finalize_sorted(DevPlan d, int64_t* out_w,
-                                                                double2* out_c) {
+__global__ void __launch_bounds__(kSortThreads) finalize_sorted(BatchView bv) {
+  int lb, nb;
+  const int b = batch_signal(bv, lb, nb);
+  const DevPlan& d = bv.plans[b];
+  int64_t* out_w = batch_out_w(bv, b);
+  double2* out_c = batch_out_c(bv, b);
   const int n = d.counters[d.nq + 2];
   if (n > kSortCap || !out_w) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -218,14 +234,18 @@ __global__ void __launch_bounds__(kSortThreads) finalize_sorted(DevPlan d, int64
   }
 }
 
-__global__ void __launch_bounds__(kRankThreads) finalize_rank(DevPlan d, int64_t* out_w,
-                                                              double2* out_c) {
+__global__ void __launch_bounds__(kRankThreads) finalize_rank(BatchView bv) {
   __shared__ uint64_t sm[kRankThreads];
   __shared__ int64_t sw[kRankThreads];
+  int lb, nb;
+  const int b = batch_signal(bv, lb, nb);
+  const DevPlan& d = bv.plans[b];
+  int64_t* out_w = batch_out_w(bv, b);
+  double2* out_c = batch_out_c(bv, b);
   const int n = d.counters[d.nq + 2];
   if (n <= kSortCap || !out_w) return;
   const int limit = max(n, d.s);
-  for (int base = blockIdx.x * kRankThreads; base < limit; base += gridDim.x * kRankThreads) {
+  for (int base = lb * kRankThreads; base < limit; base += nb * kRankThreads) {
     const int i = base + threadIdx.x;
     Pooled pi;
     uint64_t mi = 0;
@@ -258,45 +278,78 @@ __global__ void __launch_bounds__(kRankThreads) finalize_rank(DevPlan d, int64_t
   }
 }
 
+// Per-signal counters (voted counts, pool count, winner count) start at zero.
+__global__ void __launch_bounds__(64) zero_kernel(BatchView bv) {
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
+  for (int i = threadIdx.x; i < d.nq + 4; i += 64) d.counters[i] = 0;
+}
+
 cudaError_t set_smem(const void* fn) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
 }
 
+BatchView with_blk(const BatchView& bv, const LaunchSet& ls, int kind);
+
 }  // namespace
 
-int select_launches(const DevPlan& d) {
-  return 2 + (d.vcap > kSortCap ? 1 : 0) + ((int64_t)d.nq * d.s > kSortCap ? 1 : 0);
+namespace {
+BatchView with_blk(const BatchView& bv, const LaunchSet& ls, int kind) {
+  BatchView v = bv;
+  v.blk = ls.blk[kind];
+  return v;
+}
+}  // namespace
+
+cudaError_t launch_zero(const BatchView& bv, const LaunchSet& ls, cudaStream_t st) {
+  zero_kernel<<<ls.blocks[kStOne], 64, 0, st>>>(with_blk(bv, ls, kStOne));
+  return cudaGetLastError();
 }
 
-int finalize_launches(const DevPlan& d) { return 1 + (d.s > kSortCap ? 1 : 0); }
-
-cudaError_t launch_select(const DevPlan& d, int32_t* out_n, cudaStream_t st) {
+cudaError_t launch_select(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
   cudaError_t e = set_smem((const void*)shift_select);
   if (e == cudaSuccess) e = set_smem((const void*)global_select);
   if (e != cudaSuccess) return e;
-  shift_select<<<d.nq, kSortThreads, kSortSmem, st>>>(d);
-  if (d.vcap > kSortCap) {
-    const int chunks = (int)std::min<int64_t>((d.vcap + kRankThreads - 1) / kRankThreads, 64);
-    shift_select_rank<<<dim3(chunks, d.nq), kRankThreads, 0, st>>>(d);
+  shift_select<<<ls.blocks[kStShift], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStShift));
+  ++*launched;
+  if (ls.blocks[kStShiftRank] > 0) {
+    shift_select_rank<<<ls.blocks[kStShiftRank], kRankThreads, 0, st>>>(
+        with_blk(bv, ls, kStShiftRank));
+    ++*launched;
   }
-  global_select<<<1, kSortThreads, kSortSmem, st>>>(d, out_n);
-  if ((int64_t)d.nq * d.s > kSortCap) {
-    const int64_t lim = (int64_t)d.nq * d.s;
-    const int g2 = (int)std::min<int64_t>((lim + kRankThreads - 1) / kRankThreads, 256);
-    global_select_rank<<<g2, kRankThreads, 0, st>>>(d, out_n);
+  global_select<<<ls.blocks[kStOne], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStOne));
+  ++*launched;
+  if (ls.blocks[kStGlobalRank] > 0) {
+    global_select_rank<<<ls.blocks[kStGlobalRank], kRankThreads, 0, st>>>(
+        with_blk(bv, ls, kStGlobalRank));
+    ++*launched;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const DevPlan& d, int64_t* out_w, double2* out_c, cudaStream_t st) {
+cudaError_t launch_finalize(const BatchView& bv, const LaunchSet& ls, cudaStream_t st,
+                            int* launched) {
   cudaError_t e = set_smem((const void*)finalize_sorted);
   if (e != cudaSuccess) return e;
-  finalize_sorted<<<1, kSortThreads, kSortSmem, st>>>(d, out_w, out_c);
-  if (d.s > kSortCap) {
-    const int g = (int)std::min<int64_t>((d.s + kRankThreads - 1) / kRankThreads, 256);
-    finalize_rank<<<g, kRankThreads, 0, st>>>(d, out_w, out_c);
+  finalize_sorted<<<ls.blocks[kStOne], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStOne));
+  ++*launched;
+  if (ls.blocks[kStFinalRank] > 0) {
+    finalize_rank<<<ls.blocks[kStFinalRank], kRankThreads, 0, st>>>(with_blk(bv, ls, kStFinalRank));
+    ++*launched;
   }
   return cudaGetLastError();
+}
+
+int rank_blocks(const DevPlan& d, int kind) {
+  if (kind == kStShiftRank)
+    return d.vcap > kSortCap ? (int)std::min<int64_t>((d.vcap + kRankThreads - 1) / kRankThreads, 64) * d.nq : 0;
+  if (kind == kStGlobalRank) {
+    const int64_t lim = (int64_t)d.nq * d.s;
+    return lim > kSortCap ? (int)std::min<int64_t>((lim + kRankThreads - 1) / kRankThreads, 256) : 0;
+  }
+  if (kind == kStFinalRank)
+    return d.s > kSortCap ? (int)std::min<int64_t>((d.s + kRankThreads - 1) / kRankThreads, 256) : 0;
+  return 0;
 }
 
 }  // namespace sft

@@ -65,7 +65,6 @@ struct DevPlan {
   int32_t Nqt[kMaxT], Nrt[kMaxT];
   int32_t nchunk;             // sample chunks of the re-estimation (ceil(pmax / kReChunk))
   int32_t vcap;               // capacity of each shift's voted list
-  int32_t aligned16;          // f is 16-byte aligned (set per execution)
   // device tables
   const void* Ttab;           // [nq][2 kappa + 1] exp(-2 pi i (q i mod N) / N)   (prec type)
   const void* chirp;          // [K][pmax] exp(-pi i (n^2 mod 2p) / p)           (prec type)
@@ -89,16 +88,102 @@ struct DevPlan {
 };
 
 constexpr int kReChunk = 256;   // samples per re-estimation CTA
+constexpr int kResampleThreads = 256;
+constexpr int kResampleGenericThreads = 128;
+constexpr int kBinThreads = 256;       // identify / vote: one thread per bin
+constexpr int kRefineThreads = 64;
+
+// ---------------------------------------------------------------------------------------------
+// Batches.  One launch of a stage covers every signal of a batch; each signal has its own plan
+// (tables and scratch).  Blocks never straddle signals: blk[b] .. blk[b+1] are signal b's blocks
+// in this launch (a signal may have none).  A single signal needs no prefix (blk == nullptr).
+// ---------------------------------------------------------------------------------------------
+struct BatchView {
+  const DevPlan* plans;       // [n] device copies of the plans
+  int32_t n;
+  const int32_t* blk;         // [n + 1] block prefix of this launch, or nullptr when n == 1
+  const void* const* f;       // [n] input pointers (device array), or nullptr: f0
+  int64_t* const* out_w;      // [n] or nullptr: out_w0
+  double2* const* out_c;      // [n] or nullptr: out_c0
+  int32_t* const* out_n;      // [n] or nullptr: out_n0
+  const void* f0;
+  int64_t* out_w0;
+  double2* out_c0;
+  int32_t* out_n0;
+};
+
+#ifdef __CUDACC__
+// Signal of this block, its block index within the signal and the signal's block count.
+__device__ __forceinline__ int batch_signal(const BatchView& bv, int& lb, int& nb) {
+  if (!bv.blk) {
+    lb = blockIdx.x;
+    nb = gridDim.x;
+    return 0;
+  }
+  int lo = 0, hi = bv.n;
+  const int x = blockIdx.x;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (bv.blk[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  lb = x - bv.blk[lo];
+  nb = bv.blk[lo + 1] - bv.blk[lo];
+  return lo;
+}
+__device__ __forceinline__ const void* batch_f(const BatchView& bv, int b) {
+  return bv.f ? bv.f[b] : bv.f0;
+}
+__device__ __forceinline__ int64_t* batch_out_w(const BatchView& bv, int b) {
+  return bv.out_w ? bv.out_w[b] : bv.out_w0;
+}
+__device__ __forceinline__ double2* batch_out_c(const BatchView& bv, int b) {
+  return bv.out_c ? bv.out_c[b] : bv.out_c0;
+}
+__device__ __forceinline__ int32_t* batch_out_n(const BatchView& bv, int b) {
+  return bv.out_n ? bv.out_n[b] : bv.out_n0;
+}
+#endif
+
+// Stages whose per-signal block counts a launch set records.
+enum StageKind {
+  kStOne = 0,        // one block per signal (counters, global selection, final order)
+  kStResample,       // nodes / threads per block
+  kStBins,           // shifts * sum p / 256
+  kStShift,          // one block per shift
+  kStShiftRank,      // rank fallback of long voted lists (0 for signals that never need it)
+  kStGlobalRank,     // rank fallback of long pools
+  kStReest,          // shifts * K * chunks
+  kStRefine,         // s / 64
+  kStFinalRank,      // rank fallback of the final order
+  kStBluestein0,     // + log2(M) - 6: one per chirp-convolution length class
+  kStCount = kStBluestein0 + 9
+};
+
+// Host-side description of one execution's launches: total blocks of each stage and the device
+// prefix array (nullptr for a single signal).
+struct LaunchSet {
+  int32_t blocks[kStCount];
+  const int32_t* blk[kStCount];
+};
+
+int bluestein_blocks(const DevPlan& d, int M);   // chirp-convolution blocks of one signal (length M)
+int rank_blocks(const DevPlan& d, int kind);     // blocks of the rank fallbacks (0 when not needed)
 
 constexpr int kStages = 6;
 constexpr int kProfileCap = 4096;
 
+// Per-stage timing with CUDA events (plans and batches).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> events;   // kProfileCap * (kStages + 1)
+  int recorded = 0;
+};
+
 struct Plan {
   DevPlan d;
-  // per-stage timing (sft_plan_profile): kStages + 1 events per recorded execution
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;
-  int recorded = 0;
+  DevPlan* d_dev = nullptr;   // device copy of d (inside the plan's allocation)
+  Profiler prof;
   int64_t launches = 0;
   double alpha = 0, beta = 0;
   uint64_t seed = 0;
@@ -109,18 +194,33 @@ struct Plan {
   int device = 0;
 };
 
-// Kernel launch wrappers (each returns cudaGetLastError()).
-cudaError_t launch_resample(const DevPlan& d, const void* f, cudaStream_t st);
-cudaError_t launch_bluestein(const DevPlan& d, cudaStream_t st);
-cudaError_t launch_identify(const DevPlan& d, cudaStream_t st);
-cudaError_t launch_vote(const DevPlan& d, cudaStream_t st);
-cudaError_t launch_select(const DevPlan& d, int32_t* out_n, cudaStream_t st);
-cudaError_t launch_refine(const DevPlan& d, cudaStream_t st);
-cudaError_t launch_finalize(const DevPlan& d, int64_t* out_w, double2* out_c, cudaStream_t st);
-// kernels each stage launches for this plan (host-side count, matches the launch wrappers)
-int select_launches(const DevPlan& d);
-int refine_launches(const DevPlan& d);
-int finalize_launches(const DevPlan& d);
+// Kernel launch wrappers: one launch per stage for all signals of bv (each returns
+// cudaGetLastError()).  `d0` is the first signal's plan (batches share precision, input type and
+// window half-width; the chirp-convolution launch is repeated per length class present).
+cudaError_t launch_zero(const BatchView& bv, const LaunchSet& ls, cudaStream_t st);
+cudaError_t launch_resample(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                            cudaStream_t st);
+cudaError_t launch_bluestein(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                             cudaStream_t st, int* launched);
+cudaError_t launch_identify(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                            cudaStream_t st);
+cudaError_t launch_vote(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                        cudaStream_t st);
+cudaError_t launch_select(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched);
+cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t st);
+cudaError_t launch_finalize(const BatchView& bv, const LaunchSet& ls, cudaStream_t st,
+                            int* launched);
+
+// Engine (api.cu): the stage sequence for one signal or a batch.
+int signal_blocks(const DevPlan& d, int kind);
+LaunchSet single_launch_set(const DevPlan& d);
+cudaError_t run_stages(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                       cudaStream_t st, cudaEvent_t* ev, int* launched);
+
+cudaEvent_t* profile_slot(Profiler& pr);
+sft_status profile_enable(Profiler& pr, int enable);
+sft_status profile_read(Profiler& pr, double* stage_ms, int32_t* n_executions);
+void profile_release(Profiler& pr);
 
 // Host plan construction (plan.cpp).
 sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
@@ -132,5 +232,8 @@ sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t s
 
 // Thread-local error text.
 void set_error(const std::string& msg);
+
+// The plan behind a C handle (api.cu).
+Plan* sft_plan_internal(sft_plan_t plan);
 
 }  // namespace sft

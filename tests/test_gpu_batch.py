@@ -1,0 +1,94 @@
+"""Batched execution: one launch per stage for many signals, each with its own plan.
+
+Each signal's result from a batch must equal, bit for bit, the result of executing its plan alone
+(the kernels do the same arithmetic per signal; selections do not depend on the order in which
+atomics filled the lists), and agree with the oracle on a sample of the batch."""
+import numpy as np
+import pytest
+
+import paper_1706_02740_gb300 as sft
+from oracle import dsft as O
+from synth.signals import as_complex64, make_signal, upcast
+from tests import gpu_parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1706_02740_gb300 import build
+    build.build()
+    sft.load()
+
+
+SHAPES = [(2 ** 14, 6), (65521, 12), (3 ** 10, 20), (2 ** 17, 40), (100003, 9), (2 ** 15 + 3, 30),
+          (2 ** 16, 8)]
+
+
+def _signals(shapes, seed0, snr=30.0):
+    return [make_signal(N, s, seed0 + i, "unit" if i % 2 else "loguniform", snr)
+            for i, (N, s) in enumerate(shapes)]
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_heterogeneous_batch_equals_single_executions(prec):
+    import torch
+    sigs = _signals(SHAPES, 500)
+    plans = [sft.sft_plan(N, s, sft.sft_variant_init(precision=prec, K=5, c_p=6.0, seed=i))
+             for i, (N, s) in enumerate(SHAPES)]
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in sigs]
+    singles = []
+    for p, f in zip(plans, fs):
+        w, c, n = sft.execute_torch(p, f)
+        torch.cuda.synchronize()
+        singles.append((w.cpu().numpy(), c.cpu().numpy(), int(n.item())))
+    batch = sft.Batch(plans)
+    for rep in range(3):                     # repeated executions through the staging ring
+        outs = sft.execute_batch_torch(batch, fs)
+        torch.cuda.synchronize()
+        for (w, c, n), (sw, sc, sn) in zip(outs, singles):
+            assert int(n.item()) == sn
+            assert np.array_equal(w.cpu().numpy(), sw)
+            assert np.array_equal(c.cpu().numpy(), sc)
+    # and the oracle on two members
+    for i in (1, 4):
+        N, s = SHAPES[i]
+        info = plans[i].info()
+        res = O.dsft(upcast(as_complex64(sigs[i].f)), U.oracle_plan(info, N, s))
+        w, c, n = singles[i]
+        assert n == len(res.freqs)
+        U.assert_same_output(w[:n], c[:n], res.freqs, res.coefs, 1e-5 if prec == U.FP32 else 1e-11)
+    batch.destroy()
+    for p in plans:
+        p.destroy()
+
+
+def test_batch_of_identical_shapes_with_rotating_inputs():
+    import torch
+    N, s, B = 2 ** 18, 50, 6
+    plans = [sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=4.0, seed=3)) for _ in range(B)]
+    sigs = [make_signal(N, s, 900 + i, "unit", 30.0) for i in range(2 * B)]
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in sigs]
+    batch = sft.Batch(plans)
+    for half in (0, 1):
+        outs = sft.execute_batch_torch(batch, fs[half * B:(half + 1) * B])
+        torch.cuda.synchronize()
+        for i, (w, c, n) in enumerate(outs):
+            g = sigs[half * B + i]
+            got = set(w.cpu().numpy()[: int(n.item())].tolist())
+            assert len(got & set(g.omega.tolist())) >= s - 1
+    batch.destroy()
+
+
+def test_batch_rejects_mixed_variants_and_duplicates():
+    a = sft.sft_plan(2 ** 14, 4, sft.sft_variant_init(precision=0, c_p=8.0))
+    b = sft.sft_plan(2 ** 14, 4, sft.sft_variant_init(precision=1, c_p=8.0))
+    c = sft.sft_plan(2 ** 14, 4, sft.sft_variant_init(kappa=4, c_p=8.0))
+    for plans in ([a, b], [a, c], [a, a]):
+        with pytest.raises(sft.SftError) as e:
+            sft.Batch(plans)
+        assert e.value.status == sft.SFT_EINVAL
+    for p in (a, b, c):
+        p.destroy()
