@@ -4,9 +4,10 @@ workload: N = 2^26, s = 1000, complex64 input, log-uniform magnitudes on [1e-2, 
 complex Gaussian noise at 30 dB SNR.
 
 A step is one pass of the whole hot path (resampling, chirp-convolution DFTs, residues + CRT,
-vote + medians, selections, re-estimation) over one batch of `batch` signals, each a separate
-sft_execute through the C ABI.  Eight distinct 512 MiB inputs rotate so that the windows one SFT
-gathers are not left in the 129 MB L2 by the previous one.
+vote + medians, selections, re-estimation) over one batch of `batch` signals: one
+sft_batch_execute, i.e. one launch per stage for all of them.  Eight distinct 512 MiB inputs
+rotate, so the windows gathered in one step (8 x ~70 MB) far exceed the 129 MB L2 and none is
+left there by the previous step.
 
   python bench.py [--gpus N --steps K --warmup W]          # this library
   python bench.py --impl reference [--steps K --warmup W]  # the CPU oracle on host cores
@@ -46,8 +47,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--s", type=int, default=S_DEFAULT)
-    ap.add_argument("--batch", type=int, default=0, help="SFTs per step (0 = about 50 ms of work)")
+    ap.add_argument("--batch", type=int, default=8, help="SFTs per step (one batched execution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inputs", type=int, default=N_INPUTS,
+                    help="distinct resident inputs that rotate (each N complex64)")
+    ap.add_argument("--timed-only", action="store_true",
+                    help="only the warm-up and timed steps (for profiler launch lists)")
     return ap.parse_args()
 
 
@@ -58,7 +63,7 @@ def workload_config(args, batch):
         "N": args.N, "s": args.s, "kappa": PLAN["kappa"], "K": PLAN["K"], "c_p": PLAN["c_p"],
         "alpha": PLAN["alpha"], "beta": PLAN["beta"], "precision": "fp32 bulk + fp64 refine",
         "batch_per_step": batch,
-        "l2": f"{N_INPUTS} rotating distinct inputs of {args.N * 8 >> 20} MiB (> 129 MB L2)",
+        "l2": f"{args.inputs} rotating distinct inputs of {args.N * 8 >> 20} MiB (> 129 MB L2)",
     }
 
 
@@ -70,16 +75,19 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, off: bool = False):
         self.gpu = gpu_index
         self.lines = []
         self.proc = None
+        self.off = off
 
     def __enter__(self):
+        if self.off:
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "50"], stdout=subprocess.PIPE,
+                 "-i", str(self.gpu), "-lms", "20"], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -138,7 +146,7 @@ def source_digest(*names):
 
 
 def profiled_traffic(kernel_tag, digest):
-    """Per-launch DRAM bytes from the committed ncu summary of this kernel, if it was taken on the
+    """Per-SFT DRAM bytes from the committed ncu summary of this kernel, if it was taken on the
     current source (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     try:
@@ -146,7 +154,7 @@ def profiled_traffic(kernel_tag, digest):
     except OSError:
         return None
     m_src = re.search(r"source_digest:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_tr = re.search(r"dram_bytes_per_sft:\s*([0-9.eE+]+)", text)
     if not (m_src and m_tr) or m_src.group(1) != digest:
         return None
     return float(m_tr.group(1))
@@ -179,7 +187,6 @@ def aggregate_ranks(elapsed_ms, sfts_per_rank, world, device=None):
 # our arm
 # ------------------------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -191,90 +198,98 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     N, s = args.N, args.s
+    B = args.batch
+    n_in = max(1, args.inputs)
     inputs = []
-    for i in range(N_INPUTS):
+    for i in range(n_in):
         f, _, _ = make_device_signal(N, s, 3000 + 100 * rank + i, "loguniform", 30.0, dev)
         inputs.append(f)
     torch.cuda.synchronize()
 
-    v = sft.sft_variant_init(precision=sft.SFT_FP32, kappa=PLAN["kappa"], K=PLAN["K"],
-                             c_p=PLAN["c_p"], alpha=PLAN["alpha"], beta=PLAN["beta"],
-                             seed=PLAN["seed"])
-    plan = sft.sft_plan(N, s, v)
-    info = plan.info()
+    def variant(prec):
+        return sft.sft_variant_init(precision=prec, kappa=PLAN["kappa"], K=PLAN["K"],
+                                    c_p=PLAN["c_p"], alpha=PLAN["alpha"], beta=PLAN["beta"],
+                                    seed=PLAN["seed"])
+    plans = [sft.sft_plan(N, s, variant(sft.SFT_FP32)) for _ in range(B)]
+    info = plans[0].info()
+    batch = sft.Batch(plans)
     stream = torch.cuda.current_stream(dev)
     outs = [(torch.empty(s, dtype=torch.int64, device=dev),
              torch.empty(s, dtype=torch.complex128, device=dev),
-             torch.empty(1, dtype=torch.int32, device=dev)) for _ in range(2)]
+             torch.empty(1, dtype=torch.int32, device=dev)) for _ in range(B)]
+    w_ptrs = [o[0].data_ptr() for o in outs]
+    c_ptrs = [o[1].data_ptr() for o in outs]
+    n_ptrs = [o[2].data_ptr() for o in outs]
 
-    def one(i):
-        o = outs[i & 1]
-        sft.sft_execute(plan, inputs[i % N_INPUTS].data_ptr(), o[0].data_ptr(), o[1].data_ptr(),
-                        o[2].data_ptr(), stream.cuda_stream)
+    def step(k):
+        fs = [inputs[(k * B + i) % n_in].data_ptr() for i in range(B)]
+        batch.execute(fs, w_ptrs, c_ptrs, n_ptrs, stream.cuda_stream)
 
-    # pick the batch so that a step is about 50 ms
-    for i in range(4):
-        one(i)
+    # latency of one request alone (one plan, one SFT at a time)
+    p0 = plans[0]
+    for i in range(0 if args.timed_only else 3):
+        sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0], stream.cuda_stream)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(16):
-        one(i)
-    e1.record()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(0 if args.timed_only else 64)]
+    for i, (a, b) in enumerate(ev):
+        a.record()
+        sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
+                        stream.cuda_stream)
+        b.record()
     torch.cuda.synchronize()
-    est_ms = e0.elapsed_time(e1) / 16
-    batch = args.batch or max(1, int(round(50.0 / max(est_ms, 1e-3))))
+    single = sorted(a.elapsed_time(b) for a, b in ev) or [float("nan")]
 
     for w in range(args.warmup):
-        for i in range(batch):
-            one(i)
+        step(w)
     torch.cuda.synchronize()
 
     K = args.steps
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K * batch)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K * batch)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sft.sft_plan_profile(plan, True)
-    launches0 = sft.sft_plan_launches(plan)
+    batch.profile(True)
+    launches0 = batch.launches
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clocks:
+    with ClockSampler(local_rank, off=args.timed_only) as clocks:
         t0.record()
         for k in range(K):
-            for i in range(batch):
-                idx = k * batch + i
-                starts[idx].record()
-                one(idx)
-                ends[idx].record()
+            starts[k].record()
+            step(k)
+            ends[k].record()
         t1.record()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    launches = sft.sft_plan_launches(plan) - launches0
+    launches = batch.launches - launches0
     elapsed_ms = t0.elapsed_time(t1)
-    lat = sorted(a.elapsed_time(b) for a, b in zip(starts, ends))
-    stage_ms, n_rec = sft.sft_plan_profile_read(plan)
-    sft.sft_plan_profile(plan, False)
-    elapsed_ms, value = aggregate_ranks(elapsed_ms, K * batch, world, dev)
+    step_ms = sorted(a.elapsed_time(b) for a, b in zip(starts, ends))
+    stage_ms, n_rec = batch.profile_read()
+    batch.profile(False)
+    elapsed_ms, value = aggregate_ranks(elapsed_ms, K * B, world, dev)
 
-    # roofline of the gather (resampling) and of the dominant stage
+    # roofline of the gather (resampling) and of the dominant stage, per batched launch
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     per_launch_us = {k: 1e3 * v / max(n_rec, 1) for k, v in stage_ms.items()}
-    gather_bytes = 8 * (2 * info["kappa"] + 1) * info["nodes"]
+    gather_bytes = B * 8 * (2 * info["kappa"] + 1) * info["nodes"]
     rs_s = per_launch_us["resample"] * 1e-6
     digest = source_digest("resample.cu", "cplx.cuh", "sft_internal.h")
     traffic = profiled_traffic("resample_n2p26_s1000", digest)
+    if traffic is not None:
+        traffic *= B           # per batched launch: traffic grows with the SFTs it processes
     roof_gather = {"kernel": "resample", "bound": "hbm", "achieved": gather_bytes / rs_s / 1e9,
                    "peak": hbm, "unit": "GB/s", "frac": gather_bytes / rs_s / 1e9 / hbm,
                    "traffic": traffic, "algorithmic_bytes": gather_bytes,
+                   "units": f"{B} SFTs x {info['nodes']} nodes per launch",
                    "peak_source": f"{peak_kind} hbm_gbs"}
     dominant = max(per_launch_us, key=per_launch_us.get)
     if dominant == "chirp_dft":
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        fl = dft_flops(info)
+        fl = B * dft_flops(info)
         ach = fl / (per_launch_us["chirp_dft"] * 1e-6) / 1e12
         roof = {"kernel": "bluestein (chirp-convolution DFT)", "bound": "alu", "achieved": ach,
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
@@ -283,27 +298,27 @@ def run_ours(args, rank, world, local_rank):
     else:
         roof = dict(roof_gather)
 
-    # end to end: host (pinned) input copied in, result read back, every step
+    # end to end: host (pinned) input copied in, result read back, every SFT (one request at a
+    # time through sft_execute)
     e2e = None
-    if rank == 0 or world > 1:
-        hosts = [inputs[i].cpu().pin_memory() for i in range(2)]
+    if (rank == 0 or world > 1) and not args.timed_only:
+        hosts = [inputs[i % n_in].cpu().pin_memory() for i in range(2)]
         dbuf = torch.empty_like(inputs[0])
         hw = torch.empty(s, dtype=torch.int64).pin_memory()
         hc = torch.empty(s, dtype=torch.complex128).pin_memory()
         hn = torch.empty(1, dtype=torch.int32).pin_memory()
-        n_e2e = max(4, min(K, 16))
+        n_e2e = 16
         for rep in range(2):
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             for i in range(n_e2e):
                 dbuf.copy_(hosts[i & 1], non_blocking=True)
-                o = outs[0]
-                sft.sft_execute(plan, dbuf.data_ptr(), o[0].data_ptr(), o[1].data_ptr(),
-                                o[2].data_ptr(), stream.cuda_stream)
-                hw.copy_(o[0], non_blocking=True)
-                hc.copy_(o[1], non_blocking=True)
-                hn.copy_(o[2], non_blocking=True)
+                sft.sft_execute(p0, dbuf.data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
+                                stream.cuda_stream)
+                hw.copy_(outs[0][0], non_blocking=True)
+                hc.copy_(outs[0][1], non_blocking=True)
+                hn.copy_(outs[0][2], non_blocking=True)
             b.record()
             torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / n_e2e
@@ -314,21 +329,17 @@ def run_ours(args, rank, world, local_rank):
 
     # the plain one-request-at-a-time FP64 path and a full cuFFT transform, same GPU, same inputs
     plain = None
-    if rank == 0:
-        v64 = sft.sft_variant_init(precision=sft.SFT_FP64, kappa=PLAN["kappa"], K=PLAN["K"],
-                                   c_p=PLAN["c_p"], alpha=PLAN["alpha"], beta=PLAN["beta"],
-                                   seed=PLAN["seed"])
-        p64 = sft.sft_plan(N, s, v64)
-        o64 = outs[1]
+    if rank == 0 and not args.timed_only:
+        p64 = sft.sft_plan(N, s, variant(sft.SFT_FP64))
         for i in range(2):
-            sft.sft_execute(p64, inputs[i].data_ptr(), o64[0].data_ptr(), o64[1].data_ptr(),
-                            o64[2].data_ptr(), stream.cuda_stream)
+            sft.sft_execute(p64, inputs[i % n_in].data_ptr(), w_ptrs[1], c_ptrs[1], n_ptrs[1],
+                            stream.cuda_stream)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for i in range(8):
-            sft.sft_execute(p64, inputs[i % N_INPUTS].data_ptr(), o64[0].data_ptr(),
-                            o64[1].data_ptr(), o64[2].data_ptr(), stream.cuda_stream)
+            sft.sft_execute(p64, inputs[i % n_in].data_ptr(), w_ptrs[1], c_ptrs[1], n_ptrs[1],
+                            stream.cuda_stream)
         b.record()
         torch.cuda.synchronize()
         plain_ms = a.elapsed_time(b) / 8
@@ -336,42 +347,52 @@ def run_ours(args, rank, world, local_rank):
         sign = torch.ones(N, dtype=torch.float32, device=dev)
         sign[1::2] = -1.0
 
+        def cufft_only(f):
+            return torch.fft.fft(f)
+
         def cufft_step(f):
             X = torch.fft.fft(f)
             X = X * (sign / N)          # F f = (-1)^w X / N on the index grid
             mag = X.real * X.real + X.imag * X.imag
             top = torch.topk(mag, s)
             return top.indices, X[top.indices]
-        for i in range(2):
-            cufft_step(inputs[i])
-        torch.cuda.synchronize()
-        a.record()
-        for i in range(8):
-            cufft_step(inputs[i % N_INPUTS])
-        b.record()
-        torch.cuda.synchronize()
-        cufft_ms = a.elapsed_time(b) / 8
-        plain = {"plain_fp64": {"value": 1e3 / plain_ms, "unit": "SFTs/s", "ms": plain_ms},
-                 "cufft": {"value": 1e3 / cufft_ms, "unit": "SFTs/s", "ms": cufft_ms,
+        res = {}
+        for name, fn in (("fft", cufft_only), ("fft_topk", cufft_step)):
+            for i in range(2):
+                fn(inputs[i % n_in])
+            torch.cuda.synchronize()
+            a.record()
+            for i in range(8):
+                fn(inputs[i % n_in])
+            b.record()
+            torch.cuda.synchronize()
+            res[name] = a.elapsed_time(b) / 8
+        plain = {"plain_fp64": {"value": 1e3 / plain_ms, "unit": "SFTs/s", "ms": plain_ms,
+                                "what": "the FP64 path, one request at a time"},
+                 "cufft": {"value": 1e3 / res["fft_topk"], "unit": "SFTs/s",
+                           "ms": res["fft_topk"], "fft_only_ms": res["fft"],
                            "what": "torch.fft.fft (cuFFT C2C FP32) + (-1)^w/N rescale + top-s"}}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.timed_only):
         cpu = cpu_baseline_sample(N, s, sfts=2)
 
-    plan.destroy()
+    batch.destroy()
+    for p in plans:
+        p.destroy()
     if rank != 0:
         return
-    lat_ms = lat
+    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
     out = {
         "metric": METRIC, "value": value, "unit": "SFTs/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(args, batch),
-        "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
-                                                                          int(0.99 * len(lat_ms)))],
-                       "mean": sum(lat_ms) / len(lat_ms), "what": "device time of one SFT"},
-        "stages_us_per_sft": per_launch_us,
+        "config": workload_config(args, B),
+        "latency_ms": {"p50": pct(single, 0.5), "p99": pct(single, 0.99),
+                       "what": "device time of one SFT executed alone (sft_execute)"},
+        "step_ms": {"p50": pct(step_ms, 0.5), "p99": pct(step_ms, 0.99),
+                    "what": f"one batched execution of {B} SFTs"},
+        "stages_us_per_launch": per_launch_us,
         "roofline": roof, "roofline_gather": roof_gather,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
         "cpu_baseline": cpu,
