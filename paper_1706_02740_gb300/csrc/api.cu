@@ -113,7 +113,7 @@ cudaError_t run_stages(const DevPlan& d0, const BatchView& bv, const LaunchSet& 
   mark(4);
   if (e == cudaSuccess) e = launch_select(bv, ls, st, launched);
   mark(5);
-  if (e == cudaSuccess && !fp64) { e = launch_refine(bv, ls, st); *launched += 2; }
+  if (e == cudaSuccess && !fp64) { e = launch_refine(bv, ls, st); *launched += 3; }
   if (e == cudaSuccess) e = launch_finalize(bv, ls, st, launched);
   mark(6);
   return e;

@@ -103,13 +103,45 @@ template <typename C> struct DFT<16, C> {
   __device__ static __forceinline__ void run(C* a) { DFTsplit<16, C>::run(a); }
 };
 
-// One Stockham pass of radix RAD over a length-M transform in shared memory s[0..M), current
-// sub-transform length SPAN.  Item i in [0, M/RAD): reads s[i + r M/RAD], applies the twiddles
-// e^{-2 pi i r k / (SPAN RAD)} (k = i mod SPAN), takes a radix-RAD DFT and writes
-// s[(i - k) RAD + k + r SPAN].  All reads of the pass finish before any write (barrier), so the
-// pass is in place.  Each of the TPT threads of the transform handles M / (RAD TPT) items.
-template <typename C, int M, int RAD, int SPAN, int TPT>
-__device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict__ W) {
+// Where a pass takes its input and puts its output.  The chirp convolution folds its pointwise
+// steps into the passes: the first FFT's first pass reads the samples from global memory times
+// the chirp (zero beyond p), the second FFT's first pass multiplies by the filter spectrum and
+// conjugates as it reads, and its last pass writes conj(.) times the chirp straight to the p
+// outputs.  Other passes read and write shared memory.
+enum { kFromSmem = 0, kFromInput = 1, kFromSmemTimesFilter = 2 };
+enum { kToSmem = 0, kToOutput = 1 };
+
+template <typename C>
+struct ChirpIO {
+  const C* in;
+  const C* chirp;
+  const C* vhat;
+  C* out;
+  int p;          // 0 for an inactive transform slot: nothing is read or written
+};
+
+// v[r] *= w^r for r < RAD using only the table entries w^1, w^2, w^4, w^8: each element is
+// multiplied by the entries of the set bits of r (at most four products, so the rounding stays
+// within a few ulps of the exactly rounded table, and only four table values are live).
+template <typename C, int RAD>
+__device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int base, C* v) {
+#pragma unroll
+  for (int bit = 1; bit < RAD; bit <<= 1) {
+    const C pw = __ldg(W + bit * base);       // w^bit
+#pragma unroll
+    for (int r = 1; r < RAD; ++r)
+      if (r & bit) v[r] = cmul(v[r], pw);
+  }
+}
+
+// One Stockham pass of radix RAD over a length-M transform, current sub-transform length SPAN.
+// Item i in [0, M/RAD): takes element i + r M/RAD, applies the twiddles e^{-2 pi i r k / (SPAN RAD)}
+// (k = i mod SPAN), takes a radix-RAD DFT and puts element (i - k) RAD + k + r SPAN.  All reads of
+// the pass finish before any shared-memory write (barrier), so the pass is in place.  Each of the
+// TPT threads of the transform handles M / (RAD TPT) items.
+template <typename C, int M, int RAD, int SPAN, int TPT, int LOAD, int STORE>
+__device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict__ W,
+                                              const ChirpIO<C>& io) {
   constexpr int ITEMS = M / RAD / TPT;
   C v[ITEMS * RAD];
 #pragma unroll
@@ -117,12 +149,16 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
     const int i = lt + it * TPT;
     const int k = i & (SPAN - 1);
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[it * RAD + r] = s[pad16(i + r * (M / RAD))];
-    if (SPAN > 1) {
-#pragma unroll
-      for (int r = 1; r < RAD; ++r)
-        v[it * RAD + r] = cmul(v[it * RAD + r], __ldg(W + r * k * (M / (SPAN * RAD))));
+    for (int r = 0; r < RAD; ++r) {
+      const int n = i + r * (M / RAD);
+      if (LOAD == kFromInput)        // only the first p entries were written: the rest are zero
+        v[it * RAD + r] = (n < io.p) ? s[pad16(n)] : czero<C>();
+      else if (LOAD == kFromSmemTimesFilter)
+        v[it * RAD + r] = cconj(cmul(s[pad16(n)], __ldg(io.vhat + n)));
+      else
+        v[it * RAD + r] = s[pad16(n)];
     }
+    if (SPAN > 1) apply_twiddles<C, RAD>(W, k * (M / (SPAN * RAD)), &v[it * RAD]);
     DFT<RAD, C>::run(&v[it * RAD]);
   }
   __syncthreads();
@@ -132,22 +168,30 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
     const int k = i & (SPAN - 1);
     const int j0 = (i - k) * RAD + k;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) s[pad16(j0 + r * SPAN)] = v[it * RAD + r];
+    for (int r = 0; r < RAD; ++r) {
+      const int c = j0 + r * SPAN;
+      if (STORE == kToOutput) {
+        if (c < io.p) io.out[c] = cmul(cconj(v[it * RAD + r]), __ldg(io.chirp + c));
+      } else {
+        s[pad16(c)] = v[it * RAD + r];
+      }
+    }
   }
-  __syncthreads();
+  if (STORE == kToSmem) __syncthreads();
 }
 
-template <typename C, int M, int SPAN, int TPT>
+template <typename C, int M, int SPAN, int TPT, int LOAD, int STORE>
 struct FFTPasses {
-  __device__ static __forceinline__ void run(C* s, int lt, const C* W) {
+  __device__ static __forceinline__ void run(C* s, int lt, const C* W, const ChirpIO<C>& io) {
     constexpr int RAD = (M / SPAN) >= 16 ? 16 : (M / SPAN);
-    stockham_pass<C, M, RAD, SPAN, TPT>(s, lt, W);
-    FFTPasses<C, M, SPAN * RAD, TPT>::run(s, lt, W);
+    constexpr bool last = SPAN * RAD == M;
+    stockham_pass<C, M, RAD, SPAN, TPT, LOAD, last ? STORE : kToSmem>(s, lt, W, io);
+    FFTPasses<C, M, SPAN * RAD, TPT, kFromSmem, STORE>::run(s, lt, W, io);
   }
 };
-template <typename C, int M, int TPT>
-struct FFTPasses<C, M, M, TPT> {
-  __device__ static __forceinline__ void run(C*, int, const C*) {}
+template <typename C, int M, int TPT, int LOAD, int STORE>
+struct FFTPasses<C, M, M, TPT, LOAD, STORE> {
+  __device__ static __forceinline__ void run(C*, int, const C*, const ChirpIO<C>&) {}
 };
 
 // FP32 transforms up to M = 8192 are limited to 64 registers so that two CTAs share an SM.
@@ -183,16 +227,14 @@ bluestein_kernel(BatchView bv) {
   const C* vhat = reinterpret_cast<const C*>(d.vhat) + (int64_t)j * M;
   const C* W = reinterpret_cast<const C*>(d.fftw);
   C* s = buf + g * padded_len<M>();
-
-  for (int n = lt; n < M; n += TPT)
-    s[pad16(n)] = (active && n < p) ? cmul(in[n], __ldg(chirp + n)) : czero<C>();
+  const ChirpIO<C> io{in, chirp, vhat, out, active ? p : 0};
+  for (int n = lt; n < io.p; n += TPT) s[pad16(n)] = cmul(in[n], __ldg(chirp + n));
   __syncthreads();
-  FFTPasses<C, M, 1, TPT>::run(s, lt, W);
+  FFTPasses<C, M, 1, TPT, kFromInput, kToSmem>::run(s, lt, W, io);
   for (int n = lt; n < M; n += TPT) s[pad16(n)] = cconj(cmul(s[pad16(n)], __ldg(vhat + n)));
   __syncthreads();
-  FFTPasses<C, M, 1, TPT>::run(s, lt, W);
-  if (active)
-    for (int c = lt; c < p; c += TPT) out[c] = cmul(cconj(s[pad16(c)]), __ldg(chirp + c));
+  FFTPasses<C, M, 1, TPT, kFromSmem, kToSmem>::run(s, lt, W, io);
+  for (int c = lt; c < io.p; c += TPT) out[c] = cmul(cconj(s[pad16(c)]), __ldg(chirp + c));
 }
 
 template <int M> constexpr int log2_of() { return M <= 1 ? 0 : 1 + log2_of<M / 2>(); }
@@ -304,7 +346,8 @@ __global__ void __launch_bounds__(M / 16) noalloc_filter_kernel(int n, float2* V
   const int lt = threadIdx.x;
   for (int i = lt; i < M; i += TPT) s[pad16(i)] = V[i];
   __syncthreads();
-  FFTPasses<float2, M, 1, TPT>::run(s, lt, W);
+  const ChirpIO<float2> io{nullptr, nullptr, nullptr, nullptr, 0};
+  FFTPasses<float2, M, 1, TPT, kFromSmem, kToSmem>::run(s, lt, W, io);
   const float scale = (float)(1.0 / ((double)M * (double)n));
   for (int i = lt; i < M; i += TPT) V[i] = cscale(s[pad16(i)], scale);
 }

@@ -345,6 +345,8 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   const size_t o_pool = soff;    soff = align256(soff + (size_t)nq * s * sizeof(Pooled));
   const size_t o_win = soff;     soff = align256(soff + (size_t)s * sizeof(Pooled));
   const size_t o_ybuf = soff;    soff = align256(soff + (size_t)d.nchunk * s * K * sizeof(double2));
+  const size_t o_wlist = soff;   soff = align256(soff + (size_t)s * 4);
+  const size_t o_woff = soff;    soff = align256(soff + (size_t)(nq + 1) * 4);
   const size_t o_self = soff;    soff = align256(soff + sizeof(DevPlan));
   const size_t total = soff;
 
@@ -374,6 +376,8 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   d.pool = reinterpret_cast<Pooled*>(base + o_pool);
   d.winners = reinterpret_cast<Pooled*>(base + o_win);
   d.ybuf = reinterpret_cast<double2*>(base + o_ybuf);
+  d.wlist = reinterpret_cast<int32_t*>(base + o_wlist);
+  d.woff = reinterpret_cast<int32_t*>(base + o_woff);
   P->d_dev = reinterpret_cast<DevPlan*>(base + o_self);
   e = cudaMemcpy(P->d_dev, &d, sizeof(DevPlan), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {

@@ -32,19 +32,45 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
   s = t;
 }
 
+// Error-free two-sum in FP32 (Knuth): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 __device__ __forceinline__ int mod_p32(int64_t w, int p) {
   const int r = (int)w % p;
   return r < 0 ? r + p : r;
 }
 
-__global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
-  __shared__ float2 S[kReChunk];
-  __shared__ int list_r[kReChunk];
-  __shared__ int list_b[kReChunk];
-  __shared__ int list_n;
+// Winner indices grouped by shift (one CTA per signal), for the re-estimation CTAs.
+__global__ void __launch_bounds__(256) group_winners_kernel(BatchView bv) {
+  __shared__ int cnt[kMaxQ], cur[kMaxQ];
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int n = d.counters[d.nq + 2];
+  if (threadIdx.x < kMaxQ) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += 256) atomicAdd(&cnt[d.winners[r].qi], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int q = 0; q < d.nq; ++q) {
+      d.woff[q] = acc;
+      cur[q] = acc;
+      acc += cnt[q];
+    }
+    d.woff[d.nq] = acc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += 256) d.wlist[atomicAdd(&cur[d.winners[r].qi], 1)] = r;
+}
+
+__global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
+  __shared__ float2 S[kReChunk];
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int qk = lb / d.nchunk;
   const int c = lb - qk * d.nchunk;
   const int qi = qk / d.K;
@@ -54,38 +80,45 @@ __global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
   const int klen = max(0, min(kReChunk, p - k0));
   const float2* src = reinterpret_cast<const float2*>(d.samples) + (int64_t)qi * d.m + d.nodeoff[jj];
   if (threadIdx.x < klen) S[threadIdx.x] = src[k0 + threadIdx.x];
+  __syncthreads();
   const float2* Wp = d.wp32 + (int64_t)jj * d.pmax;
   float4* part = reinterpret_cast<float4*>(d.ybuf) + (int64_t)c * d.s * d.K;
-  // winners of this shift, kReChunk at a time
-  for (int base = 0; base < n; base += kReChunk) {
-    if (threadIdx.x == 0) list_n = 0;
-    __syncthreads();
-    const int r = base + threadIdx.x;
-    if (r < n) {
-      const Pooled pw = d.winners[r];
-      if (pw.qi == qi) {
-        const int slot = atomicAdd(&list_n, 1);
-        list_r[slot] = r;
-        list_b[slot] = mod_p32(pw.w, p);
-      }
+  const int beg = d.woff[qi], cnt = d.woff[qi + 1] - beg;
+  for (int t = threadIdx.x; t < cnt; t += kReChunk) {
+    const int r = d.wlist[beg + t];
+    const int b = mod_p32(d.winners[r].w, p);
+    // two independent compensated chains (even and odd k) for instruction-level parallelism
+    int i0 = (k0 * b) % p;                        // k0 b < 2^26: 32-bit
+    int i1 = i0 + b;
+    if (i1 >= p) i1 -= p;
+    int b2 = b + b;
+    if (b2 >= p) b2 -= p;
+    float sr0 = 0.f, cr0 = 0.f, si0 = 0.f, ci0 = 0.f;
+    float sr1 = 0.f, cr1 = 0.f, si1 = 0.f, ci1 = 0.f;
+    int k = 0;
+    for (; k + 1 < klen; k += 2) {
+      const float2 a0 = S[k], a1 = S[k + 1];
+      const float2 w0 = __ldg(Wp + i0), w1 = __ldg(Wp + i1);
+      neumaier_add(sr0, cr0, fmaf(a0.x, w0.x, -a0.y * w0.y));
+      neumaier_add(si0, ci0, fmaf(a0.x, w0.y, a0.y * w0.x));
+      neumaier_add(sr1, cr1, fmaf(a1.x, w1.x, -a1.y * w1.y));
+      neumaier_add(si1, ci1, fmaf(a1.x, w1.y, a1.y * w1.x));
+      i0 += b2;
+      if (i0 >= p) i0 -= p;
+      i1 += b2;
+      if (i1 >= p) i1 -= p;
     }
-    __syncthreads();
-    if (threadIdx.x < list_n) {
-      const int rr = list_r[threadIdx.x];
-      const int b = list_b[threadIdx.x];
-      int idx = (k0 * b) % p;                    // k0 b < 2^26: 32-bit
-      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-      for (int k = 0; k < klen; ++k) {
-        const float2 a = S[k];
-        const float2 w = __ldg(Wp + idx);
-        neumaier_add(sr, cr, fmaf(a.x, w.x, -a.y * w.y));
-        neumaier_add(si, ci, fmaf(a.x, w.y, a.y * w.x));
-        idx += b;
-        if (idx >= p) idx -= p;
-      }
-      part[(int64_t)rr * d.K + jj] = make_float4(sr, cr, si, ci);
+    if (k < klen) {
+      const float2 a0 = S[k];
+      const float2 w0 = __ldg(Wp + i0);
+      neumaier_add(sr0, cr0, fmaf(a0.x, w0.x, -a0.y * w0.y));
+      neumaier_add(si0, ci0, fmaf(a0.x, w0.y, a0.y * w0.x));
     }
-    __syncthreads();
+    // merge the chains: (sr0 + sr1) exactly as a (sum, error) pair, compensations added
+    float sr, er, si, ei;
+    two_sum_f(sr0, sr1, sr, er);
+    two_sum_f(si0, si1, si, ei);
+    part[(int64_t)r * d.K + jj] = make_float4(sr, er + cr0 + cr1, si, ei + ci0 + ci1);
   }
 }
 
@@ -139,6 +172,8 @@ __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView
 
 cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t st) {
   BatchView v = bv;
+  v.blk = ls.blk[kStOne];
+  group_winners_kernel<<<ls.blocks[kStOne], 256, 0, st>>>(v);
   v.blk = ls.blk[kStReest];
   reestimate_kernel<<<ls.blocks[kStReest], kReChunk, 0, st>>>(v);
   v.blk = ls.blk[kStRefine];

@@ -85,6 +85,8 @@ struct DevPlan {
   Pooled* pool;               // [nq * s]
   Pooled* winners;            // [s]
   double2* ybuf;              // [nchunk][s][K] partial sums of the re-estimated bins
+  int32_t* wlist;             // [s] winner indices grouped by shift
+  int32_t* woff;              // [nq + 1] start of each shift's group in wlist
 };
 
 constexpr int kReChunk = 256;   // samples per re-estimation CTA
