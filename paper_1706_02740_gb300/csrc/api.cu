@@ -43,6 +43,7 @@ LaunchSet single_launch_set(const DevPlan& d) {
     ls.blocks[k] = signal_blocks(d, k);
     ls.blk[k] = nullptr;
   }
+  ls.pmax = d.pmax;
   return ls;
 }
 

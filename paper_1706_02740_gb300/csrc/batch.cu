@@ -7,6 +7,7 @@
 // the same stage sequence as a single plan, each stage launched once for the whole batch.
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -98,6 +99,8 @@ sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n
     prefix[(size_t)k * (n + 1) + n] = (int32_t)acc;
     B.ls.blocks[k] = (int32_t)acc;
   }
+  B.ls.pmax = 0;
+  for (int i = 0; i < n; ++i) B.ls.pmax = std::max(B.ls.pmax, ps[i]->d.pmax);
   const size_t o_plans = 0;
   const size_t o_prefix = align256(o_plans + sizeof(DevPlan) * (size_t)n);
   const size_t o_ptrs = align256(o_prefix + prefix.size() * sizeof(int32_t));

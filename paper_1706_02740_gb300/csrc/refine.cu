@@ -6,9 +6,10 @@
 // is recomputed directly from the same filtered samples with exactly rounded twiddles
 // e^{-2 pi i ((k b) mod p_j) / p_j}.
 //
-// Work layout: one CTA per (shift, prime, chunk of kReChunk samples).  The CTA stages its chunk in
-// shared memory, collects the winners of its shift, and each thread sums the chunk against one
-// winner's twiddles with compensated (Neumaier) FP32 accumulation; the chunk partials, kept as
+// Work layout: one CTA per (shift, prime, chunk of kReChunk samples).  The CTA stages its chunk and
+// the prime's twiddle table in shared memory, and each thread sums the chunk against one winner's
+// twiddles: FMA blocks of 16 terms, added to the partial with compensation (Neumaier), in FP32.
+// The chunk partials, kept as
 // (sum, compensation) pairs, are combined exactly enough in double-single arithmetic.  The
 // componentwise medians (eq. GSFT_Estimate), the sign (-1)^w and the division by g_hat_{w - q}
 // (Lemma Periodic_Gaussian_FC) are done in FP64, spread over many CTAs.  All integer indexing is
@@ -68,57 +69,81 @@ __global__ void __launch_bounds__(256) group_winners_kernel(BatchView bv) {
 }
 
 __global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
-  __shared__ float2 S[kReChunk];
+  // [kReChunk] samples of this chunk, then the prime's [p] twiddles: each thread walks its own
+  // residue sequence (k b) mod p, so the table reads scatter across the warp; shared memory serves
+  // them with a few bank conflicts where the cached global table would take one line per lane.
+  extern __shared__ float2 sm_re[];
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int qk = lb / d.nchunk;
   const int c = lb - qk * d.nchunk;
   const int qi = qk / d.K;
   const int jj = qk - qi * d.K;
+  const int beg = d.woff[qi], cnt = d.woff[qi + 1] - beg;
+  if (cnt == 0) return;
   const int p = d.p[jj];
   const int k0 = c * kReChunk;
   const int klen = max(0, min(kReChunk, p - k0));
+  float2* S = sm_re;
+  float2* Wt = sm_re + kReChunk;
   const float2* src = reinterpret_cast<const float2*>(d.samples) + (int64_t)qi * d.m + d.nodeoff[jj];
   if (threadIdx.x < klen) S[threadIdx.x] = src[k0 + threadIdx.x];
-  __syncthreads();
   const float2* Wp = d.wp32 + (int64_t)jj * d.pmax;
+  for (int i = threadIdx.x; i < p; i += kReChunk) Wt[i] = __ldg(Wp + i);
+  __syncthreads();
   float4* part = reinterpret_cast<float4*>(d.ybuf) + (int64_t)c * d.s * d.K;
-  const int beg = d.woff[qi], cnt = d.woff[qi + 1] - beg;
   for (int t = threadIdx.x; t < cnt; t += kReChunk) {
     const int r = d.wlist[beg + t];
     const int b = mod_p32(d.winners[r].w, p);
-    // two independent compensated chains (even and odd k) for instruction-level parallelism
+    // Blocks of kBlock terms are accumulated with plain FMAs in two interleaved chains (even and
+    // odd k); the block sums are added with compensation.  A block's rounding is a few ulps of
+    // kBlock terms, so the partial stays within ~eps * sqrt(p) * |h| of exact, two orders below
+    // the weakest estimates' tolerance.
+    constexpr int kBlock = 16;
     int i0 = (k0 * b) % p;                        // k0 b < 2^26: 32-bit
     int i1 = i0 + b;
     if (i1 >= p) i1 -= p;
     int b2 = b + b;
     if (b2 >= p) b2 -= p;
-    float sr0 = 0.f, cr0 = 0.f, si0 = 0.f, ci0 = 0.f;
-    float sr1 = 0.f, cr1 = 0.f, si1 = 0.f, ci1 = 0.f;
-    int k = 0;
-    for (; k + 1 < klen; k += 2) {
-      const float2 a0 = S[k], a1 = S[k + 1];
-      const float2 w0 = __ldg(Wp + i0), w1 = __ldg(Wp + i1);
-      neumaier_add(sr0, cr0, fmaf(a0.x, w0.x, -a0.y * w0.y));
-      neumaier_add(si0, ci0, fmaf(a0.x, w0.y, a0.y * w0.x));
-      neumaier_add(sr1, cr1, fmaf(a1.x, w1.x, -a1.y * w1.y));
-      neumaier_add(si1, ci1, fmaf(a1.x, w1.y, a1.y * w1.x));
-      i0 += b2;
-      if (i0 >= p) i0 -= p;
-      i1 += b2;
-      if (i1 >= p) i1 -= p;
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    for (int kb = 0; kb < klen; kb += kBlock) {
+      const int ke = min(klen, kb + kBlock);
+      float r0 = 0.f, m0 = 0.f, r1 = 0.f, m1 = 0.f;
+      int k = kb;
+      for (; k + 1 < ke; k += 2) {
+        const float2 a0 = S[k], a1 = S[k + 1];
+        const float2 w0 = Wt[i0], w1 = Wt[i1];
+        r0 = fmaf(a0.x, w0.x, r0);
+        r0 = fmaf(-a0.y, w0.y, r0);
+        m0 = fmaf(a0.x, w0.y, m0);
+        m0 = fmaf(a0.y, w0.x, m0);
+        r1 = fmaf(a1.x, w1.x, r1);
+        r1 = fmaf(-a1.y, w1.y, r1);
+        m1 = fmaf(a1.x, w1.y, m1);
+        m1 = fmaf(a1.y, w1.x, m1);
+        i0 += b2;
+        if (i0 >= p) i0 -= p;
+        i1 += b2;
+        if (i1 >= p) i1 -= p;
+      }
+      if (k < ke) {
+        const float2 a0 = S[k];
+        const float2 w0 = Wt[i0];
+        r0 = fmaf(a0.x, w0.x, r0);
+        r0 = fmaf(-a0.y, w0.y, r0);
+        m0 = fmaf(a0.x, w0.y, m0);
+        m0 = fmaf(a0.y, w0.x, m0);
+        // the odd chain's index is one step ahead: keep both aligned for the next block
+        i0 = i1;
+        i1 += b;
+        if (i1 >= p) i1 -= p;
+      }
+      neumaier_add(sr, cr, r0);
+      neumaier_add(sr, cr, r1);
+      neumaier_add(si, ci, m0);
+      neumaier_add(si, ci, m1);
     }
-    if (k < klen) {
-      const float2 a0 = S[k];
-      const float2 w0 = __ldg(Wp + i0);
-      neumaier_add(sr0, cr0, fmaf(a0.x, w0.x, -a0.y * w0.y));
-      neumaier_add(si0, ci0, fmaf(a0.x, w0.y, a0.y * w0.x));
-    }
-    // merge the chains: (sr0 + sr1) exactly as a (sum, error) pair, compensations added
-    float sr, er, si, ei;
-    two_sum_f(sr0, sr1, sr, er);
-    two_sum_f(si0, si1, si, ei);
-    part[(int64_t)r * d.K + jj] = make_float4(sr, er + cr0 + cr1, si, ei + ci0 + ci1);
+    part[(int64_t)r * d.K + jj] = make_float4(sr, cr, si, ci);
   }
 }
 
@@ -175,7 +200,13 @@ cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t
   v.blk = ls.blk[kStOne];
   group_winners_kernel<<<ls.blocks[kStOne], 256, 0, st>>>(v);
   v.blk = ls.blk[kStReest];
-  reestimate_kernel<<<ls.blocks[kStReest], kReChunk, 0, st>>>(v);
+  const size_t smem = (size_t)(kReChunk + ls.pmax) * sizeof(float2);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(reestimate_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  reestimate_kernel<<<ls.blocks[kStReest], kReChunk, smem, st>>>(v);
   v.blk = ls.blk[kStRefine];
   refine_values_kernel<<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
   return cudaGetLastError();

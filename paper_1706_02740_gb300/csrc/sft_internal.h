@@ -167,6 +167,7 @@ enum StageKind {
 struct LaunchSet {
   int32_t blocks[kStCount];
   const int32_t* blk[kStCount];
+  int32_t pmax;               // largest prime over the signals (shared-memory sizing)
 };
 
 int bluestein_blocks(const DevPlan& d, int M);   // chirp-convolution blocks of one signal (length M)
