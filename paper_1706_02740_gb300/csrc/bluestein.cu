@@ -7,10 +7,12 @@
 //     E = w . conj( FFT( conj( FFT(h w, zero padded) . V ) ) ),
 // V = FFT(conj(w) wrapped) / (M p) precomputed per prime in FP64 on the host (the inverse FFT is the
 // forward one between two conjugations).  One transform lives in shared memory; the FFT is an
-// in-place Stockham schedule whose passes hold 16 complex values per thread in registers (radix 16
-// passes, then one radix 2/4/8 pass), with twiddles read from an exactly rounded table.  The
-// shared-memory layout inserts one pad element after every 16 (index n -> n + n/16), so the
-// strided stores of the first two passes hit distinct banks.
+// in-place Stockham schedule whose passes hold 16 complex values per thread in registers: a
+// radix-2 first pass, radix-16 passes, then one radix 2/4/8 pass where M needs it, with twiddles
+// read from exactly rounded per-pass tables.  Since p <= M/2, the first FFT's radix-2 pass only
+// duplicates its input and is skipped.
+// The shared-memory layout inserts one pad element after every 16 (index n -> n + n/16), so the
+// strided stores of the short-span passes hit distinct banks.
 #include <stdint.h>
 #include <string.h>
 
@@ -27,42 +29,33 @@ namespace {
 __device__ __forceinline__ int pad16(int n) { return n + (n >> 4); }
 template <int M> constexpr int padded_len() { return M + M / 16; }
 
-// e^{-2 pi i k / 16}, k = 0..15 (mathematical constants, correctly rounded).
-__device__ __constant__ double kW16re[16] = {
-    1.0, 0.92387953251128674, 0.70710678118654752, 0.38268343236508977,
-    0.0, -0.38268343236508977, -0.70710678118654752, -0.92387953251128674,
-    -1.0, -0.92387953251128674, -0.70710678118654752, -0.38268343236508977,
-    0.0, 0.38268343236508977, 0.70710678118654752, 0.92387953251128674};
-__device__ __constant__ double kW16im[16] = {
-    0.0, -0.38268343236508977, -0.70710678118654752, -0.92387953251128674,
-    -1.0, -0.92387953251128674, -0.70710678118654752, -0.38268343236508977,
-    0.0, 0.38268343236508977, 0.70710678118654752, 0.92387953251128674,
-    1.0, 0.92387953251128674, 0.70710678118654752, 0.38268343236508977};
+// Constants of the radix-8 and radix-16 butterflies: cos(pi/8), sin(pi/8), sqrt(1/2).
+constexpr double kC8 = 0.92387953251128674;
+constexpr double kS8 = 0.38268343236508977;
+constexpr double kH = 0.70710678118654752;
 
-__device__ __constant__ float kW16reF[16] = {
-    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
-    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
-__device__ __constant__ float kW16imF[16] = {
-    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
-    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
-    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
 
-template <typename C> __device__ __forceinline__ C w16(int k);
-template <> __device__ __forceinline__ float2 w16<float2>(int k) {
-  return make_float2(kW16reF[k], kW16imF[k]);
+// a (c - i s) for constants c, s
+template <typename C, typename R>
+__device__ __forceinline__ C mul_cs(C a, R c, R s) {
+  return C{r_fma(a.x, c, a.y * s), r_fma(a.y, c, -a.x * s)};
 }
-template <> __device__ __forceinline__ double2 w16<double2>(int k) {
-  return make_double2(kW16re[k], kW16im[k]);
+// a e^{-i pi / 4} = a (1 - i) / sqrt 2
+template <typename C> __device__ __forceinline__ C mul_w8_1(C a) {
+  using R = decltype(a.x);
+  return C{(a.x + a.y) * (R)kH, (a.y - a.x) * (R)kH};
+}
+// a e^{-3 i pi / 4} = a (-1 - i) / sqrt 2
+template <typename C> __device__ __forceinline__ C mul_w8_3(C a) {
+  using R = decltype(a.x);
+  return C{(a.y - a.x) * (R)kH, -(a.x + a.y) * (R)kH};
 }
 
-// In-register DFT of length R (forward), natural order in and out.
+// In-register forward DFT of length R, natural order in and out.  The multiplications by 1 and
+// -i are written out, so only the nontrivial twiddles cost multiplications.
 template <int R, typename C> struct DFT;
-template <typename C> struct DFT<1, C> {
-  __device__ static __forceinline__ void run(C*) {}
-};
 template <typename C> struct DFT<2, C> {
   __device__ static __forceinline__ void run(C* a) {
     C t = a[0];
@@ -80,35 +73,59 @@ template <typename C> struct DFT<4, C> {
     a[3] = csub(t1, t3);
   }
 };
-// Radix-2 split of a length-R DFT into two of length R/2 (R = 8, 16).
-template <int R, typename C> struct DFTsplit {
+// 8 = 2 x 4: X[k] = E[k] + w8^k O[k], X[k + 4] = E[k] - w8^k O[k].
+template <typename C> struct DFT<8, C> {
   __device__ static __forceinline__ void run(C* a) {
-    C e[R / 2], o[R / 2];
+    C e[4] = {a[0], a[2], a[4], a[6]}, o[4] = {a[1], a[3], a[5], a[7]};
+    DFT<4, C>::run(e);
+    DFT<4, C>::run(o);
+    o[1] = mul_w8_1(o[1]);
+    o[2] = cmul_mi(o[2]);
+    o[3] = mul_w8_3(o[3]);
 #pragma unroll
-    for (int i = 0; i < R / 2; ++i) { e[i] = a[2 * i]; o[i] = a[2 * i + 1]; }
-    DFT<R / 2, C>::run(e);
-    DFT<R / 2, C>::run(o);
-#pragma unroll
-    for (int k = 0; k < R / 2; ++k) {
-      C t = cmul(o[k], w16<C>(k * (16 / R)));
-      a[k] = cadd(e[k], t);
-      a[k + R / 2] = csub(e[k], t);
+    for (int k = 0; k < 4; ++k) {
+      a[k] = cadd(e[k], o[k]);
+      a[k + 4] = csub(e[k], o[k]);
     }
   }
 };
-template <typename C> struct DFT<8, C> {
-  __device__ static __forceinline__ void run(C* a) { DFTsplit<8, C>::run(a); }
-};
+// 16 = 4 x 4 with n = n1 + 4 n2, k = k2 + 4 k1: length-4 DFTs over n2, twiddles w16^{n1 k2},
+// length-4 DFTs over n1.
 template <typename C> struct DFT<16, C> {
-  __device__ static __forceinline__ void run(C* a) { DFTsplit<16, C>::run(a); }
+  __device__ static __forceinline__ void run(C* a) {
+    using R = decltype(a[0].x);
+    C y[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      C t[4] = {a[n1], a[n1 + 4], a[n1 + 8], a[n1 + 12]};
+      DFT<4, C>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) y[n1][k2] = t[k2];
+    }
+    y[1][1] = mul_cs(y[1][1], (R)kC8, (R)kS8);     // w16^1
+    y[1][2] = mul_w8_1(y[1][2]);                  // w16^2
+    y[1][3] = mul_cs(y[1][3], (R)kS8, (R)kC8);     // w16^3
+    y[2][1] = mul_w8_1(y[2][1]);                  // w16^2
+    y[2][2] = cmul_mi(y[2][2]);                   // w16^4
+    y[2][3] = mul_w8_3(y[2][3]);                  // w16^6
+    y[3][1] = mul_cs(y[3][1], (R)kS8, (R)kC8);     // w16^3
+    y[3][2] = mul_w8_3(y[3][2]);                  // w16^6
+    y[3][3] = mul_cs(y[3][3], (R)-kC8, (R)-kS8);   // w16^9
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      C t[4] = {y[0][k2], y[1][k2], y[2][k2], y[3][k2]};
+      DFT<4, C>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) a[k2 + 4 * k1] = t[k1];
+    }
+  }
 };
 
 // Where a pass takes its input and puts its output.  The chirp convolution folds its pointwise
-// steps into the passes: the first FFT's first pass reads the samples from global memory times
-// the chirp (zero beyond p), the second FFT's first pass multiplies by the filter spectrum and
-// conjugates as it reads, and its last pass writes conj(.) times the chirp straight to the p
-// outputs.  Other passes read and write shared memory.
-enum { kFromSmem = 0, kFromInput = 1, kFromSmemTimesFilter = 2 };
+// steps into the passes: the first FFT's first pass reads the chirp-multiplied samples (zero from p
+// on) from the first p entries of shared memory, and the second FFT's last pass writes conj(.) times
+// the chirp straight to the p outputs.  Other passes read and write shared memory.
+enum { kFromSmem = 0, kFromInput = 1 };
 enum { kToSmem = 0, kToOutput = 1 };
 
 template <typename C>
@@ -120,17 +137,19 @@ struct ChirpIO {
   int p;          // 0 for an inactive transform slot: nothing is read or written
 };
 
-// v[r] *= w^r for r < RAD using only the table entries w^1, w^2, w^4, w^8: each element is
-// multiplied by the entries of the set bits of r (at most four products, so the rounding stays
-// within a few ulps of the exactly rounded table, and only four table values are live).
-template <typename C, int RAD>
-__device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int base, C* v) {
+// v[r] *= w^r, w = e^{-2 pi i k / (SPAN RAD)}, using only the rows w^1, w^2, w^4, w^8 of the
+// pass's table: each element is multiplied by the entries of the set bits of r (at most four
+// products, so the rounding stays within a few ulps of the exactly rounded twiddle, and only one
+// table value is live).  Lanes with consecutive k read consecutive table entries.
+template <typename C, int M, int RAD, int SPAN>
+__device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C* v) {
+  constexpr int base = fft_tw_offset(M, SPAN);
 #pragma unroll
-  for (int bit = 1; bit < RAD; bit <<= 1) {
-    const C pw = __ldg(W + bit * base);       // w^bit
+  for (int row = 0; (1 << row) < RAD; ++row) {
+    const C pw = __ldg(W + base + row * SPAN + k);
 #pragma unroll
     for (int r = 1; r < RAD; ++r)
-      if (r & bit) v[r] = cmul(v[r], pw);
+      if (r & (1 << row)) v[r] = cmul(v[r], pw);
   }
 }
 
@@ -139,6 +158,10 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int base
 // (k = i mod SPAN), takes a radix-RAD DFT and puts element (i - k) RAD + k + r SPAN.  All reads of
 // the pass finish before any shared-memory write (barrier), so the pass is in place.  Each of the
 // TPT threads of the transform handles M / (RAD TPT) items.
+//
+// LOAD == kFromInput is the first pass after the radix-2 first pass of a transform whose input
+// x vanishes from p <= M/2 on: that radix-2 pass only duplicates (y[2i] = y[2i + 1] = x[i]), so it
+// is never run and this pass reads y[n] = x[n / 2] from the first p entries of shared memory.
 template <typename C, int M, int RAD, int SPAN, int TPT, int LOAD, int STORE>
 __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict__ W,
                                               const ChirpIO<C>& io) {
@@ -151,14 +174,14 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
       const int n = i + r * (M / RAD);
-      if (LOAD == kFromInput)        // only the first p entries were written: the rest are zero
-        v[it * RAD + r] = (n < io.p) ? s[pad16(n)] : czero<C>();
-      else if (LOAD == kFromSmemTimesFilter)
-        v[it * RAD + r] = cconj(cmul(s[pad16(n)], __ldg(io.vhat + n)));
-      else
+      if (LOAD == kFromInput) {
+        const int m = n >> 1;
+        v[it * RAD + r] = (m < io.p) ? s[pad16(m)] : czero<C>();
+      } else {
         v[it * RAD + r] = s[pad16(n)];
+      }
     }
-    if (SPAN > 1) apply_twiddles<C, RAD>(W, k * (M / (SPAN * RAD)), &v[it * RAD]);
+    apply_twiddles<C, M, RAD, SPAN>(W, k, &v[it * RAD]);
     DFT<RAD, C>::run(&v[it * RAD]);
   }
   __syncthreads();
@@ -180,10 +203,11 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
   if (STORE == kToSmem) __syncthreads();
 }
 
+// The passes from sub-transform length SPAN (>= 2) to M.
 template <typename C, int M, int SPAN, int TPT, int LOAD, int STORE>
 struct FFTPasses {
   __device__ static __forceinline__ void run(C* s, int lt, const C* W, const ChirpIO<C>& io) {
-    constexpr int RAD = (M / SPAN) >= 16 ? 16 : (M / SPAN);
+    constexpr int RAD = fft_radix(M, SPAN);
     constexpr bool last = SPAN * RAD == M;
     stockham_pass<C, M, RAD, SPAN, TPT, LOAD, last ? STORE : kToSmem>(s, lt, W, io);
     FFTPasses<C, M, SPAN * RAD, TPT, kFromSmem, STORE>::run(s, lt, W, io);
@@ -193,6 +217,30 @@ template <typename C, int M, int TPT, int LOAD, int STORE>
 struct FFTPasses<C, M, M, TPT, LOAD, STORE> {
   __device__ static __forceinline__ void run(C*, int, const C*, const ChirpIO<C>&) {}
 };
+
+// The radix-2 first pass (SPAN 1, no twiddles) in shared memory: y[2i] = x[i] + x[i + M/2],
+// y[2i + 1] = x[i] - x[i + M/2].  (Fusing the filter product into this pass, or into the previous
+// pass's stores, keeps 16 more values in flight and spills at the 64-register budget.)
+template <typename C, int M, int TPT>
+__device__ __forceinline__ void radix2_first(C* s, int lt) {
+  constexpr int ITEMS = M / 2 / TPT;
+  C v[2 * ITEMS];
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it) {
+    const int i = lt + it * TPT;
+    const C a = s[pad16(i)], b = s[pad16(i + M / 2)];
+    v[2 * it] = cadd(a, b);
+    v[2 * it + 1] = csub(a, b);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it) {
+    const int i = lt + it * TPT;
+    s[pad16(2 * i)] = v[2 * it];
+    s[pad16(2 * i + 1)] = v[2 * it + 1];
+  }
+  __syncthreads();
+}
 
 // FP32 transforms up to M = 8192 are limited to 64 registers so that two CTAs share an SM.
 template <typename R, int M>
@@ -228,15 +276,14 @@ bluestein_kernel(BatchView bv) {
   const C* W = reinterpret_cast<const C*>(d.fftw);
   C* s = buf + g * padded_len<M>();
   const ChirpIO<C> io{in, chirp, vhat, out, active ? p : 0};
-  for (int n = lt; n < io.p; n += TPT) s[pad16(n)] = cmul(in[n], __ldg(chirp + n));
+  for (int n = lt; n < io.p; n += TPT) s[pad16(n)] = cmul(__ldg(in + n), __ldg(chirp + n));
   __syncthreads();
-  FFTPasses<C, M, 1, TPT, kFromInput, kToSmem>::run(s, lt, W, io);
+  FFTPasses<C, M, 2, TPT, kFromInput, kToSmem>::run(s, lt, W, io);
   for (int n = lt; n < M; n += TPT) s[pad16(n)] = cconj(cmul(s[pad16(n)], __ldg(vhat + n)));
   __syncthreads();
-  FFTPasses<C, M, 1, TPT, kFromSmem, kToSmem>::run(s, lt, W, io);
-  for (int c = lt; c < io.p; c += TPT) out[c] = cmul(cconj(s[pad16(c)]), __ldg(chirp + c));
+  radix2_first<C, M, TPT>(s, lt);
+  FFTPasses<C, M, 2, TPT, kFromSmem, kToOutput>::run(s, lt, W, io);
 }
-
 template <int M> constexpr int log2_of() { return M <= 1 ? 0 : 1 + log2_of<M / 2>(); }
 
 template <typename R, int M>
@@ -316,13 +363,28 @@ std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
 int g_noalloc_n[kMaxDevices];           // length the tables currently hold (0 = none)
 
-// Twiddles e^{-2 pi i m / M}, the chirp w_k = e^{-pi i (k^2 mod 2n) / n} (k < n) and the wrapped
-// conjugate chirp V (V[k] = V[M - k] = conj(w_k), zero elsewhere), in FP64 then rounded.
+// Twiddles in the per-pass layout of the chirp convolution's FFT (entry e^{-2 pi i b k / (SPAN R)}
+// of the pass at SPAN, row log2 b, column k), the chirp w_k = e^{-pi i (k^2 mod 2n) / n} (k < n)
+// and the wrapped conjugate chirp V (V[k] = V[M - k] = conj(w_k), zero elsewhere), in FP64 then
+// rounded.
 __global__ void noalloc_tables_kernel(int n, int M, float2* chirp, float2* V, float2* W) {
+  const int entries = fft_tw_entries(M);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
     double s, c;
-    sincospi(-2.0 * (double)i / (double)M, &s, &c);
-    W[i] = make_float2((float)c, (float)s);
+    if (i < entries) {
+      int span = 2, off = 0;
+      while (true) {
+        const int R = fft_radix(M, span), rows = fft_log2(R);
+        if (i < off + rows * span) {
+          const int row = (i - off) / span, k = (i - off) - row * span;
+          sincospi(-2.0 * (double)((1 << row) * k) / (double)(span * R), &s, &c);
+          W[i] = make_float2((float)c, (float)s);
+          break;
+        }
+        off += rows * span;
+        span *= R;
+      }
+    }
     int k = -1;
     if (i < n) k = i;
     else if (i > M - n) k = M - i;
@@ -347,7 +409,8 @@ __global__ void __launch_bounds__(M / 16) noalloc_filter_kernel(int n, float2* V
   for (int i = lt; i < M; i += TPT) s[pad16(i)] = V[i];
   __syncthreads();
   const ChirpIO<float2> io{nullptr, nullptr, nullptr, nullptr, 0};
-  FFTPasses<float2, M, 1, TPT, kFromSmem, kToSmem>::run(s, lt, W, io);
+  radix2_first<float2, M, TPT>(s, lt);
+  FFTPasses<float2, M, 2, TPT, kFromSmem, kToSmem>::run(s, lt, W, io);
   const float scale = (float)(1.0 / ((double)M * (double)n));
   for (int i = lt; i < M; i += TPT) V[i] = cscale(s[pad16(i)], scale);
 }

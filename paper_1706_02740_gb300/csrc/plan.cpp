@@ -315,8 +315,13 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
     put<cd>(blob, o_wp, wp, false);
   }
   {
-    std::vector<cd> fw(M);
-    for (int n = 0; n < M; ++n) fw[n] = expi_turns(-n, M);
+    std::vector<cd> fw(M, cd(1, 0));
+    for (int span = 2; span < M; span *= fft_radix(M, span)) {
+      const int R = fft_radix(M, span), base = fft_tw_offset(M, span);
+      for (int row = 0; (1 << row) < R; ++row)
+        for (int k = 0; k < span; ++k)
+          fw[(size_t)base + (size_t)row * span + k] = expi_turns(-(int64_t)(1 << row) * k, (int64_t)span * R);
+    }
     put<cd>(blob, o_fftw, fw, fp64);
     std::vector<cd> ts(std::max(tw, 1), cd(1, 0));
     for (int l = 0; l < nT; ++l)

@@ -69,7 +69,7 @@ struct DevPlan {
   const void* Ttab;           // [nq][2 kappa + 1] exp(-2 pi i (q i mod N) / N)   (prec type)
   const void* chirp;          // [K][pmax] exp(-pi i (n^2 mod 2p) / p)           (prec type)
   const void* vhat;           // [K][fftM] FFT of the conjugate chirp / (M p)    (prec type)
-  const void* fftw;           // [fftM] exp(-2 pi i n / M)                        (prec type)
+  const void* fftw;           // [fftM] per-pass FFT twiddles (fft_tw_offset)     (prec type)
   const void* twsmall;        // [sum_l t_l] exp(-2 pi i n / t_l)                (prec type)
   const float2* wp32;         // [K][pmax] exp(-2 pi i n / p_j) for the FP32 re-estimation
   const int32_t* garner;      // [K][nT] (p_j t_1 .. t_{l-1})^{-1} mod t_l
@@ -169,6 +169,20 @@ struct LaunchSet {
   const int32_t* blk[kStCount];
   int32_t pmax;               // largest prime over the signals (shared-memory sizing)
 };
+
+// Twiddle tables of the chirp convolution's power-of-two FFT of length M.  After its radix-2 first
+// pass (no twiddles) the passes run at sub-transform lengths SPAN = 2, 2 R_1, ... with radix
+// R = fft_radix(M, SPAN) = min(16, M / SPAN), until SPAN = M.  The pass at SPAN owns log2(R) rows of
+// SPAN entries: row t, column k holds e^{-2 pi i 2^t k / (SPAN R)}.  The rows of all passes are
+// stored one after the other (fft_tw_offset); together they hold fewer than M entries.
+__host__ __device__ constexpr int fft_radix(int M, int span) { return (M / span) >= 16 ? 16 : (M / span); }
+__host__ __device__ constexpr int fft_log2(int x) { return x <= 1 ? 0 : 1 + fft_log2(x / 2); }
+__host__ __device__ constexpr int fft_tw_offset(int M, int span) {
+  int off = 0;
+  for (int s = 2; s < span; s *= fft_radix(M, s)) off += fft_log2(fft_radix(M, s)) * s;
+  return off;
+}
+__host__ __device__ constexpr int fft_tw_entries(int M) { return fft_tw_offset(M, M); }
 
 int bluestein_blocks(const DevPlan& d, int M);   // chirp-convolution blocks of one signal (length M)
 int rank_blocks(const DevPlan& d, int kind);     // blocks of the rank fallbacks (0 when not needed)
