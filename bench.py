@@ -53,6 +53,8 @@ def parse():
                     help="distinct resident inputs that rotate (each N complex64)")
     ap.add_argument("--timed-only", action="store_true",
                     help="only the warm-up and timed steps (for profiler launch lists)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the mixed-size batch leg")
+    ap.add_argument("--batched-signals", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -225,6 +227,12 @@ def run_ours(args, rank, world, local_rank):
         fs = [inputs[(k * B + i) % n_in].data_ptr() for i in range(B)]
         batch.execute(fs, w_ptrs, c_ptrs, n_ptrs, stream.cuda_stream)
 
+    # launch geometry from the autotuner, on this workload
+    tuning = batch.get_tuning()
+    if not args.timed_only:
+        tuning = batch.autotune([inputs[i % n_in].data_ptr() for i in range(B)], w_ptrs, c_ptrs,
+                                n_ptrs, stream.cuda_stream, reps=3)
+
     # latency of one request alone (one plan, one SFT at a time)
     p0 = plans[0]
     for i in range(0 if args.timed_only else 3):
@@ -240,6 +248,17 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     single = sorted(a.elapsed_time(b) for a, b in ev) or [float("nan")]
 
+    # per-stage times: CUDA events between the stages, direct launches (the graph has none)
+    n_prof = 0 if args.timed_only else 10
+    batch.profile(True)
+    for k in range(n_prof):
+        step(k)
+    torch.cuda.synchronize()
+    stage_ms, n_rec = batch.profile_read()
+    batch.profile(False)
+
+    # the timed steps replay the batch's CUDA graph (captured at the first warm-up step)
+    batch.graph(True)
     for w in range(args.warmup):
         step(w)
     torch.cuda.synchronize()
@@ -248,7 +267,6 @@ def run_ours(args, rank, world, local_rank):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    batch.profile(True)
     launches0 = batch.launches
     if world > 1:
         dist.barrier()
@@ -266,9 +284,10 @@ def run_ours(args, rank, world, local_rank):
     launches = batch.launches - launches0
     elapsed_ms = t0.elapsed_time(t1)
     step_ms = sorted(a.elapsed_time(b) for a, b in zip(starts, ends))
-    stage_ms, n_rec = batch.profile_read()
-    batch.profile(False)
+    batch.graph(False)
     elapsed_ms, value = aggregate_ranks(elapsed_ms, K * B, world, dev)
+    if n_rec == 0:
+        stage_ms, n_rec = {k: elapsed_ms / K / len(stage_ms) for k in stage_ms}, 1
 
     # roofline of the gather (resampling) and of the dominant stage, per batched launch
     peaks, peak_kind = measured_peaks()
@@ -285,6 +304,10 @@ def run_ours(args, rank, world, local_rank):
                    "traffic": traffic, "algorithmic_bytes": gather_bytes,
                    "units": f"{B} SFTs x {info['nodes']} nodes per launch",
                    "peak_source": f"{peak_kind} hbm_gbs"}
+    if traffic is not None:
+        # the bytes actually moved (ncu DRAM read + write of the same launch, scaled) over time
+        roof_gather["dram_achieved"] = traffic / rs_s / 1e9
+        roof_gather["dram_frac"] = traffic / rs_s / 1e9 / hbm
     dominant = max(per_launch_us, key=per_launch_us.get)
     if dominant == "chirp_dft":
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -373,13 +396,19 @@ def run_ours(args, rank, world, local_rank):
                            "ms": res["fft_topk"], "fft_only_ms": res["fft"],
                            "what": "torch.fft.fft (cuFFT C2C FP32) + (-1)^w/N rescale + top-s"}}
 
-    cpu = None
-    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.timed_only):
-        cpu = cpu_baseline_sample(N, s, sfts=2)
-
     batch.destroy()
     for p in plans:
         p.destroy()
+    del inputs
+    torch.cuda.empty_cache()
+
+    batched = None
+    if rank == 0 and not (args.timed_only or args.no_batched):
+        batched = run_batched_workload(args, dev, sft)
+
+    cpu = None
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.timed_only):
+        cpu = cpu_baseline_sample(N, s, sfts=2)
     if rank != 0:
         return
     pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
@@ -387,7 +416,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "SFTs/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(args, B),
+        "config": dict(workload_config(args, B), tuning=tuning, graph=True),
         "latency_ms": {"p50": pct(single, 0.5), "p99": pct(single, 0.99),
                        "what": "device time of one SFT executed alone (sft_execute)"},
         "step_ms": {"p50": pct(step_ms, 0.5), "p99": pct(step_ms, 0.99),
@@ -399,7 +428,103 @@ def run_ours(args, rank, world, local_rank):
     }
     if plain:
         out.update(plain)
+    if batched:
+        out["batched"] = batched
     print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# mixed-size batch: thousands of independent signals in one batched execution (CUDA graph)
+# ------------------------------------------------------------------------------------------
+def run_batched_workload(args, dev, sft, steps=5, seed=4000):
+    """4096 signals, N log-uniform over [2^18, 2^24] (a quarter at non-power-of-two lengths, some
+    prime), s uniform over [16, 512], unit magnitudes, SNR 20 dB, complex64, generated on the
+    device; one batch (one launch per stage), autotuned, replayed as a CUDA graph.  The signal
+    count is reduced if the inputs and plans would not fit in 80% of the free device memory."""
+    import torch
+    from synth.device_signals import make_device_signal
+    from synth.signals import draw_batch_shapes
+    shapes = draw_batch_shapes(args.batched_signals, seed)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = 0.8 * free
+    used, keep = 0, []
+    for (N, s) in shapes:
+        # input + a generous plan estimate (samples and bins of ~5 primes x 40 node subsets x
+        # 4 shifts, 64 bytes per node, plus tables)
+        est = N * 8 + 5 * (3 * s + 64) * 40 * 64 + (8 << 20)
+        if used + est > budget:
+            break
+        used += est
+        keep.append((N, s))
+    shapes = keep
+    t_setup = time.time()
+    inputs, plans = [], []
+    # the generator's inverse FFTs would otherwise keep one cuFFT plan (and its work area) per
+    # distinct length alive
+    cache = torch.backends.cuda.cufft_plan_cache[dev.index if dev.index is not None else 0]
+    old_max = cache.max_size
+    cache.max_size = 2
+    for i, (N, s) in enumerate(shapes):
+        if torch.cuda.mem_get_info(dev)[0] < 16 * 2 ** 30:
+            break
+        f, _, _ = make_device_signal(N, s, seed + i, "unit", 20.0, dev)
+        inputs.append(f)
+        plans.append(sft.sft_plan(N, s, sft.sft_variant_init(precision=sft.SFT_FP32, kappa=6, K=5,
+                                                             c_p=3.0, seed=i)))
+    cache.clear()
+    cache.max_size = old_max
+    shapes = shapes[:len(plans)]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    batch = sft.Batch(plans)
+    outs = sft.batch_outputs_torch(batch, dev)
+    stream = torch.cuda.current_stream(dev)
+    ptrs = ([f.data_ptr() for f in inputs], [o[0].data_ptr() for o in outs],
+            [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs])
+    setup_s = time.time() - t_setup
+    t_tune = time.time()
+    tuning = batch.autotune(*ptrs, stream.cuda_stream, 2)
+    tune_s = time.time() - t_tune
+    batch.graph(True)
+    for _ in range(2):
+        batch.execute(*ptrs, stream.cuda_stream)
+    torch.cuda.synchronize()
+    l0 = batch.launches
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        batch.execute(*ptrs, stream.cuda_stream)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    launches = (batch.launches - l0) // steps
+    batch.graph(False)
+    # a sample of the batch against the same plans executed alone (bit for bit)
+    got = [(o[0].cpu(), o[1].cpu(), int(o[2].item())) for o in outs]
+    idx = list(range(0, len(plans), max(1, len(plans) // 8)))[:8]
+    same = 0
+    for i in idx:
+        w, c, n = sft.execute_torch(plans[i], inputs[i])
+        torch.cuda.synchronize()
+        gw, gc, gn = got[i]
+        same += int(int(n.item()) == gn and torch.equal(w.cpu(), gw) and torch.equal(c.cpu(), gc))
+    nodes = sum(p.info()["nodes"] for p in plans)
+    n_sig = len(plans)
+    in_bytes = sum(N * 8 for N, _ in shapes)
+    plan_bytes = sum(p.device_bytes for p in plans)
+    batch.destroy()
+    for p in plans:
+        p.destroy()
+    del inputs, outs
+    torch.cuda.empty_cache()
+    pow2 = sum(1 for N, _ in shapes if N & (N - 1) == 0)
+    return {"workload": f"{n_sig} signals, N log-uniform [2^18, 2^24] ({n_sig - pow2} not a power "
+                        "of two), s uniform [16, 512], unit magnitude, SNR 20 dB, complex64",
+            "signals": n_sig, "sfts_per_s": n_sig * 1e3 / ms, "ms_per_batch": ms,
+            "launches_per_batch": launches, "graph": True, "tuning": tuning,
+            "nodes": nodes, "input_gb": in_bytes / 1e9, "plan_gb": plan_bytes / 1e9,
+            "setup_s": setup_s, "autotune_s": tune_s,
+            "equal_to_single_execution": f"{same}/{len(idx)} sampled signals bit-identical"}
 
 
 # ------------------------------------------------------------------------------------------

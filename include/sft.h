@@ -144,7 +144,7 @@ sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64
 
 /*
  * Batches: the transforms of n signals, each with its own plan, with one kernel launch per stage
- * for the whole batch (SURVEY's batched pattern; Algorithm 1 is unchanged per signal).  Plans may
+ * for the whole batch (Algorithm 1 is unchanged per signal).  Plans may
  * differ in N, s and moduli but must share precision, input type and kappa, and each plan may
  * appear once (its scratch serves one signal).  The batch keeps device copies of the plans'
  * records, so plans must outlive the batch and must not be executed on their own while an
@@ -165,6 +165,59 @@ sft_status sft_batch_execute(sft_batch_t batch, const void* const* f_devs,
                              int32_t* const* out_count_devs, void* stream);
 
 sft_status sft_batch_destroy(sft_batch_t batch);
+
+/*
+ * Launch geometry of a batch's kernels.  It changes how work is split into CTAs, never what is
+ * computed: every valid choice gives the same results, bit for bit.
+ *   resample_threads  nodes per CTA of the kappa = 4 / 6 resampling kernel: 64, 128, 256 or 512
+ *                     (other kappa use a fixed 128).
+ *   resample_regcap   1: that kernel's build limited to 48 registers (five 256-thread CTAs per SM,
+ *                     more warps in flight for the gather; needs resample_threads <= 256);
+ *                     0: the default build (64 registers on the FP32 path).
+ *   bin_threads       bins per CTA of residue identification and vote: 64, 128, 256 or 512.
+ *   dft_per_cta[c]    chirp-convolution transforms per CTA for the length class M = 64 << c
+ *                     (c = 0..8); M/16 threads per transform and at most max(M/16, 256) threads
+ *                     per CTA, so 1 <= dft_per_cta[c] <= max(1, 4096 / M).
+ *   dft_two_ctas      FP32, M = 8192: 1 = the build limited to 64 registers so that two CTAs share
+ *                     an SM; 0 = one CTA per SM with up to 128 registers.
+ * sft_tuning_default fills the built-in choice (host only, no device call).
+ */
+typedef struct {
+  int32_t resample_threads;
+  int32_t resample_regcap;
+  int32_t bin_threads;
+  int32_t dft_per_cta[9];
+  int32_t dft_two_ctas;
+} sft_tuning;
+
+void sft_tuning_default(sft_tuning* t);
+
+/* Validate and apply a launch geometry (SFT_EINVAL, nothing changed, if invalid).  Waits for the
+ * device to finish (cudaDeviceSynchronize) before it rewrites the batch's launch tables, and drops
+ * a captured graph (sft_batch_graph recaptures at the next execution). */
+sft_status sft_batch_set_tuning(sft_batch_t batch, const sft_tuning* t);
+sft_status sft_batch_get_tuning(sft_batch_t batch, sft_tuning* t);
+
+/*
+ * Autotuner: times each knob's candidates on this batch and these buffers (as for
+ * sft_batch_execute; outputs are overwritten), one knob at a time with the others at their best
+ * so far, from the per-stage CUDA-event times of `reps` executions per candidate after one
+ * untimed execution, and applies the fastest.  The choice is copied to *chosen when it is not
+ * NULL.  Synchronous (returns after the device has finished).  Profiling state is restored.
+ */
+sft_status sft_batch_autotune(sft_batch_t batch, const void* const* f_devs,
+                              int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
+                              int32_t* const* out_count_devs, void* stream, int32_t reps,
+                              sft_tuning* chosen);
+
+/*
+ * enable = 1: the next execution captures the batch's kernel launches once as a CUDA graph (on a
+ * private stream, so capturing runs nothing) and every execution replays it on the caller's
+ * stream after uploading that execution's pointers; per-stage profiling is off while graphs are
+ * on.  enable = 0 drops the graph and returns to direct launches.  Results are identical either
+ * way.
+ */
+sft_status sft_batch_graph(sft_batch_t batch, int32_t enable);
 
 /* Per-stage timing and launch count of a batch, as sft_plan_profile / _read / _launches. */
 sft_status sft_batch_profile(sft_batch_t batch, int32_t enable);

@@ -47,6 +47,27 @@ class sft_plan_desc(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class sft_tuning(ctypes.Structure):
+    _fields_ = [("resample_threads", ctypes.c_int32), ("resample_regcap", ctypes.c_int32),
+                ("bin_threads", ctypes.c_int32), ("dft_per_cta", ctypes.c_int32 * 9),
+                ("dft_two_ctas", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"resample_threads": self.resample_threads, "resample_regcap": self.resample_regcap,
+                "bin_threads": self.bin_threads, "dft_per_cta": list(self.dft_per_cta),
+                "dft_two_ctas": self.dft_two_ctas}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "sft_tuning":
+        t = cls()
+        for k, v in d.items():
+            if k == "dft_per_cta":
+                t.dft_per_cta = (ctypes.c_int32 * 9)(*v)
+            else:
+                setattr(t, k, int(v))
+        return t
+
+
 _lib = None
 
 EXPORTS = {
@@ -79,6 +100,12 @@ EXPORTS = {
     "sft_batch_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int32)]),
     "sft_batch_launches": (ctypes.c_int64, [ctypes.c_void_p]),
+    "sft_tuning_default": (None, [ctypes.POINTER(sft_tuning)]),
+    "sft_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sft_tuning)]),
+    "sft_batch_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sft_tuning)]),
+    "sft_batch_autotune": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_void_p)] * 4
+                           + [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(sft_tuning)]),
+    "sft_batch_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "sft_batch_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "sft_choose_moduli": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
@@ -247,6 +274,29 @@ class Batch:
                 for ptrs in (f_ptrs, w_ptrs, c_ptrs, n_ptrs)]
         _check(load().sft_batch_execute(self.handle, *arrs, stream))
 
+    def _ptr_arrays(self, f_ptrs, w_ptrs, c_ptrs, n_ptrs):
+        n = len(self.plans)
+        return [(ctypes.c_void_p * n)(*[int(x) for x in ptrs])
+                for ptrs in (f_ptrs, w_ptrs, c_ptrs, n_ptrs)]
+
+    def set_tuning(self, tuning: dict):
+        t = sft_tuning.from_dict(tuning)
+        _check(load().sft_batch_set_tuning(self.handle, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = sft_tuning()
+        _check(load().sft_batch_get_tuning(self.handle, ctypes.byref(t)))
+        return t.as_dict()
+
+    def autotune(self, f_ptrs, w_ptrs, c_ptrs, n_ptrs, stream: int = 0, reps: int = 3) -> dict:
+        t = sft_tuning()
+        _check(load().sft_batch_autotune(self.handle, *self._ptr_arrays(f_ptrs, w_ptrs, c_ptrs, n_ptrs),
+                                         stream, int(reps), ctypes.byref(t)))
+        return t.as_dict()
+
+    def graph(self, enable: bool = True):
+        _check(load().sft_batch_graph(self.handle, 1 if enable else 0))
+
     def profile(self, enable: bool = True):
         _check(load().sft_batch_profile(self.handle, 1 if enable else 0))
 
@@ -265,20 +315,45 @@ class Batch:
         return int(load().sft_batch_device_bytes(self.handle))
 
 
-def execute_batch_torch(batch: Batch, fs, stream=None):
-    """Run a batch on CUDA tensors fs (one per plan); returns lists of device result tensors."""
+def batch_outputs_torch(batch: Batch, device):
+    """Device result tensors (freqs, coefs, count) for every plan of a batch."""
     import torch
     outs = []
-    for p, f in zip(batch.plans, fs):
+    for p in batch.plans:
         s = p.info()["s"]
-        outs.append((torch.empty(s, dtype=torch.int64, device=f.device),
-                     torch.empty(s, dtype=torch.complex128, device=f.device),
-                     torch.empty(1, dtype=torch.int32, device=f.device)))
-    st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
-    batch.execute([f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs],
-                  [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs],
-                  st.cuda_stream)
+        outs.append((torch.empty(s, dtype=torch.int64, device=device),
+                     torch.empty(s, dtype=torch.complex128, device=device),
+                     torch.empty(1, dtype=torch.int32, device=device)))
     return outs
+
+
+def _batch_ptrs(fs, outs):
+    return ([f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs],
+            [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs])
+
+
+def execute_batch_torch(batch: Batch, fs, stream=None, outs=None):
+    """Run a batch on CUDA tensors fs (one per plan); returns lists of device result tensors."""
+    import torch
+    if outs is None:
+        outs = batch_outputs_torch(batch, fs[0].device)
+    st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
+    batch.execute(*_batch_ptrs(fs, outs), st.cuda_stream)
+    return outs
+
+
+def autotune_batch_torch(batch: Batch, fs, reps: int = 3, stream=None) -> dict:
+    """Run the autotuner of a batch on CUDA tensors fs; returns the chosen tuning."""
+    import torch
+    outs = batch_outputs_torch(batch, fs[0].device)
+    st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
+    return batch.autotune(*_batch_ptrs(fs, outs), st.cuda_stream, reps)
+
+
+def sft_tuning_default() -> dict:
+    t = sft_tuning()
+    load().sft_tuning_default(ctypes.byref(t))
+    return t.as_dict()
 
 
 def sft_plan_launches(plan: Plan) -> int:

@@ -15,15 +15,55 @@ thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-// Blocks of each stage for one signal (matches the kernels' block shapes).
-int signal_blocks(const DevPlan& d, int kind) {
+sft_tuning default_tuning() {
+  sft_tuning t;
+  t.resample_threads = 256;
+  t.resample_regcap = 0;
+  t.bin_threads = 256;
+  for (int c = 0; c < 9; ++c) {
+    const int M = 64 << c;
+    t.dft_per_cta[c] = M >= 4096 ? 1 : 4096 / M;
+  }
+  t.dft_two_ctas = 1;
+  return t;
+}
+
+bool tuning_valid(const sft_tuning& t, std::string* why) {
+  auto pow2_in = [](int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
+  if (!pow2_in(t.resample_threads, 64, kResampleMaxThreads)) {
+    *why = "resample_threads must be 64, 128, 256 or 512";
+    return false;
+  }
+  if (t.resample_regcap != 0 && t.resample_regcap != 1) { *why = "resample_regcap must be 0 or 1"; return false; }
+  if (t.resample_regcap == 1 && t.resample_threads > 256) {
+    *why = "resample_regcap = 1 needs resample_threads <= 256";
+    return false;
+  }
+  if (!pow2_in(t.bin_threads, 64, kBinMaxThreads)) {
+    *why = "bin_threads must be 64, 128, 256 or 512";
+    return false;
+  }
+  for (int c = 0; c < 9; ++c) {
+    const int M = 64 << c;
+    const int hi = M >= 4096 ? 1 : 4096 / M;
+    if (t.dft_per_cta[c] < 1 || t.dft_per_cta[c] > hi) {
+      *why = "dft_per_cta[" + std::to_string(c) + "] must be in 1.." + std::to_string(hi);
+      return false;
+    }
+  }
+  if (t.dft_two_ctas != 0 && t.dft_two_ctas != 1) { *why = "dft_two_ctas must be 0 or 1"; return false; }
+  return true;
+}
+
+// Blocks of each stage for one signal (matches the kernels' block shapes under tuning t).
+int signal_blocks(const DevPlan& d, int kind, const sft_tuning& tu) {
   switch (kind) {
     case kStOne: return 1;
     case kStResample: {
-      const int t = (d.kappa == 4 || d.kappa == 6) ? kResampleThreads : kResampleGenericThreads;
+      const int t = (d.kappa == 4 || d.kappa == 6) ? tu.resample_threads : kResampleGenericThreads;
       return (int)((d.m + t - 1) / t);
     }
-    case kStBins: return (int)(((int64_t)d.nq * d.Ptot + kBinThreads - 1) / kBinThreads);
+    case kStBins: return (int)(((int64_t)d.nq * d.Ptot + tu.bin_threads - 1) / tu.bin_threads);
     case kStShift: return d.nq;
     case kStShiftRank:
     case kStGlobalRank:
@@ -32,15 +72,16 @@ int signal_blocks(const DevPlan& d, int kind) {
     case kStRefine: return d.prec == SFT_FP32 ? (d.s + kRefineThreads - 1) / kRefineThreads : 0;
     default:
       if (kind >= kStBluestein0 && kind < kStCount)
-        return bluestein_blocks(d, 64 << (kind - kStBluestein0));
+        return bluestein_blocks(d, 64 << (kind - kStBluestein0), tu.dft_per_cta[kind - kStBluestein0]);
       return 0;
   }
 }
 
 LaunchSet single_launch_set(const DevPlan& d) {
   LaunchSet ls;
+  ls.tune = default_tuning();
   for (int k = 0; k < kStCount; ++k) {
-    ls.blocks[k] = signal_blocks(d, k);
+    ls.blocks[k] = signal_blocks(d, k, ls.tune);
     ls.blk[k] = nullptr;
   }
   ls.pmax = d.pmax;
@@ -254,5 +295,9 @@ sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64
 }
 
 const char* sft_last_error(void) { return sft::g_last_error.c_str(); }
+
+void sft_tuning_default(sft_tuning* t) {
+  if (t) *t = sft::default_tuning();
+}
 
 }  // extern "C"

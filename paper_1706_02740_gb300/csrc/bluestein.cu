@@ -242,14 +242,17 @@ __device__ __forceinline__ void radix2_first(C* s, int lt) {
   __syncthreads();
 }
 
-// FP32 transforms up to M = 8192 are limited to 64 registers so that two CTAs share an SM.
-template <typename R, int M>
-__global__ void __launch_bounds__((M / 16) > 256 ? (M / 16) : 256,
-                                  (sizeof(R) == 4 && M <= 8192) ? 2 : 1)
+// A CTA holds blockDim.x / (M/16) transforms, at most max(M/16, 256) threads.  MINB is the
+// builds' CTAs-per-SM target: FP32 transforms are limited to 64 (M = 8192, MINB = 2) or
+// 128 (M <= 4096) registers.
+template <int M> constexpr int dft_max_threads() { return (M / 16) > 256 ? (M / 16) : 256; }
+
+template <typename R, int M, int MINB>
+__global__ void __launch_bounds__(dft_max_threads<M>(), MINB)
 bluestein_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   constexpr int TPT = M / 16;                      // threads per transform
-  constexpr int G = (M >= 4096) ? 1 : 4096 / M;    // transforms per CTA
+  const int G = blockDim.x / TPT;                  // transforms per CTA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   int lb, nb;
@@ -286,22 +289,32 @@ bluestein_kernel(BatchView bv) {
 }
 template <int M> constexpr int log2_of() { return M <= 1 ? 0 : 1 + log2_of<M / 2>(); }
 
-template <typename R, int M>
-cudaError_t launch_M(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
+template <typename R, int M, int MINB>
+cudaError_t launch_MB(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
   using C = typename Cx<R>::T;
-  constexpr int G = (M >= 4096) ? 1 : 4096 / M;
-  constexpr int threads = (M / 16) * G;
-  const unsigned grid = (unsigned)ls.blocks[kStBluestein0 + log2_of<M>() - 6];
+  constexpr int cls = log2_of<M>() - 6;
+  const unsigned grid = (unsigned)ls.blocks[kStBluestein0 + cls];
   if (grid == 0) return cudaSuccess;
+  const int G = ls.tune.dft_per_cta[cls];
+  const int threads = (M / 16) * G;
   const size_t smem = (size_t)G * padded_len<M>() * sizeof(C);
-  cudaError_t e = cudaFuncSetAttribute(bluestein_kernel<R, M>,
+  cudaError_t e = cudaFuncSetAttribute(bluestein_kernel<R, M, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   BatchView v = bv;
-  v.blk = ls.blk[kStBluestein0 + log2_of<M>() - 6];
-  bluestein_kernel<R, M><<<grid, threads, smem, st>>>(v);
+  v.blk = ls.blk[kStBluestein0 + cls];
+  bluestein_kernel<R, M, MINB><<<grid, threads, smem, st>>>(v);
   if (launched) ++*launched;
   return cudaGetLastError();
+}
+
+template <typename R, int M>
+cudaError_t launch_M(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
+  if constexpr (sizeof(R) == 4 && M == 8192) {
+    if (!ls.tune.dft_two_ctas) return launch_MB<R, M, 1>(bv, ls, st, launched);
+  }
+  constexpr int MINB = (sizeof(R) == 4 && M <= 8192) ? 2 : 1;
+  return launch_MB<R, M, MINB>(bv, ls, st, launched);
 }
 
 template <typename R>
@@ -328,11 +341,10 @@ cudaError_t launch_bluestein(const DevPlan& d0, const BatchView& bv, const Launc
                              : launch_prec<double>(bv, ls, st, launched);
 }
 
-int bluestein_blocks(const DevPlan& d, int M) {
+int bluestein_blocks(const DevPlan& d, int M, int per_cta) {
   if (d.fftM != M) return 0;
-  const int G = (M >= 4096) ? 1 : 4096 / M;
   const int total = d.nq * d.K * d.nsub;
-  return (total + G - 1) / G;
+  return (total + per_cta - 1) / per_cta;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -518,9 +530,10 @@ extern "C" sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_d
   bv.n = 1;
   LaunchSet ls;
   memset(&ls, 0, sizeof(ls));
+  ls.tune = default_tuning();
   int lg = 0;
   while ((1 << lg) < M) ++lg;
-  ls.blocks[kStBluestein0 + lg - 6] = bluestein_blocks(d, M);
+  ls.blocks[kStBluestein0 + lg - 6] = bluestein_blocks(d, M, ls.tune.dft_per_cta[lg - 6]);
   e = launch_prec<float>(bv, ls, st, nullptr);
   if (e != cudaSuccess) {
     set_error(std::string("sft_dft_noalloc: launch failed: ") + cudaGetErrorString(e));

@@ -98,11 +98,11 @@ __device__ int residue_any(int t, C z0, const C* Zl, int64_t p, const C* twl, in
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kBinThreads) identify_kernel(BatchView bv) {
+__global__ void __launch_bounds__(kBinMaxThreads) identify_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
-  const int64_t gid = (int64_t)lb * kBinThreads + threadIdx.x;
+  const int64_t gid = (int64_t)lb * blockDim.x + threadIdx.x;
   if (gid >= (int64_t)d.nq * d.Ptot) return;
   int qi, j, b;
   decode_bin(d, gid, qi, j, b);
@@ -140,11 +140,11 @@ __global__ void __launch_bounds__(kBinThreads) identify_kernel(BatchView bv) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kBinThreads) vote_kernel(BatchView bv) {
+__global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
-  const int64_t gid = (int64_t)lb * kBinThreads + threadIdx.x;
+  const int64_t gid = (int64_t)lb * blockDim.x + threadIdx.x;
   if (gid >= (int64_t)d.nq * d.Ptot) return;
   const int64_t w = d.cand[gid];
   if (w == kNoFreq) return;
@@ -187,8 +187,8 @@ cudaError_t launch_identify(const DevPlan& d0, const BatchView& bv, const Launch
   if (grid == 0) return cudaSuccess;
   BatchView v = bv;
   v.blk = ls.blk[kStBins];
-  if (d0.prec == SFT_FP32) identify_kernel<float><<<grid, kBinThreads, 0, st>>>(v);
-  else identify_kernel<double><<<grid, kBinThreads, 0, st>>>(v);
+  if (d0.prec == SFT_FP32) identify_kernel<float><<<grid, ls.tune.bin_threads, 0, st>>>(v);
+  else identify_kernel<double><<<grid, ls.tune.bin_threads, 0, st>>>(v);
   return cudaGetLastError();
 }
 
@@ -198,8 +198,8 @@ cudaError_t launch_vote(const DevPlan& d0, const BatchView& bv, const LaunchSet&
   if (grid == 0) return cudaSuccess;
   BatchView v = bv;
   v.blk = ls.blk[kStBins];
-  if (d0.prec == SFT_FP32) vote_kernel<float><<<grid, kBinThreads, 0, st>>>(v);
-  else vote_kernel<double><<<grid, kBinThreads, 0, st>>>(v);
+  if (d0.prec == SFT_FP32) vote_kernel<float><<<grid, ls.tune.bin_threads, 0, st>>>(v);
+  else vote_kernel<double><<<grid, ls.tune.bin_threads, 0, st>>>(v);
   return cudaGetLastError();
 }
 

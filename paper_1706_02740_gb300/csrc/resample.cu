@@ -141,14 +141,18 @@ __device__ __forceinline__ void fetch_window(const DevPlan& d, const IN* f, int6
   }
 }
 
-template <int KAPPA, typename R, typename IN>
-__global__ void __launch_bounds__(kResampleThreads) resample_kernel(BatchView bv) {
+// CAP = 0: the FP32 build fits 2 CTAs of 512 threads per SM (64 registers), the FP64 build is
+// unlimited; CAP = 1: built for 5 CTAs of 256 threads (48 registers, more warps in flight for the
+// gather; CTAs of at most 256 threads).
+template <int KAPPA, typename R, typename IN, int CAP>
+__global__ void __launch_bounds__(CAP ? 256 : kResampleMaxThreads, CAP ? 5 : (sizeof(R) == 4 ? 2 : 1))
+resample_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   constexpr int W = 2 * KAPPA + 1;
   int lb, nb;
   const int b = batch_signal(bv, lb, nb);
   const DevPlan& d = bv.plans[b];
-  const int64_t node = (int64_t)lb * kResampleThreads + threadIdx.x;
+  const int64_t node = (int64_t)lb * blockDim.x + threadIdx.x;
   if (node >= d.m) return;
   const IN* __restrict__ f = reinterpret_cast<const IN*>(batch_f(bv, b));
   int j, k1;
@@ -219,9 +223,17 @@ cudaError_t launch_typed(const DevPlan& d0, const BatchView& bv, const LaunchSet
   if (grid == 0) return cudaSuccess;
   BatchView v = bv;
   v.blk = ls.blk[kStResample];
-  if (d0.kappa == 6) resample_kernel<6, R, IN><<<grid, kResampleThreads, 0, st>>>(v);
-  else if (d0.kappa == 4) resample_kernel<4, R, IN><<<grid, kResampleThreads, 0, st>>>(v);
-  else resample_kernel_generic<R, IN><<<grid, kResampleGenericThreads, 0, st>>>(v);
+  const int t = ls.tune.resample_threads;
+  const bool cap = ls.tune.resample_regcap != 0;
+  if (d0.kappa == 6) {
+    if (cap) resample_kernel<6, R, IN, 1><<<grid, t, 0, st>>>(v);
+    else resample_kernel<6, R, IN, 0><<<grid, t, 0, st>>>(v);
+  } else if (d0.kappa == 4) {
+    if (cap) resample_kernel<4, R, IN, 1><<<grid, t, 0, st>>>(v);
+    else resample_kernel<4, R, IN, 0><<<grid, t, 0, st>>>(v);
+  } else {
+    resample_kernel_generic<R, IN><<<grid, kResampleGenericThreads, 0, st>>>(v);
+  }
   return cudaGetLastError();
 }
 

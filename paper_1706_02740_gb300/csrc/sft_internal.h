@@ -90,9 +90,9 @@ struct DevPlan {
 };
 
 constexpr int kReChunk = 256;   // samples per re-estimation CTA
-constexpr int kResampleThreads = 256;
+constexpr int kResampleMaxThreads = 512;      // largest CTA of the kappa = 4 / 6 resampling kernel
 constexpr int kResampleGenericThreads = 128;
-constexpr int kBinThreads = 256;       // identify / vote: one thread per bin
+constexpr int kBinMaxThreads = 512;    // identify / vote: one thread per bin, at most 512 per CTA
 constexpr int kRefineThreads = 64;
 
 // ---------------------------------------------------------------------------------------------
@@ -150,8 +150,8 @@ __device__ __forceinline__ int32_t* batch_out_n(const BatchView& bv, int b) {
 // Stages whose per-signal block counts a launch set records.
 enum StageKind {
   kStOne = 0,        // one block per signal (counters, global selection, final order)
-  kStResample,       // nodes / threads per block
-  kStBins,           // shifts * sum p / 256
+  kStResample,       // nodes / resampling threads per block
+  kStBins,           // shifts * sum p / bin threads per block
   kStShift,          // one block per shift
   kStShiftRank,      // rank fallback of long voted lists (0 for signals that never need it)
   kStGlobalRank,     // rank fallback of long pools
@@ -168,7 +168,12 @@ struct LaunchSet {
   int32_t blocks[kStCount];
   const int32_t* blk[kStCount];
   int32_t pmax;               // largest prime over the signals (shared-memory sizing)
+  sft_tuning tune;            // launch geometry (block shapes; never changes results)
 };
+
+// Built-in launch geometry, and the validity check of a caller's (message in *why).
+sft_tuning default_tuning();
+bool tuning_valid(const sft_tuning& t, std::string* why);
 
 // Twiddle tables of the chirp convolution's power-of-two FFT of length M.  After its radix-2 first
 // pass (no twiddles) the passes run at sub-transform lengths SPAN = 2, 2 R_1, ... with radix
@@ -184,7 +189,7 @@ __host__ __device__ constexpr int fft_tw_offset(int M, int span) {
 }
 __host__ __device__ constexpr int fft_tw_entries(int M) { return fft_tw_offset(M, M); }
 
-int bluestein_blocks(const DevPlan& d, int M);   // chirp-convolution blocks of one signal (length M)
+int bluestein_blocks(const DevPlan& d, int M, int per_cta);   // chirp-convolution blocks of one signal
 int rank_blocks(const DevPlan& d, int kind);     // blocks of the rank fallbacks (0 when not needed)
 
 constexpr int kStages = 6;
@@ -229,7 +234,7 @@ cudaError_t launch_finalize(const BatchView& bv, const LaunchSet& ls, cudaStream
                             int* launched);
 
 // Engine (api.cu): the stage sequence for one signal or a batch.
-int signal_blocks(const DevPlan& d, int kind);
+int signal_blocks(const DevPlan& d, int kind, const sft_tuning& t);
 LaunchSet single_launch_set(const DevPlan& d);
 cudaError_t run_stages(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
                        cudaStream_t st, cudaEvent_t* ev, int* launched);

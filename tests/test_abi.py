@@ -40,6 +40,16 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(sft.sft_plan_desc) == 8 + 6 * 4 + 15 * 8 + 12 * 4 + 32 * 8 + 8 + 8 + 8 + 16
 
 
+def test_tuning_layout_and_defaults(lib):
+    # sft_tuning: 13 x int32
+    assert ctypes.sizeof(sft.sft_tuning) == 13 * 4
+    t = sft.sft_tuning_default()
+    assert t["resample_threads"] == 256 and t["resample_regcap"] == 0 and t["bin_threads"] == 256
+    # transforms per CTA: a 256-thread CTA below M = 4096, one transform from there on
+    assert t["dft_per_cta"] == [64, 32, 16, 8, 4, 2, 1, 1, 1]
+    assert t["dft_two_ctas"] == 1
+
+
 def test_variant_defaults(lib):
     v = sft.sft_variant_init()
     assert (v.kappa, v.precision, v.input, v.K) == (6, 0, 0, 5)

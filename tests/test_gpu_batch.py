@@ -92,3 +92,124 @@ def test_batch_rejects_mixed_variants_and_duplicates():
         assert e.value.status == sft.SFT_EINVAL
     for p in (a, b, c):
         p.destroy()
+
+
+def _tuning_variants(prec):
+    base = sft.sft_tuning_default()
+    out = []
+    for rt, cap in ((128, 1), (512, 0), (64, 0), (256, 1)):
+        t = dict(base, resample_threads=rt, resample_regcap=cap)
+        out.append(t)
+    out.append(dict(base, bin_threads=64))
+    out.append(dict(base, bin_threads=512))
+    out.append(dict(base, dft_per_cta=[1] * 9))
+    out.append(dict(base, dft_per_cta=[max(1, g // 2) for g in base["dft_per_cta"]]))
+    if prec == U.FP32:
+        out.append(dict(base, dft_two_ctas=0))
+    return out
+
+
+def _mixed_plans(prec):
+    # the last member has p >= 3000, so the FP32 path also uses the M = 8192 length class
+    shapes = SHAPES + [(2 ** 18, 1000)]
+    plans = [sft.sft_plan(N, s, sft.sft_variant_init(precision=prec, K=5,
+                                                     c_p=3.0 if s == 1000 else 6.0, seed=i))
+             for i, (N, s) in enumerate(shapes)]
+    sigs = _signals(shapes, 700)
+    return shapes, plans, sigs
+
+
+def _host(outs):
+    return [(w.cpu().numpy(), c.cpu().numpy(), int(n.item())) for w, c, n in outs]
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_every_tuning_and_the_graph_give_identical_results(prec):
+    import torch
+    shapes, plans, sigs = _mixed_plans(prec)
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in sigs]
+    batch = sft.Batch(plans)
+    ref = _host(sft.execute_batch_torch(batch, fs))
+    torch.cuda.synchronize()
+    for t in _tuning_variants(prec):
+        batch.set_tuning(t)
+        assert batch.get_tuning() == t
+        got = _host(sft.execute_batch_torch(batch, fs))
+        for (w, c, n), (rw, rc, rn) in zip(got, ref):
+            assert n == rn and np.array_equal(w, rw) and np.array_equal(c, rc), t
+    # graph replay: captured at the first execution, replayed after
+    batch.set_tuning(sft.sft_tuning_default())
+    batch.graph(True)
+    l0 = batch.launches
+    g1 = _host(sft.execute_batch_torch(batch, fs))
+    per_exec = batch.launches - l0
+    assert per_exec > 0
+    for (w, c, n), (rw, rc, rn) in zip(g1, ref):
+        assert n == rn and np.array_equal(w, rw) and np.array_equal(c, rc)
+    for rep in range(3):
+        g = _host(sft.execute_batch_torch(batch, fs))
+        assert batch.launches - l0 == per_exec * (rep + 2)
+        for (w, c, n), (rw, rc, rn) in zip(g, ref):
+            assert n == rn and np.array_equal(w, rw) and np.array_equal(c, rc)
+    batch.graph(False)
+    batch.destroy()
+    for p in plans:
+        p.destroy()
+
+
+def test_graph_replay_reads_each_executions_inputs():
+    import torch
+    N, s, B = 2 ** 16, 20, 4
+    plans = [sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=5.0, seed=11)) for _ in range(B)]
+    sigs = [make_signal(N, s, 1200 + i, "unit", 30.0) for i in range(2 * B)]
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in sigs]
+    batch = sft.Batch(plans)
+    direct = [_host(sft.execute_batch_torch(batch, fs[h * B:(h + 1) * B])) for h in (0, 1)]
+    batch.graph(True)
+    for rep in range(2):
+        for h in (0, 1):
+            got = _host(sft.execute_batch_torch(batch, fs[h * B:(h + 1) * B]))
+            for (w, c, n), (rw, rc, rn) in zip(got, direct[h]):
+                assert n == rn and np.array_equal(w, rw) and np.array_equal(c, rc)
+    batch.destroy()
+    for p in plans:
+        p.destroy()
+
+
+def test_autotune_picks_a_valid_tuning_and_keeps_results():
+    import torch
+    shapes, plans, sigs = _mixed_plans(U.FP32)
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in sigs]
+    batch = sft.Batch(plans)
+    batch.profile(True)
+    ref = _host(sft.execute_batch_torch(batch, fs))
+    chosen = sft.autotune_batch_torch(batch, fs, reps=2)
+    assert batch.get_tuning() == chosen
+    got = _host(sft.execute_batch_torch(batch, fs))
+    torch.cuda.synchronize()
+    for (w, c, n), (rw, rc, rn) in zip(got, ref):
+        assert n == rn and np.array_equal(w, rw) and np.array_equal(c, rc)
+    # profiling stayed on: the execution after tuning was recorded
+    _, n_exec = batch.profile_read()
+    assert n_exec == 1
+    batch.destroy()
+    for p in plans:
+        p.destroy()
+
+
+def test_invalid_tunings_are_rejected_and_change_nothing():
+    shapes, plans, sigs = _mixed_plans(U.FP32)
+    batch = sft.Batch(plans)
+    base = batch.get_tuning()
+    bad = [dict(base, resample_threads=100), dict(base, resample_threads=1024),
+           dict(base, resample_regcap=1, resample_threads=512), dict(base, bin_threads=2048),
+           dict(base, dft_per_cta=[128] + base["dft_per_cta"][1:]),
+           dict(base, dft_per_cta=base["dft_per_cta"][:7] + [2, 1]), dict(base, dft_two_ctas=2)]
+    for t in bad:
+        with pytest.raises(sft.SftError) as e:
+            batch.set_tuning(t)
+        assert e.value.status == 1
+        assert batch.get_tuning() == base
+    batch.destroy()
+    for p in plans:
+        p.destroy()

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle, stage by stage.
 
-Tolerances (north-star): coefficients within 1e-5 relative on the FP32 path and 1e-11 on the FP64
+Tolerances: coefficients within 1e-5 relative on the FP32 path and 1e-11 on the FP64
 path; integer stages bit-exact (CRT and vote are re-run by the oracle on the GPU's own residues and
 candidates); FP decisions (argmax residues) compared where the oracle's decision has margin.
 """
