@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--timed-only", action="store_true",
                     help="only the warm-up and timed steps (for profiler launch lists)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-size batch leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--batched-signals", type=int, default=4096)
     return ap.parse_args()
 
@@ -126,6 +127,83 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (read-only queries) every ~2 ms from a
+    thread, for timed regions too short for nvidia-smi's sampling period.  Falls back to
+    ClockSampler when NVML cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device, off: bool = False):
+        self.dev = torch_device
+        self.off = off
+        self.samples = []
+        self.max_mhz = None
+        self.fallback = None
+        self._stop = threading.Event()
+
+    def _open(self):
+        import ctypes
+        import torch
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(self.dev)
+        bus = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                    props.pci_device_id)
+        if lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+        self.lib, self.h, self.ct = lib, h, ctypes
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+
+    def _run(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self._stop.is_set():
+            ok = self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0
+            ok2 = self.reason_fn(self.h, ct.byref(rs)) == 0
+            if ok:
+                self.samples.append((float(mhz.value), int(rs.value) if ok2 else 0))
+            time.sleep(0.002)
+
+    def __enter__(self):
+        if self.off:
+            return self
+        try:
+            self._open()
+        except (OSError, AttributeError, TypeError):
+            self.fallback = ClockSampler(self.dev.index or 0).__enter__()
+            return self
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.fallback:
+            return self.fallback.__exit__(*exc)
+        if not self.off and hasattr(self, "t"):
+            self._stop.set()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if self.fallback:
+            return self.fallback.summary()
+        sm = [m for m, _ in self.samples]
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvml"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -271,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank, off=args.timed_only) as clocks:
+    with NvmlSampler(dev, off=args.timed_only) as clocks:
         t0.record()
         for k in range(K):
             starts[k].record()
@@ -402,9 +480,11 @@ def run_ours(args, rank, world, local_rank):
     del inputs
     torch.cuda.empty_cache()
 
-    batched = None
+    batched = serving = None
     if rank == 0 and not (args.timed_only or args.no_batched):
         batched = run_batched_workload(args, dev, sft)
+    if rank == 0 and not (args.timed_only or args.no_serving):
+        serving = run_serving_workload(args, dev, sft)
 
     cpu = None
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.timed_only):
@@ -430,6 +510,8 @@ def run_ours(args, rank, world, local_rank):
         out.update(plain)
     if batched:
         out["batched"] = batched
+    if serving:
+        out["serving"] = serving
     print(json.dumps(out), flush=True)
 
 
@@ -525,6 +607,163 @@ def run_batched_workload(args, dev, sft, steps=5, seed=4000):
             "nodes": nodes, "input_gb": in_bytes / 1e9, "plan_gb": plan_bytes / 1e9,
             "setup_s": setup_s, "autotune_s": tune_s,
             "equal_to_single_execution": f"{same}/{len(idx)} sampled signals bit-identical"}
+
+
+# ------------------------------------------------------------------------------------------
+# serving: Poisson arrivals of mixed-size requests through the serving loop
+# ------------------------------------------------------------------------------------------
+def run_serving_workload(args, dev, sft, seed=5000, pool_size=32):
+    """Requests with N log-uniform over [2^16, 2^27] (arbitrary integers), s log-uniform over
+    [8, 2048], SNR uniform over [10, 40] dB, complex64, drawn from a pool of `pool_size` resident
+    signals; a server with a 16 GiB plan budget.  Capacity from a closed-loop burst, then
+    open-loop Poisson arrivals at fractions of it (p50/p99 latency, sustained SFTs/s), beside
+    the same requests one at a time on the FP64 and FP32 paths."""
+    import random
+
+    import torch
+    from synth.device_signals import make_device_signal
+    from synth.signals import draw_stream
+    pool = draw_stream(pool_size, seed, 1.0)
+    sigs = []
+    for i, (_, N, s, snr) in enumerate(pool):
+        f, _, _ = make_device_signal(N, s, seed + i, "unit", snr, dev)
+        sigs.append((N, s, f))
+    torch.backends.cuda.cufft_plan_cache[dev.index or 0].clear()
+    torch.cuda.synchronize()
+    variant = dict(precision=sft.SFT_FP32, kappa=6, K=5, c_p=3.0, seed=1)
+    srv = sft.Server(mem_budget=16 << 30, max_batch=32, max_inflight=3,
+                     variant=sft.sft_variant_init(**variant))
+    rng = random.Random(seed)
+
+    def outputs(count):
+        return [(torch.empty(2048, dtype=torch.int64, device=dev),
+                 torch.empty(2048, dtype=torch.complex128, device=dev),
+                 torch.empty(1, dtype=torch.int32, device=dev)) for _ in range(count)]
+
+    def submit(k, o):
+        N, s, f = sigs[k]
+        return srv.submit(N, s, f.data_ptr(), o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr())
+
+    # warm: every pool entry once (builds its plan)
+    o_warm = outputs(pool_size)
+    t = time.perf_counter()
+    ids = [submit(k, o_warm[k]) for k in range(pool_size)]
+    for r in ids:
+        srv.wait(r)
+    warm_s = time.perf_counter() - t
+    st_warm = srv.stats()
+    # served results equal the same plans run alone
+    same = 0
+    for k in range(0, pool_size, 4):
+        N, s, f = sigs[k]
+        p = sft.sft_plan(N, s, sft.sft_variant_init(**variant))
+        w, c, n = sft.execute_torch(p, f)
+        torch.cuda.synchronize()
+        o = o_warm[k]
+        nn = int(n.item())
+        same += int(nn == int(o[2].item()) and torch.equal(w[:nn], o[0][:nn])
+                    and torch.equal(c[:nn], o[1][:nn]))
+        p.destroy()
+    for r in ids:
+        srv.release(r)
+
+    # capacity: closed-loop burst
+    n_burst = 384
+    ks = [rng.randrange(pool_size) for _ in range(n_burst)]
+    o_b = outputs(n_burst)
+    t = time.perf_counter()
+    ids = [submit(k, o) for k, o in zip(ks, o_b)]
+    for r in ids:
+        srv.wait(r)
+    burst_s = time.perf_counter() - t
+    capacity = n_burst / burst_s
+    for r in ids:
+        srv.release(r)
+
+    # open loop: Poisson arrivals at fractions of the capacity
+    rates = []
+    for frac in (0.3, 0.6, 0.9):
+        rate = frac * capacity
+        n_req = int(min(1500, max(100, rate * 1.5)))
+        gaps = [rng.expovariate(rate) for _ in range(n_req)]
+        ks = [rng.randrange(pool_size) for _ in range(n_req)]
+        o_r = outputs(n_req)
+        torch.cuda.synchronize()
+        ids, lags = [], []
+        t0 = time.perf_counter()
+        due = t0
+        for g, k, o in zip(gaps, ks, o_r):
+            due += g
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 0.002:
+                    time.sleep(due - now - 0.001)
+            lags.append((time.perf_counter() - due) * 1e3)
+            ids.append(submit(k, o))
+        for r in ids:
+            srv.wait(r)
+        t_end = time.perf_counter()
+        infos = [srv.query(r) for r in ids]
+        lat = sorted(q["latency_ms"] for q in infos)
+        bs = [q["batch_size"] for q in infos]
+        for r in ids:
+            srv.release(r)
+        q = lambda v, x: v[min(len(v) - 1, int(x * len(v)))]
+        rates.append({"offered_per_s": rate, "requests": n_req,
+                      "sustained_sfts_per_s": n_req / (t_end - t0),
+                      "p50_ms": q(lat, 0.5), "p99_ms": q(lat, 0.99),
+                      "mean_batch": sum(bs) / len(bs),
+                      "submit_lag_p99_ms": q(sorted(lags), 0.99)})
+        del o_r
+    st = srv.stats()
+    srv.destroy()
+
+    # the same mix one request at a time: FP64 path (shapes whose chirp length fits FP64) and
+    # the FP32 path without batching
+    def one_at_a_time(prec, keys):
+        plans = {}
+        for k in set(keys):
+            N, s, _ = sigs[k]
+            plans[k] = sft.sft_plan(N, s, sft.sft_variant_init(**dict(variant, precision=prec)))
+        o = outputs(1)[0]
+        for k in set(keys):
+            sft.sft_execute(plans[k], sigs[k][2].data_ptr(), o[0].data_ptr(), o[1].data_ptr(),
+                            o[2].data_ptr(), 0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for k in keys:
+            sft.sft_execute(plans[k], sigs[k][2].data_ptr(), o[0].data_ptr(), o[1].data_ptr(),
+                            o[2].data_ptr(), 0)
+            torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        for p in plans.values():
+            p.destroy()
+        return len(keys) / dt
+
+    def fp64_fits(k):
+        N, s, _ = sigs[k]
+        primes = sft.sft_choose_moduli(N, s, variant["K"], variant["c_p"], variant["seed"])[0]
+        return 2 * max(primes) - 1 <= 8192
+    fp64_ok = [k for k in range(pool_size) if fp64_fits(k)]
+    keys64 = [rng.choice(fp64_ok) for _ in range(96)] if fp64_ok else []
+    keys32 = [rng.randrange(pool_size) for _ in range(96)]
+    plain64 = one_at_a_time(sft.SFT_FP64, keys64) if keys64 else None
+    plain32 = one_at_a_time(sft.SFT_FP32, keys32)
+    del sigs
+    torch.cuda.empty_cache()
+    return {"workload": f"Poisson arrivals; N log-uniform [2^16, 2^27], s log-uniform [8, 2048], "
+                        f"SNR U[10, 40] dB, complex64; {pool_size} resident signals",
+            "server": {"mem_budget_gib": 16, "max_batch": 32, "max_inflight": 3},
+            "capacity_sfts_per_s": capacity, "rates": rates,
+            "plans": {"built": st["plans_built"], "reused": st["plans_reused"],
+                      "evicted": st["plans_evicted"], "arena_peak_gb": st["arena_peak"] / 1e9},
+            "warm_s": warm_s, "warm_plans_built": st_warm["plans_built"],
+            "one_at_a_time": {"fp64_sfts_per_s": plain64, "fp32_sfts_per_s": plain32,
+                              "fp64_note": "requests whose length-p DFT fits the FP64 kernel "
+                                           "(2p - 1 <= 8192)"},
+            "equal_to_alone": f"{same}/{len(range(0, pool_size, 4))} sampled requests bit-identical"}
 
 
 # ------------------------------------------------------------------------------------------

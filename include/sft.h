@@ -266,6 +266,85 @@ sft_status sft_plan_profile_read(sft_plan_t plan, double* stage_ms, int32_t* n_e
 int64_t sft_plan_launches(sft_plan_t plan);
 
 /*
+ * Serving loop.  A server owns one device-memory arena of `mem_budget` bytes from which it carves
+ * the plans of the requests it admits (tables, filter constants and scratch stay resident for
+ * later requests of the same N and s), a scheduler thread and `max_inflight` non-blocking
+ * streams.  Requests of any N and s are queued in arrival order; whenever a stream is free the
+ * scheduler takes up to `max_batch` queued requests whose plans it can hold (building plans, and
+ * evicting least recently used idle plans when the arena is full) and runs them as one batched
+ * execution (one launch per stage for all of them, as sft_batch_execute).  Requests that arrive
+ * while others run join the next batch, and batches on different streams overlap on the device.
+ * A request waits at the head of the queue until memory frees up; one whose plan does not fit
+ * the whole arena fails with SFT_ENOMEM.  Each result is the one sft_execute gives for a plan of
+ * the same N, s and variant, bit for bit, whatever else ran with it.
+ *
+ * Every plan uses `variant`.  Tuning `tune` (sft_tuning_default when tune.resample_threads is 0)
+ * sets the launch geometry.  mem_budget covers the plans; each stream adds a small record
+ * buffer (< 1 MiB at max_batch = 256).
+ */
+typedef struct sft_server_s* sft_server_t;
+typedef int64_t sft_request_t;
+
+typedef struct {
+  size_t mem_budget;      /* device bytes for plans (the arena); >= 1 MiB */
+  int32_t max_batch;      /* requests per batched execution, 1..256 */
+  int32_t max_inflight;   /* batched executions in flight at once (streams), 1..8 */
+  sft_variant variant;
+  sft_tuning tune;
+} sft_server_config;
+
+typedef struct {
+  int32_t state;          /* 0 queued, 1 running, 2 done, 3 failed */
+  int32_t status;         /* sft_status: SFT_OK, or why the request failed */
+  int32_t batch_size;     /* requests in the batched execution that served it (0 until launched) */
+  int32_t plan_reused;    /* 1 if its plan was resident already, 0 if built for it */
+  double queued_ms;       /* submission -> launch of its batch (host clock) */
+  double latency_ms;      /* submission -> results complete in device memory (host clock) */
+} sft_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, batches;
+  int64_t plans_built, plans_reused, plans_evicted;
+  int64_t kernel_launches;
+  size_t arena_bytes, arena_used, arena_peak;
+  int32_t resident_plans, max_batch_seen;
+} sft_server_stats;
+
+/* Default configuration: 8 GiB, max_batch 64, max_inflight 2, sft_variant_init, default tuning. */
+void sft_server_config_init(sft_server_config* cfg);
+
+/* Allocate the arena and the streams, start the scheduler.  SFT_EINVAL for a bad configuration,
+ * SFT_ENOMEM if the arena cannot be allocated. */
+sft_status sft_server_create(sft_server_t* out, const sft_server_config* cfg);
+
+/*
+ * Queue one transform.  f_dev holds N elements of the variant's input type and must be fully
+ * written before the call (synchronise the producing stream first); the outputs are laid out as
+ * for sft_execute.  All four buffers are the caller's and must stay valid until the request is
+ * done or failed.  *id receives the request's handle.  Never blocks on the device.
+ */
+sft_status sft_server_submit(sft_server_t server, int64_t N, int32_t s, const void* f_dev,
+                             int64_t* out_freqs_dev, void* out_coefs_dev, int32_t* out_count_dev,
+                             sft_request_t* id);
+
+/* State and timings of a request (SFT_EINVAL for an unknown or released handle). */
+sft_status sft_server_query(sft_server_t server, sft_request_t id, sft_request_info* info);
+
+/* Block until the request has finished, done or failed (SFT_OK; sft_server_query tells which and
+ * why), or timeout_ms has passed (SFT_ETIMEOUT; timeout_ms < 0 waits without limit).  SFT_EINVAL
+ * for an unknown handle.  A done request's results are complete in device memory and visible to
+ * every stream. */
+sft_status sft_server_wait(sft_server_t server, sft_request_t id, int32_t timeout_ms);
+
+/* Forget a finished request's record (SFT_EBUSY while it is queued or running). */
+sft_status sft_server_release(sft_server_t server, sft_request_t id);
+
+sft_status sft_server_stats_read(sft_server_t server, sft_server_stats* out);
+
+/* Finish every queued and running request, stop the scheduler, free everything. */
+sft_status sft_server_destroy(sft_server_t server);
+
+/*
  * Batched DFT that allocates no device memory, for callers that cannot call cudaMalloc: code that
  * runs while another component owns the device's memory (a host framework's caching allocator, a
  * plug-in with a fixed memory budget, or a phase where allocating would stall or fragment the

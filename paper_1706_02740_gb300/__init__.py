@@ -68,6 +68,27 @@ class sft_tuning(ctypes.Structure):
         return t
 
 
+class sft_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("variant", sft_variant), ("tune", sft_tuning)]
+
+
+class sft_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("plan_reused", ctypes.c_int32),
+                ("queued_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class sft_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("plans_built", ctypes.c_int64), ("plans_reused", ctypes.c_int64),
+                ("plans_evicted", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
+                ("arena_peak", ctypes.c_size_t), ("resident_plans", ctypes.c_int32),
+                ("max_batch_seen", ctypes.c_int32)]
+
+
 _lib = None
 
 EXPORTS = {
@@ -106,6 +127,18 @@ EXPORTS = {
     "sft_batch_autotune": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_void_p)] * 4
                            + [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(sft_tuning)]),
     "sft_batch_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "sft_server_config_init": (None, [ctypes.POINTER(sft_server_config)]),
+    "sft_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(sft_server_config)]),
+    "sft_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "sft_server_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.POINTER(sft_request_info)]),
+    "sft_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "sft_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "sft_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sft_server_stats)]),
+    "sft_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sft_batch_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "sft_choose_moduli": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
@@ -348,6 +381,67 @@ def autotune_batch_torch(batch: Batch, fs, reps: int = 3, stream=None) -> dict:
     outs = batch_outputs_torch(batch, fs[0].device)
     st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
     return batch.autotune(*_batch_ptrs(fs, outs), st.cuda_stream, reps)
+
+
+REQUEST_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
+class Server:
+    """Owns an sft_server_t (serving loop: memory-budget admission, resident plans, continuous
+    batching).  Buffers passed to submit must stay alive until the request has finished."""
+
+    def __init__(self, mem_budget: int = 8 << 30, max_batch: int = 64, max_inflight: int = 2,
+                 variant: sft_variant | None = None, tuning: dict | None = None):
+        cfg = sft_server_config()
+        load().sft_server_config_init(ctypes.byref(cfg))
+        cfg.mem_budget = int(mem_budget)
+        cfg.max_batch = int(max_batch)
+        cfg.max_inflight = int(max_inflight)
+        if variant is not None:
+            cfg.variant = variant
+        if tuning is not None:
+            cfg.tune = sft_tuning.from_dict(tuning)
+        h = ctypes.c_void_p()
+        _check(load().sft_server_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self.handle = h.value
+
+    def submit(self, N: int, s: int, f_ptr: int, w_ptr: int, c_ptr: int, n_ptr: int) -> int:
+        rid = ctypes.c_int64()
+        _check(load().sft_server_submit(self.handle, int(N), int(s), f_ptr, w_ptr, c_ptr, n_ptr,
+                                        ctypes.byref(rid)))
+        return rid.value
+
+    def query(self, rid: int) -> dict:
+        info = sft_request_info()
+        _check(load().sft_server_query(self.handle, int(rid), ctypes.byref(info)))
+        return {"state": REQUEST_STATES[info.state], "status": info.status,
+                "batch_size": info.batch_size, "plan_reused": bool(info.plan_reused),
+                "queued_ms": info.queued_ms, "latency_ms": info.latency_ms}
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> int:
+        """Waits for the request to finish; returns its status (SFT_OK when done, else why it
+        failed).  Raises on timeout or an unknown handle."""
+        _check(load().sft_server_wait(self.handle, int(rid), int(timeout_ms)))
+        return self.query(rid)["status"]
+
+    def release(self, rid: int):
+        _check(load().sft_server_release(self.handle, int(rid)))
+
+    def stats(self) -> dict:
+        st = sft_server_stats()
+        _check(load().sft_server_stats_read(self.handle, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in sft_server_stats._fields_}
+
+    def destroy(self):
+        if self.handle:
+            load().sft_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def sft_tuning_default() -> dict:

@@ -137,7 +137,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
                       const int64_t* primes_in, int32_t n_primes, const int32_t* small_in,
-                      int32_t n_small) {
+                      int32_t n_small, DeviceMemory* mem) {
   DevPlan& d = P->d;
   memset(&d, 0, sizeof(d));
   if (!v) { set_error("variant is NULL"); return SFT_EINVAL; }
@@ -356,14 +356,25 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   const size_t total = soff;
 
   char* base = nullptr;
-  cudaError_t e = cudaMalloc((void**)&base, total);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error(std::string("cudaMalloc of plan memory failed: ") + cudaGetErrorString(e));
-    return SFT_ENOMEM;
+  cudaError_t e = cudaSuccess;
+  P->mem = mem;
+  if (mem) {
+    base = static_cast<char*>(mem->alloc(total));
+    if (!base) {
+      set_error("plan needs " + std::to_string(total) + " device bytes: not available in the arena");
+      return SFT_ENOMEM;
+    }
+  } else {
+    e = cudaMalloc((void**)&base, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error(std::string("cudaMalloc of plan memory failed: ") + cudaGetErrorString(e));
+      return SFT_ENOMEM;
+    }
   }
   P->allocations.push_back(base);
-  e = cudaMemcpy(base, blob.data(), table_bytes, cudaMemcpyHostToDevice);
+  e = mem ? mem->upload(base, blob.data(), table_bytes)
+          : cudaMemcpy(base, blob.data(), table_bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     set_error(std::string("copy of plan tables failed: ") + cudaGetErrorString(e));
     free_plan(P);
@@ -384,7 +395,8 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   d.wlist = reinterpret_cast<int32_t*>(base + o_wlist);
   d.woff = reinterpret_cast<int32_t*>(base + o_woff);
   P->d_dev = reinterpret_cast<DevPlan*>(base + o_self);
-  e = cudaMemcpy(P->d_dev, &d, sizeof(DevPlan), cudaMemcpyHostToDevice);
+  e = mem ? mem->upload(P->d_dev, &d, sizeof(DevPlan))
+          : cudaMemcpy(P->d_dev, &d, sizeof(DevPlan), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     set_error(std::string("copy of the plan record failed: ") + cudaGetErrorString(e));
     free_plan(P);
@@ -412,7 +424,10 @@ sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t s
 }
 
 void free_plan(Plan* P) {
-  for (void* a : P->allocations) cudaFree(a);
+  for (void* a : P->allocations) {
+    if (P->mem) P->mem->release(a);
+    else cudaFree(a);
+  }
   P->allocations.clear();
 }
 

@@ -1,0 +1,602 @@
+// Serving loop (sft_server_*): admission by device-memory budget, resident plans and continuous
+// batching over several streams.
+//
+// Threads: callers submit and query under one mutex; one scheduler thread owns the plans, the
+// arena and the launch slots; CUDA's host-callback thread marks a slot done when its batched
+// execution has finished on the device.  The scheduler makes no CUDA call while it holds the
+// mutex, so a completion callback never waits on CUDA work.
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "arena.h"
+#include "sft_internal.h"
+
+namespace sft {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr int kMaxServerBatch = 256;
+constexpr int kMaxInflight = 8;
+
+// The budget as device memory: one cudaMalloc, blocks handed out by OffsetArena, uploads on a
+// private non-blocking stream (never the legacy default stream, which would wait for other work).
+class DeviceArena final : public DeviceMemory {
+ public:
+  ~DeviceArena() override {
+    if (st_) cudaStreamDestroy(st_);
+    if (base_) cudaFree(base_);
+  }
+  cudaError_t init(size_t bytes) {
+    book_.reset(bytes);
+    cudaError_t e = cudaMalloc((void**)&base_, book_.capacity());
+    if (e != cudaSuccess) {
+      base_ = nullptr;
+      return e;
+    }
+    return cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking);
+  }
+  void* alloc(size_t bytes) override {
+    std::lock_guard<std::mutex> g(mu_);
+    last_request_ = bytes;
+    const int64_t off = book_.alloc(bytes);
+    return off < 0 ? nullptr : base_ + off;
+  }
+  void release(void* p) override {
+    std::lock_guard<std::mutex> g(mu_);
+    book_.release((size_t)(static_cast<char*>(p) - base_));
+  }
+  cudaError_t upload(void* dst, const void* src, size_t bytes) override {
+    std::lock_guard<std::mutex> g(up_mu_);
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st_);
+    return e == cudaSuccess ? cudaStreamSynchronize(st_) : e;
+  }
+  size_t last_request() { std::lock_guard<std::mutex> g(mu_); return last_request_; }
+  size_t largest_free() { std::lock_guard<std::mutex> g(mu_); return book_.largest_free(); }
+  void usage(size_t* cap, size_t* used, size_t* peak) {
+    std::lock_guard<std::mutex> g(mu_);
+    *cap = book_.capacity();
+    *used = book_.used();
+    *peak = book_.peak();
+  }
+
+ private:
+  char* base_ = nullptr;
+  cudaStream_t st_ = nullptr;
+  OffsetArena book_;
+  size_t last_request_ = 0;
+  std::mutex mu_, up_mu_;
+};
+
+struct Entry {                       // a resident plan
+  Plan P;
+  int64_t N = 0;
+  int32_t s = 0;
+  bool busy = false;
+  std::list<Entry*>::iterator lru_it;  // position in the idle list while idle
+};
+
+struct Request {
+  int64_t N = 0;
+  int32_t s = 0;
+  const void* f = nullptr;
+  int64_t* w = nullptr;
+  void* c = nullptr;
+  int32_t* n = nullptr;
+  int32_t state = 0;                 // 0 queued, 1 running, 2 done, 3 failed
+  int32_t status = SFT_OK;
+  int32_t batch_size = 0, reused = 0;
+  Clock::time_point t_submit, t_launch, t_done;
+  Entry* plan = nullptr;
+};
+
+struct Server;
+
+struct Slot {                        // one batched execution in flight
+  Server* srv = nullptr;
+  cudaStream_t st = nullptr;
+  char* dev = nullptr;               // plan records | block prefixes | pointer arrays
+  char* host = nullptr;              // pinned staging of the same
+  size_t bytes = 0;
+  bool busy = false;
+  bool done = false;                 // set by the completion callback (under the server mutex)
+  Clock::time_point t_done;
+  std::vector<int64_t> reqs;
+  std::vector<Entry*> plans;
+};
+
+struct Server {
+  sft_server_config cfg;
+  DeviceArena arena;
+  std::vector<Slot*> slots;
+  std::mutex mu;
+  std::condition_variable cv;        // wakes the scheduler
+  std::condition_variable done_cv;   // wakes waiters
+  std::thread th;
+  bool stop = false;
+  std::deque<int64_t> queue;
+  std::unordered_map<int64_t, Request> reqs;
+  int64_t next_id = 1;
+  // scheduler-thread state
+  std::multimap<std::pair<int64_t, int32_t>, Entry*> plans;
+  std::list<Entry*> lru;             // idle plans, least recently used first
+  sft_server_stats stats;            // guarded by mu
+  int device = 0;
+};
+
+void CUDART_CB on_slot_done(void* p) {
+  Slot* sl = static_cast<Slot*>(p);
+  {
+    std::lock_guard<std::mutex> g(sl->srv->mu);
+    sl->t_done = Clock::now();
+    sl->done = true;
+  }
+  sl->srv->cv.notify_all();
+}
+
+void evict(Server& S, Entry* e) {
+  S.lru.erase(e->lru_it);
+  auto range = S.plans.equal_range({e->N, e->s});
+  for (auto it = range.first; it != range.second; ++it)
+    if (it->second == e) {
+      S.plans.erase(it);
+      break;
+    }
+  free_plan(&e->P);
+  delete e;
+  std::lock_guard<std::mutex> g(S.mu);
+  ++S.stats.plans_evicted;
+  --S.stats.resident_plans;
+}
+
+// A resident idle plan for (N, s), or a new one carved from the arena (evicting least recently
+// used idle plans when it does not fit).  SFT_ENOMEM when it cannot fit beside the busy plans.
+sft_status acquire(Server& S, int64_t N, int32_t s, Entry** out, bool* reused) {
+  auto range = S.plans.equal_range({N, s});
+  for (auto it = range.first; it != range.second; ++it) {
+    Entry* e = it->second;
+    if (!e->busy) {
+      S.lru.erase(e->lru_it);
+      e->busy = true;
+      *out = e;
+      *reused = true;
+      return SFT_OK;
+    }
+  }
+  Entry* e = new (std::nothrow) Entry();
+  if (!e) return SFT_ENOMEM;
+  for (;;) {
+    sft_status st = build_plan(&e->P, N, s, &S.cfg.variant, 0, nullptr, 0, nullptr, 0, &S.arena);
+    if (st == SFT_OK) break;
+    free_plan(&e->P);
+    e->P = Plan();
+    if (st != SFT_ENOMEM || S.lru.empty()) {
+      delete e;
+      return st;
+    }
+    // evict until a block of the requested size is free, then build again
+    const size_t need = S.arena.last_request();
+    while (!S.lru.empty() && S.arena.largest_free() < need) evict(S, S.lru.front());
+  }
+  e->N = N;
+  e->s = s;
+  e->busy = true;
+  S.plans.insert({{N, s}, e});
+  {
+    std::lock_guard<std::mutex> g(S.mu);
+    ++S.stats.resident_plans;
+  }
+  *out = e;
+  *reused = false;
+  return SFT_OK;
+}
+
+void release_plan(Server& S, Entry* e) {
+  e->busy = false;
+  S.lru.push_back(e);
+  e->lru_it = std::prev(S.lru.end());
+}
+
+// Upload the batch's plan records, block prefixes and pointers, launch every stage, and queue the
+// completion callback, all on the slot's stream.
+cudaError_t launch_slot(Server& S, Slot& sl, const std::vector<Request*>& rq, int* launched) {
+  const int n = (int)rq.size();
+  const size_t o_prefix = align256(sizeof(DevPlan) * (size_t)n);
+  const size_t o_ptrs = align256(o_prefix + sizeof(int32_t) * (size_t)kStCount * (n + 1));
+  const size_t used = o_ptrs + sizeof(void*) * 4 * (size_t)n;
+  if (used > sl.bytes) return cudaErrorInvalidValue;
+  LaunchSet ls;
+  memset(&ls, 0, sizeof(ls));
+  ls.tune = S.cfg.tune;
+  int32_t* pre = reinterpret_cast<int32_t*>(sl.host + o_prefix);
+  void** ptr = reinterpret_cast<void**>(sl.host + o_ptrs);
+  for (int i = 0; i < n; ++i) {
+    const DevPlan& d = rq[i]->plan->P.d;
+    memcpy(sl.host + sizeof(DevPlan) * i, &d, sizeof(DevPlan));
+    ls.pmax = std::max(ls.pmax, d.pmax);
+    ptr[i] = const_cast<void*>(rq[i]->f);
+    ptr[n + i] = rq[i]->w;
+    ptr[2 * n + i] = rq[i]->c;
+    ptr[3 * n + i] = rq[i]->n;
+  }
+  for (int k = 0; k < kStCount; ++k) {
+    int64_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+      pre[(size_t)k * (n + 1) + i] = (int32_t)acc;
+      acc += signal_blocks(rq[i]->plan->P.d, k, ls.tune);
+    }
+    if (acc > 0x7fffffff) return cudaErrorInvalidValue;
+    pre[(size_t)k * (n + 1) + n] = (int32_t)acc;
+    ls.blocks[k] = (int32_t)acc;
+    ls.blk[k] = reinterpret_cast<const int32_t*>(sl.dev + o_prefix) + (size_t)k * (n + 1);
+  }
+  cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, used, cudaMemcpyHostToDevice, sl.st);
+  if (e != cudaSuccess) return e;
+  BatchView bv;
+  memset(&bv, 0, sizeof(bv));
+  bv.plans = reinterpret_cast<const DevPlan*>(sl.dev);
+  bv.n = n;
+  void** dptr = reinterpret_cast<void**>(sl.dev + o_ptrs);
+  bv.f = const_cast<const void* const*>(dptr);
+  bv.out_w = reinterpret_cast<int64_t* const*>(dptr + n);
+  bv.out_c = reinterpret_cast<double2* const*>(dptr + 2 * n);
+  bv.out_n = reinterpret_cast<int32_t* const*>(dptr + 3 * n);
+  e = run_stages(rq[0]->plan->P.d, bv, ls, sl.st, nullptr, launched);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchHostFunc(sl.st, on_slot_done, &sl);
+}
+
+void scheduler(Server* Sp) {
+  Server& S = *Sp;
+  cudaSetDevice(S.device);
+  std::unique_lock<std::mutex> lk(S.mu);
+  for (;;) {
+    // retire finished slots
+    bool retired = false;
+    for (Slot* sl : S.slots) {
+      if (!sl->busy || !sl->done) continue;
+      for (int64_t id : sl->reqs) {
+        auto it = S.reqs.find(id);
+        if (it == S.reqs.end()) continue;
+        it->second.state = 2;
+        it->second.t_done = sl->t_done;
+        ++S.stats.completed;
+      }
+      for (Entry* e : sl->plans) release_plan(S, e);
+      sl->reqs.clear();
+      sl->plans.clear();
+      sl->busy = sl->done = false;
+      retired = true;
+    }
+    if (retired) S.done_cv.notify_all();
+    Slot* free_slot = nullptr;
+    bool any_busy = false;
+    for (Slot* sl : S.slots) {
+      if (sl->busy) any_busy = true;
+      else if (!free_slot) free_slot = sl;
+    }
+    if (S.stop && S.queue.empty() && !any_busy) break;
+    if (!free_slot || S.queue.empty()) {
+      S.cv.wait(lk, [&] {
+        bool busy = false, idle = false;
+        for (Slot* sl : S.slots) {
+          if (sl->busy && sl->done) return true;
+          (sl->busy ? busy : idle) = true;
+        }
+        if (S.queue.empty()) return S.stop && !busy;
+        return idle;
+      });
+      continue;
+    }
+    // take up to max_batch queued requests, in arrival order
+    std::vector<int64_t> take;
+    while (!S.queue.empty() && (int)take.size() < S.cfg.max_batch) {
+      take.push_back(S.queue.front());
+      S.queue.pop_front();
+    }
+    std::vector<Request*> rq;
+    for (int64_t id : take) rq.push_back(&S.reqs[id]);   // records stay put until released
+    lk.unlock();
+
+    std::vector<int64_t> admitted, deferred;
+    std::vector<Request*> arq;
+    std::vector<std::pair<int64_t, sft_status>> failed;
+    std::vector<int32_t> was_reused;
+    int64_t built = 0, reused_n = 0;
+    for (size_t i = 0; i < take.size(); ++i) {
+      if (!deferred.empty()) {                 // keep arrival order behind a waiting request
+        deferred.push_back(take[i]);
+        continue;
+      }
+      Entry* e = nullptr;
+      bool reused = false;
+      const sft_status st = acquire(S, rq[i]->N, rq[i]->s, &e, &reused);
+      if (st == SFT_OK) {
+        rq[i]->plan = e;                       // read only by this thread until retired
+        (reused ? reused_n : built) += 1;
+        was_reused.push_back(reused ? 1 : 0);
+        admitted.push_back(take[i]);
+        arq.push_back(rq[i]);
+      } else if (st == SFT_ENOMEM && (any_busy || !admitted.empty())) {
+        deferred.push_back(take[i]);           // memory frees up when running work finishes
+      } else {
+        failed.push_back({take[i], st});
+      }
+    }
+    int launched = 0;
+    cudaError_t ce = cudaSuccess;
+    if (!arq.empty()) ce = launch_slot(S, *free_slot, arq, &launched);
+
+    lk.lock();
+    for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) S.queue.push_front(*it);
+    for (auto& f : failed) {
+      Request& r = S.reqs[f.first];
+      r.state = 3;
+      r.status = f.second;
+      r.t_done = Clock::now();
+      ++S.stats.failed;
+    }
+    S.stats.plans_built += built;
+    S.stats.plans_reused += reused_n;
+    if (!arq.empty()) {
+      const auto now = Clock::now();
+      for (size_t i = 0; i < arq.size(); ++i) {
+        arq[i]->batch_size = (int32_t)arq.size();
+        arq[i]->reused = was_reused[i];
+      }
+      if (ce == cudaSuccess) {
+        free_slot->busy = true;
+        free_slot->done = false;
+        free_slot->reqs = admitted;
+        free_slot->plans.clear();
+        for (Request* r : arq) {
+          r->state = 1;
+          r->t_launch = now;
+          free_slot->plans.push_back(r->plan);
+        }
+        ++S.stats.batches;
+        S.stats.kernel_launches += launched;
+        S.stats.max_batch_seen = std::max(S.stats.max_batch_seen, (int32_t)arq.size());
+      } else {
+        cudaGetLastError();
+        for (Request* r : arq) {
+          r->state = 3;
+          r->status = SFT_ECUDA;
+          r->t_done = now;
+          release_plan(S, r->plan);
+          ++S.stats.failed;
+        }
+      }
+    }
+    if (!failed.empty() || ce != cudaSuccess) S.done_cv.notify_all();
+    if (arq.empty() && !deferred.empty()) {
+      // nothing could start: wait for running work to finish (it frees memory)
+      S.cv.wait(lk, [&] {
+        bool busy = false;
+        for (Slot* sl : S.slots) {
+          if (sl->busy && sl->done) return true;
+          busy = busy || sl->busy;
+        }
+        return !busy;
+      });
+    }
+  }
+}
+
+void destroy_server(Server* S) {
+  for (Slot* sl : S->slots) {
+    if (sl->st) cudaStreamDestroy(sl->st);
+    if (sl->dev) cudaFree(sl->dev);
+    if (sl->host) cudaFreeHost(sl->host);
+    delete sl;
+  }
+  S->slots.clear();
+  for (auto& kv : S->plans) {
+    free_plan(&kv.second->P);
+    delete kv.second;
+  }
+  S->plans.clear();
+  S->lru.clear();
+}
+
+}  // namespace
+}  // namespace sft
+
+struct sft_server_s {
+  sft::Server S;
+};
+
+extern "C" {
+
+void sft_server_config_init(sft_server_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->mem_budget = (size_t)8 << 30;
+  cfg->max_batch = 64;
+  cfg->max_inflight = 2;
+  sft_variant_init(&cfg->variant);
+  cfg->tune = sft::default_tuning();
+}
+
+sft_status sft_server_create(sft_server_t* out, const sft_server_config* cfg) {
+  using namespace sft;
+  if (!out || !cfg) { set_error("sft_server_create: NULL argument"); return SFT_EINVAL; }
+  *out = nullptr;
+  if (cfg->mem_budget < ((size_t)1 << 20) || cfg->max_batch < 1 || cfg->max_batch > kMaxServerBatch ||
+      cfg->max_inflight < 1 || cfg->max_inflight > kMaxInflight) {
+    set_error("sft_server_create: need mem_budget >= 1 MiB, 1 <= max_batch <= 256, "
+              "1 <= max_inflight <= 8");
+    return SFT_EINVAL;
+  }
+  sft_tuning tune = cfg->tune.resample_threads == 0 ? default_tuning() : cfg->tune;
+  std::string why;
+  if (!tuning_valid(tune, &why)) { set_error("sft_server_create: " + why); return SFT_EINVAL; }
+  sft_server_s* h = new (std::nothrow) sft_server_s();
+  if (!h) { set_error("host allocation failed"); return SFT_ENOMEM; }
+  Server& S = h->S;
+  S.cfg = *cfg;
+  S.cfg.tune = tune;
+  memset(&S.stats, 0, sizeof(S.stats));
+  cudaGetDevice(&S.device);
+  cudaError_t e = S.arena.init(cfg->mem_budget);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    set_error(std::string("sft_server_create: arena allocation failed: ") + cudaGetErrorString(e));
+    return SFT_ENOMEM;
+  }
+  const int nb = cfg->max_batch;
+  const size_t slot_bytes = align256(align256(sizeof(DevPlan) * (size_t)nb) +
+                                     sizeof(int32_t) * (size_t)kStCount * (nb + 1)) +
+                            sizeof(void*) * 4 * (size_t)nb;
+  for (int i = 0; i < cfg->max_inflight && e == cudaSuccess; ++i) {
+    Slot* sl = new (std::nothrow) Slot();
+    if (!sl) { e = cudaErrorMemoryAllocation; break; }
+    sl->srv = &S;
+    sl->bytes = slot_bytes;
+    S.slots.push_back(sl);
+    e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sl->dev, slot_bytes);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl->host, slot_bytes, cudaHostAllocDefault);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_server(&S);
+    delete h;
+    set_error(std::string("sft_server_create: set-up failed: ") + cudaGetErrorString(e));
+    return SFT_ENOMEM;
+  }
+  S.th = std::thread(scheduler, &S);
+  *out = h;
+  return SFT_OK;
+}
+
+sft_status sft_server_submit(sft_server_t server, int64_t N, int32_t s, const void* f_dev,
+                             int64_t* out_freqs_dev, void* out_coefs_dev, int32_t* out_count_dev,
+                             sft_request_t* id) {
+  using namespace sft;
+  if (!server || !f_dev || !out_freqs_dev || !out_coefs_dev || !out_count_dev || !id) {
+    set_error("sft_server_submit: NULL argument");
+    return SFT_EINVAL;
+  }
+  Server& S = server->S;
+  const size_t align = S.cfg.variant.input == SFT_IN_C64 ? 8 : 16;
+  if ((uintptr_t)f_dev % align) { set_error("sft_server_submit: f is misaligned"); return SFT_EINVAL; }
+  {
+    std::lock_guard<std::mutex> g(S.mu);
+    if (S.stop) { set_error("sft_server_submit: the server is stopping"); return SFT_EINVAL; }
+    const int64_t rid = S.next_id++;
+    Request& r = S.reqs[rid];
+    r.N = N;
+    r.s = s;
+    r.f = f_dev;
+    r.w = out_freqs_dev;
+    r.c = out_coefs_dev;
+    r.n = out_count_dev;
+    r.t_submit = Clock::now();
+    S.queue.push_back(rid);
+    ++S.stats.submitted;
+    *id = rid;
+  }
+  S.cv.notify_all();
+  return SFT_OK;
+}
+
+sft_status sft_server_query(sft_server_t server, sft_request_t id, sft_request_info* info) {
+  using namespace sft;
+  if (!server || !info) { set_error("sft_server_query: NULL argument"); return SFT_EINVAL; }
+  Server& S = server->S;
+  std::lock_guard<std::mutex> g(S.mu);
+  auto it = S.reqs.find(id);
+  if (it == S.reqs.end()) { set_error("sft_server_query: unknown request"); return SFT_EINVAL; }
+  const Request& r = it->second;
+  memset(info, 0, sizeof(*info));
+  info->state = r.state;
+  info->status = r.status;
+  info->batch_size = r.batch_size;
+  info->plan_reused = r.reused;
+  if (r.state >= 1 && r.state != 3) info->queued_ms = ms_between(r.t_submit, r.t_launch);
+  if (r.state >= 2) info->latency_ms = ms_between(r.t_submit, r.t_done);
+  return SFT_OK;
+}
+
+sft_status sft_server_wait(sft_server_t server, sft_request_t id, int32_t timeout_ms) {
+  using namespace sft;
+  if (!server) { set_error("sft_server_wait: NULL server"); return SFT_EINVAL; }
+  Server& S = server->S;
+  std::unique_lock<std::mutex> lk(S.mu);
+  auto it = S.reqs.find(id);
+  if (it == S.reqs.end()) { set_error("sft_server_wait: unknown request"); return SFT_EINVAL; }
+  auto finished = [&] {
+    auto jt = S.reqs.find(id);
+    return jt == S.reqs.end() || jt->second.state >= 2;
+  };
+  if (timeout_ms < 0) {
+    S.done_cv.wait(lk, finished);
+  } else if (!S.done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished)) {
+    set_error("sft_server_wait: timed out");
+    return SFT_ETIMEOUT;
+  }
+  return SFT_OK;
+}
+
+sft_status sft_server_release(sft_server_t server, sft_request_t id) {
+  using namespace sft;
+  if (!server) { set_error("sft_server_release: NULL server"); return SFT_EINVAL; }
+  Server& S = server->S;
+  std::lock_guard<std::mutex> g(S.mu);
+  auto it = S.reqs.find(id);
+  if (it == S.reqs.end()) { set_error("sft_server_release: unknown request"); return SFT_EINVAL; }
+  if (it->second.state < 2) { set_error("sft_server_release: request not finished"); return SFT_EBUSY; }
+  S.reqs.erase(it);
+  return SFT_OK;
+}
+
+sft_status sft_server_stats_read(sft_server_t server, sft_server_stats* out) {
+  using namespace sft;
+  if (!server || !out) { set_error("sft_server_stats_read: NULL argument"); return SFT_EINVAL; }
+  Server& S = server->S;
+  {
+    std::lock_guard<std::mutex> g(S.mu);
+    *out = S.stats;
+  }
+  S.arena.usage(&out->arena_bytes, &out->arena_used, &out->arena_peak);
+  return SFT_OK;
+}
+
+sft_status sft_server_destroy(sft_server_t server) {
+  using namespace sft;
+  if (!server) return SFT_OK;
+  Server& S = server->S;
+  {
+    std::lock_guard<std::mutex> g(S.mu);
+    S.stop = true;
+  }
+  S.cv.notify_all();
+  if (S.th.joinable()) S.th.join();
+  destroy_server(&S);
+  delete server;
+  return SFT_OK;
+}
+
+}  // extern "C"

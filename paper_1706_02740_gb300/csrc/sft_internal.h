@@ -202,6 +202,14 @@ struct Profiler {
   int recorded = 0;
 };
 
+// Where a plan's device memory comes from when it is not cudaMalloc (the server's arena).
+struct DeviceMemory {
+  virtual ~DeviceMemory() = default;
+  virtual void* alloc(size_t bytes) = 0;                         // nullptr when it does not fit
+  virtual void release(void* p) = 0;
+  virtual cudaError_t upload(void* dst, const void* src, size_t bytes) = 0;  // host -> device, done on return
+};
+
 struct Plan {
   DevPlan d;
   DevPlan* d_dev = nullptr;   // device copy of d (inside the plan's allocation)
@@ -213,6 +221,7 @@ struct Plan {
   std::vector<int32_t> primes, small;
   size_t device_bytes = 0;
   std::vector<void*> allocations;
+  DeviceMemory* mem = nullptr;   // nullptr: allocations came from cudaMalloc
   int device = 0;
 };
 
@@ -247,7 +256,7 @@ void profile_release(Profiler& pr);
 // Host plan construction (plan.cpp).
 sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
                       const int64_t* primes, int32_t n_primes, const int32_t* small,
-                      int32_t n_small);
+                      int32_t n_small, DeviceMemory* mem = nullptr);
 void free_plan(Plan* P);
 sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                          int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);

@@ -50,6 +50,28 @@ def test_tuning_layout_and_defaults(lib):
     assert t["dft_two_ctas"] == 1
 
 
+def test_server_structs_and_config_defaults(lib):
+    assert ctypes.sizeof(sft.sft_server_config) == 8 + 4 + 4 + 48 + 13 * 4 + 4   # + tail padding
+    assert ctypes.sizeof(sft.sft_request_info) == 4 * 4 + 2 * 8
+    assert ctypes.sizeof(sft.sft_server_stats) == 8 * 8 + 3 * 8 + 2 * 4
+    cfg = sft.sft_server_config()
+    lib.sft_server_config_init(ctypes.byref(cfg))
+    assert cfg.mem_budget == 8 << 30 and cfg.max_batch == 64 and cfg.max_inflight == 2
+    assert (cfg.variant.kappa, cfg.variant.K) == (6, 5)
+    assert cfg.tune.resample_threads == 256
+
+
+@pytest.mark.parametrize("field,value", [("mem_budget", 1000), ("max_batch", 0), ("max_batch", 257),
+                                         ("max_inflight", 0), ("max_inflight", 9)])
+def test_server_rejects_bad_configurations_without_touching_the_device(lib, field, value):
+    cfg = sft.sft_server_config()
+    lib.sft_server_config_init(ctypes.byref(cfg))
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert lib.sft_server_create(ctypes.byref(h), ctypes.byref(cfg)) == sft.SFT_EINVAL
+    assert not h.value
+
+
 def test_variant_defaults(lib):
     v = sft.sft_variant_init()
     assert (v.kappa, v.precision, v.input, v.K) == (6, 0, 0, 5)

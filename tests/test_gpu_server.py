@@ -1,0 +1,175 @@
+"""Serving loop: requests of mixed N and s, admitted by device-memory budget, batched as they arrive
+and run on several streams.  Every result must equal, bit for bit, what the same plan gives for
+the request alone (sft_execute), whatever else it was batched or overlapped with."""
+import time
+
+import numpy as np
+import pytest
+
+import paper_1706_02740_gb300 as sft
+from synth.signals import as_complex64, make_signal
+
+pytestmark = pytest.mark.gpu
+
+VARIANT = dict(K=5, c_p=6.0, seed=5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1706_02740_gb300 import build
+    build.build()
+    sft.load()
+
+
+def _inputs(shapes, seed0):
+    import torch
+    return [torch.from_numpy(as_complex64(make_signal(N, s, seed0 + i, "unit", 30.0).f)).cuda()
+            for i, (N, s) in enumerate(shapes)]
+
+
+def _outputs(shapes):
+    import torch
+    return [(torch.full((s,), -7, dtype=torch.int64, device="cuda"),
+             torch.zeros(s, dtype=torch.complex128, device="cuda"),
+             torch.full((1,), -1, dtype=torch.int32, device="cuda")) for N, s in shapes]
+
+
+def _alone(shapes, fs):
+    import torch
+    res = []
+    for (N, s), f in zip(shapes, fs):
+        p = sft.sft_plan(N, s, sft.sft_variant_init(**VARIANT))
+        w, c, n = sft.execute_torch(p, f)
+        torch.cuda.synchronize()
+        res.append((w.cpu().numpy(), c.cpu().numpy(), int(n.item())))
+        p.destroy()
+    return res
+
+
+def _submit(srv, shapes, fs, outs):
+    return [srv.submit(N, s, f.data_ptr(), o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr())
+            for (N, s), f, o in zip(shapes, fs, outs)]
+
+
+def _check_equal(outs, ref, idx=None):
+    for i, ((w, c, n), (rw, rc, rn)) in enumerate(zip(outs, ref)):
+        if idx is not None and i not in idx:
+            continue
+        assert int(n.item()) == rn, i
+        assert np.array_equal(w.cpu().numpy(), rw), i
+        assert np.array_equal(c.cpu().numpy(), rc), i
+
+
+SHAPES = [(2 ** 14, 6), (65521, 12), (2 ** 16, 8), (2 ** 14, 6), (3 ** 10, 20), (2 ** 17, 40),
+          (65521, 12), (100003, 9), (2 ** 15 + 3, 30), (2 ** 14, 6), (2 ** 18, 64), (2 ** 16, 8)]
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    fs = _inputs(SHAPES, 2000)
+    ref = _alone(SHAPES, fs)
+    srv = sft.Server(mem_budget=2 << 30, max_batch=3, max_inflight=2,
+                     variant=sft.sft_variant_init(**VARIANT))
+    outs = _outputs(SHAPES)
+    ids = _submit(srv, SHAPES, fs, outs)
+    for rid in ids:
+        assert srv.wait(rid, 60000) == sft.SFT_OK
+    _check_equal(outs, ref)
+    infos = [srv.query(r) for r in ids]
+    assert all(q["state"] == "done" and q["latency_ms"] >= q["queued_ms"] >= 0 for q in infos)
+    assert max(q["batch_size"] for q in infos) >= 2          # requests were batched
+    st = srv.stats()
+    assert st["completed"] == len(SHAPES) and st["failed"] == 0
+    assert st["plans_built"] + st["plans_reused"] == len(SHAPES)
+    assert st["max_batch_seen"] <= 3 and st["batches"] >= len(SHAPES) // 3
+    assert st["kernel_launches"] > 0
+    # a second pass over the same shapes reuses the resident plans
+    outs2 = _outputs(SHAPES)
+    ids2 = _submit(srv, SHAPES, fs, outs2)
+    for rid in ids2:
+        assert srv.wait(rid, 60000) == sft.SFT_OK
+    _check_equal(outs2, ref)
+    assert srv.stats()["plans_reused"] > st["plans_reused"]
+    for rid in ids + ids2:
+        srv.release(rid)
+    with pytest.raises(sft.SftError):
+        srv.query(ids[0])
+    srv.destroy()
+
+
+def test_requests_arriving_while_others_run_join_later_batches():
+    fs = _inputs(SHAPES, 2100)
+    ref = _alone(SHAPES, fs)
+    srv = sft.Server(mem_budget=2 << 30, max_batch=4, max_inflight=3,
+                     variant=sft.sft_variant_init(**VARIANT))
+    outs = _outputs(SHAPES)
+    ids = []
+    for i in range(len(SHAPES)):              # a trickle: some arrive while earlier ones run
+        ids += _submit(srv, SHAPES[i:i + 1], fs[i:i + 1], outs[i:i + 1])
+        time.sleep(0.0005 * (i % 3))
+    for rid in ids:
+        assert srv.wait(rid, 60000) == sft.SFT_OK
+    _check_equal(outs, ref)
+    srv.destroy()
+
+
+def test_small_budget_evicts_idle_plans_and_makes_requests_wait():
+    shapes = [(2 ** 16, 30), (2 ** 17, 40), (3 ** 10, 20)] * 3
+    sizes = []
+    for N, s in set(shapes):
+        p = sft.sft_plan(N, s, sft.sft_variant_init(**VARIANT))
+        sizes.append(p.device_bytes)
+        p.destroy()
+    budget = max(1 << 20, int(1.6 * max(sizes)))     # room for one plan (or two small ones)
+    fs = _inputs(shapes, 2200)
+    ref = _alone(shapes, fs)
+    srv = sft.Server(mem_budget=budget, max_batch=4, max_inflight=2,
+                     variant=sft.sft_variant_init(**VARIANT))
+    outs = _outputs(shapes)
+    ids = _submit(srv, shapes, fs, outs)
+    for rid in ids:
+        assert srv.wait(rid, 120000) == sft.SFT_OK
+    _check_equal(outs, ref)
+    st = srv.stats()
+    assert st["completed"] == len(shapes) and st["failed"] == 0
+    assert st["plans_evicted"] > 0
+    assert st["arena_peak"] <= st["arena_bytes"] <= budget
+    srv.destroy()
+
+
+def test_request_larger_than_the_arena_fails_and_the_server_goes_on():
+    srv = sft.Server(mem_budget=1 << 20, max_batch=2, max_inflight=1,
+                     variant=sft.sft_variant_init(**VARIANT))
+    big, small = (2 ** 20, 200), (2 ** 12, 4)
+    fs = _inputs([big, small], 2300)
+    outs = _outputs([big, small])
+    r_big, r_small = _submit(srv, [big, small], fs, outs)
+    assert srv.wait(r_big, 60000) == sft.SFT_ENOMEM
+    assert srv.query(r_big)["state"] == "failed"
+    assert srv.wait(r_small, 60000) == sft.SFT_OK
+    _check_equal(outs[1:], _alone([small], fs[1:]))
+    assert int(outs[0][2].item()) == -1                     # untouched
+    srv.destroy()
+
+
+def test_invalid_requests_fail_without_stopping_the_server():
+    import torch
+    srv = sft.Server(mem_budget=256 << 20, max_batch=4, max_inflight=1,
+                     variant=sft.sft_variant_init(**VARIANT))
+    f = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    o = _outputs([(16, 4)])[0]
+    bad = [srv.submit(1, 1, f.data_ptr(), o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr()),
+           srv.submit(16, 0, f.data_ptr(), o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr())]
+    for rid in bad:
+        assert srv.wait(rid, 60000) == sft.SFT_EINVAL
+    with pytest.raises(sft.SftError):
+        srv.submit(16, 4, 0, o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr())
+    shapes = [(2 ** 14, 6)]
+    fs = _inputs(shapes, 2400)
+    outs = _outputs(shapes)
+    rid = _submit(srv, shapes, fs, outs)[0]
+    assert srv.wait(rid, 60000) == sft.SFT_OK
+    _check_equal(outs, _alone(shapes, fs))
+    assert srv.stats()["failed"] == 2
+    srv.destroy()
