@@ -667,24 +667,29 @@ def run_serving_workload(args, dev, sft, seed=5000, pool_size=32):
     for r in ids:
         srv.release(r)
 
-    # capacity: closed-loop burst
-    n_burst = 384
-    ks = [rng.randrange(pool_size) for _ in range(n_burst)]
+    # closed-loop bursts: the first builds the extra plans that concurrent requests of one shape
+    # need (a plan serves one request at a time); the second, with every plan resident, gives the
+    # capacity
+    n_burst = 1024
     o_b = outputs(n_burst)
-    t = time.perf_counter()
-    ids = [submit(k, o) for k, o in zip(ks, o_b)]
-    for r in ids:
-        srv.wait(r)
-    burst_s = time.perf_counter() - t
+    for phase in ("warm", "capacity"):
+        ks = [rng.randrange(pool_size) for _ in range(n_burst)]
+        t = time.perf_counter()
+        ids = [submit(k, o) for k, o in zip(ks, o_b)]
+        for r in ids:
+            srv.wait(r)
+        burst_s = time.perf_counter() - t
+        burst_batch = sum(srv.query(r)["batch_size"] for r in ids) / n_burst
+        for r in ids:
+            srv.release(r)
     capacity = n_burst / burst_s
-    for r in ids:
-        srv.release(r)
+    built_before_open_loop = srv.stats()["plans_built"]
 
     # open loop: Poisson arrivals at fractions of the capacity
     rates = []
     for frac in (0.3, 0.6, 0.9):
         rate = frac * capacity
-        n_req = int(min(1500, max(100, rate * 1.5)))
+        n_req = int(min(4000, max(200, rate * 1.5)))
         gaps = [rng.expovariate(rate) for _ in range(n_req)]
         ks = [rng.randrange(pool_size) for _ in range(n_req)]
         o_r = outputs(n_req)
@@ -756,7 +761,9 @@ def run_serving_workload(args, dev, sft, seed=5000, pool_size=32):
     return {"workload": f"Poisson arrivals; N log-uniform [2^16, 2^27], s log-uniform [8, 2048], "
                         f"SNR U[10, 40] dB, complex64; {pool_size} resident signals",
             "server": {"mem_budget_gib": 16, "max_batch": 32, "max_inflight": 3},
-            "capacity_sfts_per_s": capacity, "rates": rates,
+            "capacity_sfts_per_s": capacity, "capacity_mean_batch": burst_batch,
+            "rates": rates,
+            "plans_built_during_open_loop": st["plans_built"] - built_before_open_loop,
             "plans": {"built": st["plans_built"], "reused": st["plans_reused"],
                       "evicted": st["plans_evicted"], "arena_peak_gb": st["arena_peak"] / 1e9},
             "warm_s": warm_s, "warm_plans_built": st_warm["plans_built"],

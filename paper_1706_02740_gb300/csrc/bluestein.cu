@@ -137,19 +137,29 @@ struct ChirpIO {
   int p;          // 0 for an inactive transform slot: nothing is read or written
 };
 
-// v[r] *= w^r, w = e^{-2 pi i k / (SPAN RAD)}, using only the rows w^1, w^2, w^4, w^8 of the
-// pass's table: each element is multiplied by the entries of the set bits of r (at most four
-// products, so the rounding stays within a few ulps of the exactly rounded twiddle, and only one
-// table value is live).  Lanes with consecutive k read consecutive table entries.
+// v[r] *= w^r, w = e^{-2 pi i k / (SPAN RAD)}, r = 4a + c, from the pass's table rows w^1, w^2, w^3
+// (and w^4, w^8, w^12 below RAD): w^r is w^c, (w^4)^a, or their product, so every twiddle is at
+// most one rounding away from the exactly rounded table.  Lanes with consecutive k read
+// consecutive table entries.
 template <typename C, int M, int RAD, int SPAN>
 __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C* v) {
   constexpr int base = fft_tw_offset(M, SPAN);
+  if constexpr (RAD == 2) {
+    v[1] = cmul(v[1], __ldg(W + base + k));
+  } else {
+    const C w1 = __ldg(W + base + k), w2 = __ldg(W + base + SPAN + k),
+            w3 = __ldg(W + base + 2 * SPAN + k);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
 #pragma unroll
-  for (int row = 0; (1 << row) < RAD; ++row) {
-    const C pw = __ldg(W + base + row * SPAN + k);
-#pragma unroll
-    for (int r = 1; r < RAD; ++r)
-      if (r & (1 << row)) v[r] = cmul(v[r], pw);
+    for (int a = 1; a < RAD / 4; ++a) {
+      const C P = __ldg(W + base + (2 + a) * SPAN + k);     // w^{4a}
+      v[4 * a] = cmul(v[4 * a], P);
+      v[4 * a + 1] = cmul(v[4 * a + 1], cmul(P, w1));
+      v[4 * a + 2] = cmul(v[4 * a + 2], cmul(P, w2));
+      v[4 * a + 3] = cmul(v[4 * a + 3], cmul(P, w3));
+    }
   }
 }
 
@@ -279,10 +289,20 @@ bluestein_kernel(BatchView bv) {
   const C* W = reinterpret_cast<const C*>(d.fftw);
   C* s = buf + g * padded_len<M>();
   const ChirpIO<C> io{in, chirp, vhat, out, active ? p : 0};
-  for (int n = lt; n < io.p; n += TPT) s[pad16(n)] = cmul(__ldg(in + n), __ldg(chirp + n));
+  // p <= M/2: at most 8 input elements per thread.  (The unroll factors of this and the filter
+  // sweep are the largest that keep the FP32 builds free of register spills.)
+#pragma unroll 4
+  for (int it = 0; it < 8; ++it) {
+    const int n = lt + it * TPT;
+    if (n < io.p) s[pad16(n)] = cmul(__ldg(in + n), __ldg(chirp + n));
+  }
   __syncthreads();
   FFTPasses<C, M, 2, TPT, kFromInput, kToSmem>::run(s, lt, W, io);
-  for (int n = lt; n < M; n += TPT) s[pad16(n)] = cconj(cmul(s[pad16(n)], __ldg(vhat + n)));
+#pragma unroll 8
+  for (int it = 0; it < 16; ++it) {
+    const int n = lt + it * TPT;
+    s[pad16(n)] = cconj(cmul(s[pad16(n)], __ldg(vhat + n)));
+  }
   __syncthreads();
   radix2_first<C, M, TPT>(s, lt);
   FFTPasses<C, M, 2, TPT, kFromSmem, kToOutput>::run(s, lt, W, io);
@@ -375,8 +395,8 @@ std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
 int g_noalloc_n[kMaxDevices];           // length the tables currently hold (0 = none)
 
-// Twiddles in the per-pass layout of the chirp convolution's FFT (entry e^{-2 pi i b k / (SPAN R)}
-// of the pass at SPAN, row log2 b, column k), the chirp w_k = e^{-pi i (k^2 mod 2n) / n} (k < n)
+// Twiddles in the per-pass layout of the chirp convolution's FFT (entry e^{-2 pi i e_t k / (SPAN R)}
+// of the pass at SPAN, row t, column k), the chirp w_k = e^{-pi i (k^2 mod 2n) / n} (k < n)
 // and the wrapped conjugate chirp V (V[k] = V[M - k] = conj(w_k), zero elsewhere), in FP64 then
 // rounded.
 __global__ void noalloc_tables_kernel(int n, int M, float2* chirp, float2* V, float2* W) {
@@ -386,10 +406,10 @@ __global__ void noalloc_tables_kernel(int n, int M, float2* chirp, float2* V, fl
     if (i < entries) {
       int span = 2, off = 0;
       while (true) {
-        const int R = fft_radix(M, span), rows = fft_log2(R);
+        const int R = fft_radix(M, span), rows = fft_tw_rows(R);
         if (i < off + rows * span) {
           const int row = (i - off) / span, k = (i - off) - row * span;
-          sincospi(-2.0 * (double)((1 << row) * k) / (double)(span * R), &s, &c);
+          sincospi(-2.0 * (double)(fft_tw_exp(row) * k) / (double)(span * R), &s, &c);
           W[i] = make_float2((float)c, (float)s);
           break;
         }

@@ -318,9 +318,10 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
     std::vector<cd> fw(M, cd(1, 0));
     for (int span = 2; span < M; span *= fft_radix(M, span)) {
       const int R = fft_radix(M, span), base = fft_tw_offset(M, span);
-      for (int row = 0; (1 << row) < R; ++row)
+      for (int row = 0; row < fft_tw_rows(R); ++row)
         for (int k = 0; k < span; ++k)
-          fw[(size_t)base + (size_t)row * span + k] = expi_turns(-(int64_t)(1 << row) * k, (int64_t)span * R);
+          fw[(size_t)base + (size_t)row * span + k] =
+              expi_turns(-(int64_t)fft_tw_exp(row) * k, (int64_t)span * R);
     }
     put<cd>(blob, o_fftw, fw, fp64);
     std::vector<cd> ts(std::max(tw, 1), cd(1, 0));

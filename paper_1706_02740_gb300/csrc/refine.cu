@@ -3,13 +3,15 @@
 // The bulk path's length-p measurements come from FP32 chirp convolutions whose rounding is spread
 // over every bin.  For the s winners only, each needed bin
 //     Y_j[b] = (1/p_j) sum_k h_q(-pi + 2 pi k / p_j) e^{-2 pi i k b / p_j},   b = w mod p_j,
-// is recomputed directly from the same filtered samples with exactly rounded twiddles
-// e^{-2 pi i ((k b) mod p_j) / p_j}.
+// is recomputed directly from the same filtered samples with twiddles e^{-2 pi i ((k b) mod p_j) / p_j}
+// taken as products of two exactly rounded table entries.
 //
 // Work layout: one CTA per (shift, prime, chunk of kReChunk samples).  The CTA stages its chunk and
 // the prime's twiddle table in shared memory, and each thread sums the chunk against one winner's
-// twiddles: FMA blocks of 16 terms, added to the partial with compensation (Neumaier), in FP32.
-// The chunk partials, kept as
+// twiddles in blocks of 16 terms: the block's twiddles factor as w^{(k0 + 16 m) b} w^{j b}, so a
+// thread reads its 16 powers w^{j b} once per chunk and one block factor per 16 terms (exactly
+// rounded table entries both), takes FMA sums within blocks and adds the block values with
+// compensation (Neumaier), in FP32.  The chunk partials, kept as
 // (sum, compensation) pairs, are combined exactly enough in double-single arithmetic.  The
 // componentwise medians (eq. GSFT_Estimate), the sign (-1)^w and the division by g_hat_{w - q}
 // (Lemma Periodic_Gaussian_FC) are done in FP64, spread over many CTAs.  All integer indexing is
@@ -92,56 +94,62 @@ __global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
   for (int i = threadIdx.x; i < p; i += kReChunk) Wt[i] = __ldg(Wp + i);
   __syncthreads();
   float4* part = reinterpret_cast<float4*>(d.ybuf) + (int64_t)c * d.s * d.K;
+  const float4* S4 = reinterpret_cast<const float4*>(S);
   for (int t = threadIdx.x; t < cnt; t += kReChunk) {
     const int r = d.wlist[beg + t];
     const int b = mod_p32(d.winners[r].w, p);
-    // Blocks of kBlock terms are accumulated with plain FMAs in two interleaved chains (even and
-    // odd k); the block sums are added with compensation.  A block's rounding is a few ulps of
-    // kBlock terms, so the partial stays within ~eps * sqrt(p) * |h| of exact, two orders below
-    // the weakest estimates' tolerance.
-    constexpr int kBlock = 16;
-    int i0 = (k0 * b) % p;                        // k0 b < 2^26: 32-bit
-    int i1 = i0 + b;
-    if (i1 >= p) i1 -= p;
-    int b2 = b + b;
-    if (b2 >= p) b2 -= p;
+    // The chunk's sum in blocks of 16 consecutive k = k0 + 16 m + j:
+    //     sum_m w^{(k0 + 16 m) b} * sum_{j<16} h_{k0 + 16 m + j} w^{j b},   w = e^{-2 pi i / p},
+    // both factors exactly rounded table entries.  The inner sums are plain FMA chains of at most
+    // 16 products; the block values are added with compensation.  Per block the rounding is a few
+    // ulps of 16 terms, so the partial stays within ~eps * sqrt(p) * |h| of exact.
+    float2 R[16];
+    {
+      int ij = 0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        R[j] = Wt[ij];
+        ij += b;
+        if (ij >= p) ij -= p;
+      }
+    }
+    int ib = (k0 * b) % p;                        // k0 b < 2^26: 32-bit
+    const int b16 = (16 * b) % p;
     float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    for (int kb = 0; kb < klen; kb += kBlock) {
-      const int ke = min(klen, kb + kBlock);
-      float r0 = 0.f, m0 = 0.f, r1 = 0.f, m1 = 0.f;
-      int k = kb;
-      for (; k + 1 < ke; k += 2) {
-        const float2 a0 = S[k], a1 = S[k + 1];
-        const float2 w0 = Wt[i0], w1 = Wt[i1];
-        r0 = fmaf(a0.x, w0.x, r0);
-        r0 = fmaf(-a0.y, w0.y, r0);
-        m0 = fmaf(a0.x, w0.y, m0);
-        m0 = fmaf(a0.y, w0.x, m0);
-        r1 = fmaf(a1.x, w1.x, r1);
-        r1 = fmaf(-a1.y, w1.y, r1);
-        m1 = fmaf(a1.x, w1.y, m1);
-        m1 = fmaf(a1.y, w1.x, m1);
-        i0 += b2;
-        if (i0 >= p) i0 -= p;
-        i1 += b2;
-        if (i1 >= p) i1 -= p;
+    for (int kb = 0; kb < klen; kb += 16) {
+      float ur0 = 0.f, ui0 = 0.f, ur1 = 0.f, ui1 = 0.f;
+      if (kb + 16 <= klen) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 h = S4[(kb >> 1) + q];     // h_{2q}, h_{2q+1} of this block
+          const float2 r0 = R[2 * q], r1 = R[2 * q + 1];
+          ur0 = fmaf(h.x, r0.x, ur0);
+          ur0 = fmaf(-h.y, r0.y, ur0);
+          ui0 = fmaf(h.x, r0.y, ui0);
+          ui0 = fmaf(h.y, r0.x, ui0);
+          ur1 = fmaf(h.z, r1.x, ur1);
+          ur1 = fmaf(-h.w, r1.y, ur1);
+          ui1 = fmaf(h.z, r1.y, ui1);
+          ui1 = fmaf(h.w, r1.x, ui1);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (kb + j < klen) {
+            const float2 h = S[kb + j];
+            ur0 = fmaf(h.x, R[j].x, ur0);
+            ur0 = fmaf(-h.y, R[j].y, ur0);
+            ui0 = fmaf(h.x, R[j].y, ui0);
+            ui0 = fmaf(h.y, R[j].x, ui0);
+          }
+        }
       }
-      if (k < ke) {
-        const float2 a0 = S[k];
-        const float2 w0 = Wt[i0];
-        r0 = fmaf(a0.x, w0.x, r0);
-        r0 = fmaf(-a0.y, w0.y, r0);
-        m0 = fmaf(a0.x, w0.y, m0);
-        m0 = fmaf(a0.y, w0.x, m0);
-        // the odd chain's index is one step ahead: keep both aligned for the next block
-        i0 = i1;
-        i1 += b;
-        if (i1 >= p) i1 -= p;
-      }
-      neumaier_add(sr, cr, r0);
-      neumaier_add(sr, cr, r1);
-      neumaier_add(si, ci, m0);
-      neumaier_add(si, ci, m1);
+      const float ur = ur0 + ur1, ui = ui0 + ui1;
+      const float2 T = Wt[ib];
+      neumaier_add(sr, cr, fmaf(ur, T.x, -ui * T.y));
+      neumaier_add(si, ci, fmaf(ur, T.y, ui * T.x));
+      ib += b16;
+      if (ib >= p) ib -= p;
     }
     part[(int64_t)r * d.K + jj] = make_float4(sr, cr, si, ci);
   }

@@ -177,14 +177,18 @@ bool tuning_valid(const sft_tuning& t, std::string* why);
 
 // Twiddle tables of the chirp convolution's power-of-two FFT of length M.  After its radix-2 first
 // pass (no twiddles) the passes run at sub-transform lengths SPAN = 2, 2 R_1, ... with radix
-// R = fft_radix(M, SPAN) = min(16, M / SPAN), until SPAN = M.  The pass at SPAN owns log2(R) rows of
-// SPAN entries: row t, column k holds e^{-2 pi i 2^t k / (SPAN R)}.  The rows of all passes are
-// stored one after the other (fft_tw_offset); together they hold fewer than M entries.
+// R = fft_radix(M, SPAN) = min(16, M / SPAN), until SPAN = M.  The pass at SPAN owns
+// fft_tw_rows(R) rows of SPAN entries: row t, column k holds e^{-2 pi i e_t k / (SPAN R)} with
+// exponents e_t = 1, 2, 3, 4, 8, 12 (those below R); every power r = 4a + c < R is then one
+// product (w^4)^a w^c of two entries.  The rows of all passes are stored one after the other
+// (fft_tw_offset); together they hold fewer than M entries.
 __host__ __device__ constexpr int fft_radix(int M, int span) { return (M / span) >= 16 ? 16 : (M / span); }
 __host__ __device__ constexpr int fft_log2(int x) { return x <= 1 ? 0 : 1 + fft_log2(x / 2); }
+__host__ __device__ constexpr int fft_tw_rows(int R) { return R >= 16 ? 6 : R == 8 ? 4 : R == 4 ? 3 : 1; }
+__host__ __device__ constexpr int fft_tw_exp(int t) { return t < 3 ? t + 1 : 4 * (t - 2); }
 __host__ __device__ constexpr int fft_tw_offset(int M, int span) {
   int off = 0;
-  for (int s = 2; s < span; s *= fft_radix(M, s)) off += fft_log2(fft_radix(M, s)) * s;
+  for (int s = 2; s < span; s *= fft_radix(M, s)) off += fft_tw_rows(fft_radix(M, s)) * s;
   return off;
 }
 __host__ __device__ constexpr int fft_tw_entries(int M) { return fft_tw_offset(M, M); }
