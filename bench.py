@@ -486,9 +486,19 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not (args.timed_only or args.no_serving):
         serving = run_serving_workload(args, dev, sft)
 
-    cpu = None
+    cpu = precision = None
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.timed_only):
-        cpu = cpu_baseline_sample(N, s, sfts=2)
+        import numpy as np
+        f_host = _oracle_input(N, s)                     # complex64 values, held in complex128
+        f_dev = torch.from_numpy(f_host.astype(np.complex64)).to(dev)
+        pg = sft.sft_plan(N, s, variant(sft.SFT_FP32))
+        gw, gc, gn = sft.execute_torch(pg, f_dev)
+        torch.cuda.synchronize()
+        gw, gc, gn = gw.cpu().numpy(), gc.cpu().numpy(), int(gn.item())
+        pg.destroy()
+        del f_dev
+        cpu, res = cpu_baseline_sample(N, s, f=f_host)
+        precision = precision_vs_oracle(gw, gc, gn, res)
     if rank != 0:
         return
     pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
@@ -504,7 +514,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_us_per_launch": per_launch_us,
         "roofline": roof, "roofline_gather": roof_gather,
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
-        "cpu_baseline": cpu,
+        "cpu_baseline": cpu, "precision": precision,
     }
     if plain:
         out.update(plain)
@@ -782,24 +792,38 @@ def _oracle_input(N, s):
     return upcast(as_complex64(sig.f))
 
 
-def cpu_baseline_sample(N, s, sfts=2, f=None, plan=None):
-    """Times the oracle, as it stands, on sfts * ceil(c2) of Algorithm 1's shift iterations (each
-    is 1/ceil(c2) of one SFT; the final top-s is negligible) and scales to SFTs/s."""
-    from oracle.dsft import make_plan, ussft_shift
+def cpu_baseline_sample(N, s, f=None):
+    """Times the oracle, as it stands, on one full SFT (Algorithm 1: every shift iteration and the
+    final selection) of the workload; returns the baseline record and the oracle's result."""
+    from oracle.dsft import dsft, make_plan
     if f is None:
         f = _oracle_input(N, s)
-    if plan is None:
-        plan = make_plan(N, s, kappa=PLAN["kappa"], K=PLAN["K"], c_p=PLAN["c_p"],
-                         alpha=PLAN["alpha"], beta=PLAN["beta"], seed=PLAN["seed"])
-    nq = len(plan.shifts)
-    shifts = sfts * nq
+    plan = make_plan(N, s, kappa=PLAN["kappa"], K=PLAN["K"], c_p=PLAN["c_p"],
+                     alpha=PLAN["alpha"], beta=PLAN["beta"], seed=PLAN["seed"])
     t = time.perf_counter()
-    for k in range(shifts):
-        ussft_shift(f, plan, plan.shifts[k % nq])
+    res = dsft(f, plan)
     dt = time.perf_counter() - t
-    return {"value": (shifts / nq) / dt, "unit": "SFTs/s", "cores": 1, "kind": "oracle",
-            "sample": f"{shifts} of the {nq} shift iterations of one N={N}, s={s} SFT "
-                      f"({dt:.1f} s; numpy FP64, single thread)"}
+    return ({"value": 1.0 / dt, "unit": "SFTs/s", "cores": 1, "kind": "oracle",
+             "sample": f"one full N={N}, s={s} SFT of the workload ({dt:.1f} s; numpy FP64, "
+                       "single thread)"}, res)
+
+
+def precision_vs_oracle(w, c, n, res, tol=1e-5):
+    """Per-coefficient error of one GPU result against the oracle's result on the same input."""
+    import numpy as np
+    g = dict(zip(w[:n].tolist(), c[:n]))
+    o = dict(zip(res.freqs.tolist(), res.coefs))
+    common = sorted(set(g) & set(o))
+    diff = sorted(set(g) ^ set(o))
+    err = np.array([abs(g[k] - o[k]) / abs(o[k]) for k in common]) if common else np.zeros(1)
+    top = max(abs(o[k]) for k in o) if o else 1.0
+    return {"vs": "FP64 CPU oracle on the same input (one full SFT)", "tolerance": tol,
+            "support_common": len(common), "support_differs": len(diff),
+            "largest_differing_rel": (max(abs(g.get(k, o.get(k))) for k in diff) / top
+                                      if diff else 0.0),
+            "rel_err_max": float(err.max()), "rel_err_p50": float(np.median(err)),
+            "rel_err_p99": float(np.quantile(err, 0.99)),
+            "within_tolerance": bool(err.max() <= tol)}
 
 
 def run_reference(args, rank, world):
