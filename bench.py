@@ -493,12 +493,15 @@ def run_ours(args, rank, world, local_rank):
         f_dev = torch.from_numpy(f_host.astype(np.complex64)).to(dev)
         pg = sft.sft_plan(N, s, variant(sft.SFT_FP32))
         gw, gc, gn = sft.execute_torch(pg, f_dev)
+        rho = sft.residual_energy_torch(pg, f_dev, gc, gn)
         torch.cuda.synchronize()
         gw, gc, gn = gw.cpu().numpy(), gc.cpu().numpy(), int(gn.item())
         pg.destroy()
         del f_dev
         cpu, res = cpu_baseline_sample(N, s, f=f_host)
         precision = precision_vs_oracle(gw, gc, gn, res)
+        precision["residual_energy"] = rho
+        precision["noise_energy_share"] = 1.0 / (1.0 + 10.0 ** 3.0)   # SNR 30 dB
     if rank != 0:
         return
     pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]

@@ -73,6 +73,15 @@ typedef struct {
   uint64_t seed;
 } sft_variant;
 
+/*
+ * Theorem-parameter mode (Theorem total_convolution_error): every filtered sample is then within
+ * 3 ||f||_p N^{-r} of (g * f)(x).  Sets v->beta = 6 sqrt(r), v->kappa = ceil(6 r ln N / (sqrt(2) pi))
+ * + 1 (the theorem's window half-width) and v->alpha = v->beta (band-edge filter gain e^{-1/2},
+ * which meets Section 4's lower bound on alpha); other fields are unchanged.  Host only.
+ * SFT_EINVAL for r < 1, N < 36 r (outside the theorem's range) or a half-width above 48.
+ */
+sft_status sft_variant_theorem(sft_variant* v, int64_t N, double r);
+
 typedef struct sft_plan_s* sft_plan_t;
 
 /* Plan description returned by sft_plan_info (host memory, filled by the library). */
@@ -249,6 +258,21 @@ sft_status sft_plan_info(sft_plan_t plan, sft_plan_desc* out);
  * *bytes receives the buffer size.  Returns SFT_EINVAL for an unknown index.
  */
 sft_status sft_plan_debug_buffer(sft_plan_t plan, int32_t which, void** dev_ptr, size_t* bytes);
+
+/*
+ * Residual-energy check of a result (after the execution that produced it, in stream order).  With
+ * f-hat = F f, F[w, j] = (-1)^w e^{-2 pi i w j / N} / N (Section 2), Parseval's identity gives
+ * ||f-hat||_2^2 = ||f||_2^2 / N, so for the returned terms c_0..c_{count-1}
+ *     rho = 1 - (sum_r |c_r|^2) / (||f||_2^2 / N)
+ * is the fraction of the spectrum's energy the s-term approximation leaves out (the tail and the
+ * noise, when the estimates are exact; a negative rho flags over-estimated coefficients).  f_dev is
+ * the input of that execution (N elements of the plan's input type), coefs_dev / count_dev its
+ * outputs; *out_dev (one double, device memory) receives rho.  Reads f once; the sums of |f|^2 are
+ * formed in double-single FP32 (complex64 input) or FP64 (complex128) per thread and combined in
+ * FP64 in a fixed order, so the result is deterministic.  Two kernel launches on `stream`.
+ */
+sft_status sft_residual_energy(sft_plan_t plan, const void* f_dev, const void* coefs_dev,
+                               const int32_t* count_dev, double* out_dev, void* stream);
 
 /*
  * Per-stage timing of this plan's executions with CUDA events recorded on the execution stream

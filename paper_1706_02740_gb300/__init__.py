@@ -93,6 +93,8 @@ _lib = None
 
 EXPORTS = {
     "sft_variant_init": (ctypes.c_int, [ctypes.POINTER(sft_variant)]),
+    "sft_variant_theorem": (ctypes.c_int, [ctypes.POINTER(sft_variant), ctypes.c_int64,
+                                           ctypes.c_double]),
     "sft_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int32,
                                 ctypes.POINTER(sft_variant), ctypes.c_int32,
                                 ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
@@ -110,6 +112,8 @@ EXPORTS = {
     "sft_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int32)]),
     "sft_plan_launches": (ctypes.c_int64, [ctypes.c_void_p]),
+    "sft_residual_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sft_dft_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "sft_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p),
@@ -185,6 +189,13 @@ def sft_variant_init(**overrides) -> sft_variant:
         if not hasattr(v, k):
             raise TypeError(f"unknown variant field {k}")
         setattr(v, k, val)
+    return v
+
+
+def sft_variant_theorem(N: int, r: float, v: sft_variant | None = None, **overrides) -> sft_variant:
+    """A variant with the theorem parameters for error order N^-r (beta, kappa, alpha set)."""
+    v = v if v is not None else sft_variant_init(**overrides)
+    _check(load().sft_variant_theorem(ctypes.byref(v), int(N), float(r)))
     return v
 
 
@@ -448,6 +459,16 @@ def sft_tuning_default() -> dict:
     t = sft_tuning()
     load().sft_tuning_default(ctypes.byref(t))
     return t.as_dict()
+
+
+def residual_energy_torch(plan: Plan, f, coefs, count, stream=None) -> float:
+    """sft_residual_energy on CUDA tensors (the input and outputs of one execution); returns rho."""
+    import torch
+    out = torch.empty(1, dtype=torch.float64, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    _check(load().sft_residual_energy(plan.handle, f.data_ptr(), coefs.data_ptr(), count.data_ptr(),
+                                      out.data_ptr(), st.cuda_stream))
+    return float(out.item())
 
 
 def sft_plan_launches(plan: Plan) -> int:

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsft.so")
 SOURCES = ["api.cu", "batch.cu", "plan.cpp", "server.cpp", "resample.cu", "bluestein.cu", "identify.cu",
-           "select.cu", "refine.cu"]
+           "select.cu", "refine.cu", "energy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

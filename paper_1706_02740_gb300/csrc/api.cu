@@ -2,6 +2,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cmath>
 #include <new>
 #include <string>
 
@@ -185,6 +186,24 @@ sft_status sft_variant_init(sft_variant* v) {
   v->alpha = 1.5;
   v->beta = 1.5;
   v->seed = 0;
+  return SFT_OK;
+}
+
+sft_status sft_variant_theorem(sft_variant* v, int64_t N, double r) {
+  if (!v) { sft::set_error("variant is NULL"); return SFT_EINVAL; }
+  if (!(r >= 1.0) || (double)N < 36.0 * r) {
+    sft::set_error("theorem parameters need r >= 1 and N >= 36 r");
+    return SFT_EINVAL;
+  }
+  const double kPi = 3.14159265358979323846;
+  const double half = std::ceil(6.0 * r * std::log((double)N) / (std::sqrt(2.0) * kPi)) + 1.0;
+  if (half > sft::kMaxKappa) {
+    sft::set_error("theorem half-width " + std::to_string((int64_t)half) + " exceeds 48");
+    return SFT_EINVAL;
+  }
+  v->kappa = (int32_t)half;
+  v->beta = 6.0 * std::sqrt(r);
+  v->alpha = v->beta;
   return SFT_OK;
 }
 

@@ -353,6 +353,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   const size_t o_ybuf = soff;    soff = align256(soff + (size_t)d.nchunk * s * K * sizeof(double2));
   const size_t o_wlist = soff;   soff = align256(soff + (size_t)s * 4);
   const size_t o_woff = soff;    soff = align256(soff + (size_t)(nq + 1) * 4);
+  const size_t o_epart = soff;   soff = align256(soff + (size_t)kEnergyBlocks * sizeof(double));
   const size_t o_self = soff;    soff = align256(soff + sizeof(DevPlan));
   const size_t total = soff;
 
@@ -395,6 +396,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   d.ybuf = reinterpret_cast<double2*>(base + o_ybuf);
   d.wlist = reinterpret_cast<int32_t*>(base + o_wlist);
   d.woff = reinterpret_cast<int32_t*>(base + o_woff);
+  d.epart = reinterpret_cast<double*>(base + o_epart);
   P->d_dev = reinterpret_cast<DevPlan*>(base + o_self);
   e = mem ? mem->upload(P->d_dev, &d, sizeof(DevPlan))
           : cudaMemcpy(P->d_dev, &d, sizeof(DevPlan), cudaMemcpyHostToDevice);

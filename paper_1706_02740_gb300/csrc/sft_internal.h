@@ -87,6 +87,7 @@ struct DevPlan {
   double2* ybuf;              // [nchunk][s][K] partial sums of the re-estimated bins
   int32_t* wlist;             // [s] winner indices grouped by shift
   int32_t* woff;              // [nq + 1] start of each shift's group in wlist
+  double* epart;              // [kEnergyBlocks] partial sums of |f|^2 (residual-energy check)
 };
 
 constexpr int kReChunk = 256;   // samples per re-estimation CTA
@@ -94,6 +95,8 @@ constexpr int kResampleMaxThreads = 512;      // largest CTA of the kappa = 4 / 
 constexpr int kResampleGenericThreads = 128;
 constexpr int kBinMaxThreads = 512;    // identify / vote: one thread per bin, at most 512 per CTA
 constexpr int kRefineThreads = 64;
+constexpr int kEnergyBlocks = 304;     // residual-energy check: two CTAs per SM, fixed reduction order
+constexpr int kEnergyThreads = 512;
 
 // ---------------------------------------------------------------------------------------------
 // Batches.  One launch of a stage covers every signal of a batch; each signal has its own plan

@@ -72,6 +72,24 @@ def test_server_rejects_bad_configurations_without_touching_the_device(lib, fiel
     assert not h.value
 
 
+@pytest.mark.parametrize("N,r,kappa", [(2 ** 26, 1.0, 26), (2 ** 14, 1.0, 15), (3 ** 9, 2.0, 28),
+                                        (2 ** 20, 1.5, 30)])
+def test_theorem_variant(lib, N, r, kappa):
+    # Theorem total_convolution_error: beta = 6 sqrt(r), half-width ceil(6 r ln N / (sqrt 2 pi)) + 1
+    import math
+    v = sft.sft_variant_theorem(N, r)
+    assert v.kappa == kappa == math.ceil(6 * r * math.log(N) / (math.sqrt(2) * math.pi)) + 1
+    assert abs(v.beta - 6 * math.sqrt(r)) < 1e-15 and v.alpha == v.beta
+    assert (v.K, v.c_p, v.precision) == (5, 3.0, 0)
+
+
+@pytest.mark.parametrize("N,r", [(2 ** 26, 2.0), (100, 3.0), (2 ** 20, 0.5)])
+def test_theorem_variant_rejects_out_of_range(lib, N, r):
+    v = sft.sft_variant_init()
+    assert lib.sft_variant_theorem(ctypes.byref(v), N, r) == sft.SFT_EINVAL
+    assert v.kappa == 6 and v.beta == 1.5
+
+
 def test_variant_defaults(lib):
     v = sft.sft_variant_init()
     assert (v.kappa, v.precision, v.input, v.K) == (6, 0, 0, 5)

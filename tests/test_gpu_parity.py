@@ -139,6 +139,67 @@ def test_edge_cases_match_oracle(N, s, kappa, K, c_p):
         U.assert_same_output(g["freqs"][:n], g["coefs"][:n], res.freqs, res.coefs, 1e-11)
 
 
+@pytest.mark.parametrize("N,s,r", [(2 ** 14, 8, 1.0), (3 ** 9, 12, 1.0), (2 ** 14, 6, 2.0)])
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_theorem_parameter_mode_matches_oracle(N, s, r, prec):
+    """Theorem total_convolution_error's parameters (beta = 6 sqrt(r), half-width
+    ceil(6 r ln N / (sqrt 2 pi)) + 1: 31 to 57 taps, the generic resampling kernel) on both paths."""
+    import torch
+    sig = make_signal(N, s, 40 + int(r), "unit", 40.0)
+    f32 = as_complex64(sig.f)
+    f = f32 if prec == U.FP32 else upcast(f32)
+    v = sft.sft_variant_theorem(N, r, precision=prec, K=5, c_p=4.0, seed=2,
+                                input=0 if prec == U.FP32 else 1)
+    plan = sft.sft_plan(N, s, v)
+    info = plan.info()
+    assert info["kappa"] == v.kappa > 6
+    w, c, n = sft.execute_torch(plan, torch.from_numpy(f).cuda())
+    torch.cuda.synchronize()
+    n = int(n.item())
+    oplan = O.make_plan(N, s, kappa=info["kappa"], alpha=v.alpha, beta=v.beta,
+                        primes=info["primes"], small=info["small"], n_shifts=info["n_shifts"])
+    assert abs(oplan.c1 - info["c1"]) <= 1e-15 * oplan.c1
+    # stage 1: every filtered sample against the oracle's direct per-tap sum
+    got = U.debug_arrays(sft, plan, info)[0]
+    ref = U.oracle_samples(upcast(f32), oplan, info)
+    tol = 2e-6 if prec == U.FP32 else 1e-13
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    res = O.dsft(upcast(f32), oplan)
+    assert n == len(res.freqs)
+    U.assert_same_output(w.cpu().numpy()[:n], c.cpu().numpy()[:n], res.freqs, res.coefs,
+                         1e-5 if prec == U.FP32 else 1e-11)
+    assert set(res.freqs.tolist()) == set(sig.omega.tolist())
+    plan.destroy()
+
+
+@pytest.mark.parametrize("N,s,snr,prec,c128", [(100003, 12, 20.0, U.FP32, False),
+                                               (2 ** 16, 8, None, U.FP32, False),
+                                               (3 ** 10, 20, 20.0, U.FP64, True),
+                                               (2 ** 15 + 3, 10, 30.0, U.FP32, True)])
+def test_residual_energy_follows_parseval(N, s, snr, prec, c128):
+    """rho = 1 - sum |c|^2 / (||f||^2 / N) against the same sums in float64 on the host."""
+    import torch
+    sig = make_signal(N, s, 77, "unit", snr)
+    f = upcast(as_complex64(sig.f)) if c128 else as_complex64(sig.f)
+    v = sft.sft_variant_init(precision=prec, K=5, c_p=5.0, seed=4, input=1 if c128 else 0)
+    plan = sft.sft_plan(N, s, v)
+    ft = torch.from_numpy(f).cuda()
+    w, c, n = sft.execute_torch(plan, ft)
+    rho = sft.residual_energy_torch(plan, ft, c, n)
+    nn = int(n.item())
+    fh = f.astype(np.complex128)
+    ref = 1.0 - np.sum(np.abs(c.cpu().numpy()[:nn]) ** 2) / (np.sum(np.abs(fh) ** 2) / N)
+    assert abs(rho - ref) <= 1e-12
+    if snr is None:
+        assert abs(rho) <= 1e-5                  # exactly s-sparse: the s terms carry it all
+    else:
+        # the noise's share of the energy, less what the estimates absorb (each bin aliases the
+        # noise of ~L/p frequencies, amplified by 1/g_hat towards the band edges)
+        noise = 1.0 / (1.0 + 10.0 ** (snr / 10.0))
+        assert abs(rho) < 3.0 * noise
+    plan.destroy()
+
+
 def test_repeated_execution_is_deterministic():
     N, s = 2 ** 17, 16
     sig = make_signal(N, s, 9, "unit", 30.0)
