@@ -5,9 +5,9 @@ complex Gaussian noise at 30 dB SNR.
 
 A step is one pass of the whole hot path (resampling, chirp-convolution DFTs, residues + CRT,
 vote + medians, selections, re-estimation) over one batch of `batch` signals: one
-sft_batch_execute, i.e. one launch per stage for all of them.  Eight distinct 512 MiB inputs
-rotate, so the windows gathered in one step (8 x ~70 MB) far exceed the 129 MB L2 and none is
-left there by the previous step.
+sft_batch_execute, i.e. one launch per stage for all of them (16 by default).  Distinct 512 MiB
+inputs rotate (16 by default), so the windows gathered in one step (16 x ~120 MB of DRAM traffic) far
+exceed the 129 MB L2 and none is left there by the previous step.
 
   python bench.py [--gpus N --steps K --warmup W]          # this library
   python bench.py --impl reference [--steps K --warmup W]  # the CPU oracle on host cores
@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 N_DEFAULT, S_DEFAULT = 2 ** 26, 1000
 PLAN = dict(kappa=6, K=5, c_p=3.0, alpha=1.5, beta=1.5, seed=1)
 METRIC = "SFTs/sec at N=2^26, s=1000 (p50/p99 latency, vs plain FP64 path and cuFFT; % HBM roofline)"
-N_INPUTS = 8
+N_INPUTS = 16
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--s", type=int, default=S_DEFAULT)
-    ap.add_argument("--batch", type=int, default=8, help="SFTs per step (one batched execution)")
+    ap.add_argument("--batch", type=int, default=16, help="SFTs per step (one batched execution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inputs", type=int, default=N_INPUTS,
                     help="distinct resident inputs that rotate (each N complex64)")
@@ -392,9 +392,14 @@ def run_ours(args, rank, world, local_rank):
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         fl = B * dft_flops(info)
         ach = fl / (per_launch_us["chirp_dft"] * 1e-6) / 1e12
+        dft_traffic = profiled_traffic("bluestein_n2p26_s1000",
+                                       source_digest("bluestein.cu", "cplx.cuh", "sft_internal.h"))
         roof = {"kernel": "bluestein (chirp-convolution DFT)", "bound": "alu", "achieved": ach,
-                "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                "traffic": dft_traffic * B if dft_traffic is not None else None,
                 "algorithmic_flops": fl,
+                "units": f"{B} SFTs x {info['n_shifts'] * info['n_sub'] * info['K']} transforms "
+                         f"of length {info['fft_size']} per launch",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
     else:
         roof = dict(roof_gather)
