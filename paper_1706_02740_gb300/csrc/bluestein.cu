@@ -172,23 +172,35 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C
 // LOAD == kFromInput is the first pass after the radix-2 first pass of a transform whose input
 // x vanishes from p <= M/2 on: that radix-2 pass only duplicates (y[2i] = y[2i + 1] = x[i]), so it
 // is never run and this pass reads y[n] = x[n / 2] from the first p entries of shared memory.
+// Offsets of an item's elements: (a + 16 e) >> 4 = (a >> 4) + e, so when the element stride d is
+// a multiple of 16, pad16(a + r d) = pad16(a) + r (d + d / 16): one padded base per item and
+// compile-time offsets instead of a shift and an add per access.
 template <typename C, int M, int RAD, int SPAN, int TPT, int LOAD, int STORE>
 __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict__ W,
                                               const ChirpIO<C>& io) {
   constexpr int ITEMS = M / RAD / TPT;
+  constexpr int STRIDE = M / RAD;          // input stride of an item's elements
   C v[ITEMS * RAD];
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     const int i = lt + it * TPT;
     const int k = i & (SPAN - 1);
+    if (LOAD == kFromInput) {
+      // element n = i + r STRIDE reads x[n / 2] = x[(i >> 1) + r STRIDE / 2] (STRIDE is even)
+      const int m0 = i >> 1, pm0 = pad16(m0);
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) {
-      const int n = i + r * (M / RAD);
-      if (LOAD == kFromInput) {
-        const int m = n >> 1;
-        v[it * RAD + r] = (m < io.p) ? s[pad16(m)] : czero<C>();
-      } else {
-        v[it * RAD + r] = s[pad16(n)];
+      for (int r = 0; r < RAD; ++r) {
+        const int m = m0 + r * (STRIDE / 2);
+        const int pm = (STRIDE / 2) % 16 == 0 ? pm0 + r * ((STRIDE / 2) + (STRIDE / 2) / 16)
+                                               : pad16(m);
+        v[it * RAD + r] = (m < io.p) ? s[pm] : czero<C>();
+      }
+    } else {
+      const int p0 = pad16(i);
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        const int pn = STRIDE % 16 == 0 ? p0 + r * (STRIDE + STRIDE / 16) : pad16(i + r * STRIDE);
+        v[it * RAD + r] = s[pn];
       }
     }
     apply_twiddles<C, M, RAD, SPAN>(W, k, &v[it * RAD]);
@@ -200,13 +212,18 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
     const int i = lt + it * TPT;
     const int k = i & (SPAN - 1);
     const int j0 = (i - k) * RAD + k;
+    if (STORE == kToOutput) {
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) {
-      const int c = j0 + r * SPAN;
-      if (STORE == kToOutput) {
+      for (int r = 0; r < RAD; ++r) {
+        const int c = j0 + r * SPAN;
         if (c < io.p) io.out[c] = cmul(cconj(v[it * RAD + r]), __ldg(io.chirp + c));
-      } else {
-        s[pad16(c)] = v[it * RAD + r];
+      }
+    } else {
+      const int p0 = pad16(j0);
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        const int pc = SPAN % 16 == 0 ? p0 + r * (SPAN + SPAN / 16) : pad16(j0 + r * SPAN);
+        s[pc] = v[it * RAD + r];
       }
     }
   }
@@ -238,7 +255,8 @@ __device__ __forceinline__ void radix2_first(C* s, int lt) {
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     const int i = lt + it * TPT;
-    const C a = s[pad16(i)], b = s[pad16(i + M / 2)];
+    const int pi = pad16(i);
+    const C a = s[pi], b = s[pi + M / 2 + M / 32];       // pad16(i + M/2), M/2 a multiple of 16
     v[2 * it] = cadd(a, b);
     v[2 * it + 1] = csub(a, b);
   }
@@ -246,8 +264,9 @@ __device__ __forceinline__ void radix2_first(C* s, int lt) {
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     const int i = lt + it * TPT;
-    s[pad16(2 * i)] = v[2 * it];
-    s[pad16(2 * i + 1)] = v[2 * it + 1];
+    const int pe = pad16(2 * i);                          // 2i even: 2i + 1 pads to pe + 1
+    s[pe] = v[2 * it];
+    s[pe + 1] = v[2 * it + 1];
   }
   __syncthreads();
 }
