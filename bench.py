@@ -55,6 +55,8 @@ def parse():
                     help="only the warm-up and timed steps (for profiler launch lists)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-size batch leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--only", choices=["batched", "serving"], default=None,
+                    help="run one extra leg alone and print its JSON")
     ap.add_argument("--study", choices=["sweep-n", "sweep-s", "noise"], default=None,
                     help="the paper's experiments instead of the bench line (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
@@ -314,20 +316,28 @@ def run_ours(args, rank, world, local_rank):
         tuning = batch.autotune([inputs[i % n_in].data_ptr() for i in range(B)], w_ptrs, c_ptrs,
                                 n_ptrs, stream.cuda_stream, reps=3)
 
-    # latency of one request alone (one plan, one SFT at a time)
+    # latency of one request alone (one plan, one SFT at a time; the plan's CUDA graph, and direct
+    # launches for reference)
     p0 = plans[0]
-    for i in range(0 if args.timed_only else 3):
-        sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0], stream.cuda_stream)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(0 if args.timed_only else 64)]
-    for i, (a, b) in enumerate(ev):
-        a.record()
-        sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
-                        stream.cuda_stream)
-        b.record()
-    torch.cuda.synchronize()
-    single = sorted(a.elapsed_time(b) for a, b in ev) or [float("nan")]
+
+    def single_latency(graph):
+        sft.sft_plan_graph(p0, graph)
+        for i in range(0 if args.timed_only else 3):
+            sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
+                            stream.cuda_stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(0 if args.timed_only else 64)]
+        for i, (a, b) in enumerate(ev):
+            a.record()
+            sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
+                            stream.cuda_stream)
+            b.record()
+        torch.cuda.synchronize()
+        sft.sft_plan_graph(p0, False)
+        return sorted(a.elapsed_time(b) for a, b in ev) or [float("nan")]
+    single = single_latency(True)
+    single_direct = single_latency(False)
 
     # per-stage times: CUDA events between the stages, direct launches (the graph has none)
     n_prof = 0 if args.timed_only else 10
@@ -519,7 +529,8 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(args, B), tuning=tuning, graph=True),
         "latency_ms": {"p50": pct(single, 0.5), "p99": pct(single, 0.99),
-                       "what": "device time of one SFT executed alone (sft_execute)"},
+                       "direct_launches_p50": pct(single_direct, 0.5),
+                       "what": "device time of one SFT executed alone (sft_execute, plan graph)"},
         "step_ms": {"p50": pct(step_ms, 0.5), "p99": pct(step_ms, 0.99),
                     "what": f"one batched execution of {B} SFTs"},
         "stages_us_per_launch": per_launch_us,
@@ -670,7 +681,7 @@ def run_serving_workload(args, dev, sft, seed=5000, pool_size=32):
     t = time.perf_counter()
     ids = [submit(k, o_warm[k]) for k in range(pool_size)]
     for r in ids:
-        srv.wait(r)
+        srv.wait(r, 120000)
     warm_s = time.perf_counter() - t
     st_warm = srv.stats()
     # served results equal the same plans run alone
@@ -698,7 +709,7 @@ def run_serving_workload(args, dev, sft, seed=5000, pool_size=32):
         t = time.perf_counter()
         ids = [submit(k, o) for k, o in zip(ks, o_b)]
         for r in ids:
-            srv.wait(r)
+            srv.wait(r, 120000)
         burst_s = time.perf_counter() - t
         burst_batch = sum(srv.query(r)["batch_size"] for r in ids) / n_burst
         for r in ids:
@@ -729,7 +740,7 @@ def run_serving_workload(args, dev, sft, seed=5000, pool_size=32):
             lags.append((time.perf_counter() - due) * 1e3)
             ids.append(submit(k, o))
         for r in ids:
-            srv.wait(r)
+            srv.wait(r, 120000)
         t_end = time.perf_counter()
         infos = [srv.query(r) for r in ids]
         lat = sorted(q["latency_ms"] for q in infos)
@@ -803,7 +814,7 @@ def run_study(args):
     support is exact (Section 5.4).  Inputs as in Section 5.1: s frequencies uniform over B, unit
     magnitude, random phase, f by an inverse DFT (complex64).  DMSFT-4 and DMSFT-6 (kappa = 4, 6),
     with (K, c_p) tuned per point as Section 5.1 prescribes (see the ladder below).  Times: device
-    time of one request alone (sft_execute), median over the trials; cuFFT: torch.fft.fft of the
+    time of one request alone (sft_execute replaying the plan's CUDA graph), median over the trials; cuFFT: torch.fft.fft of the
     same input, alone and with the (-1)^w/N rescale and top-s."""
     import numpy as np
     import torch
@@ -848,8 +859,10 @@ def run_study(args):
         for t in range(trials):
             f, omega, coef = make_device_signal(N, s, 6000 + 97 * t + s, "unit", snr, dev)
             w, c, n = sft.execute_torch(plan, f)
+            sft.sft_plan_graph(plan, True)
             ms = timed(lambda: sft.sft_execute(plan, f.data_ptr(), w.data_ptr(), c.data_ptr(),
                                                n.data_ptr(), torch.cuda.current_stream().cuda_stream))
+            sft.sft_plan_graph(plan, False)
             times.append(ms)
             if stages and t == 0:
                 sft.sft_plan_profile(plan, True)
@@ -994,6 +1007,17 @@ def main():
     if args.study:
         if rank == 0:
             run_study(args)
+        return
+    if args.only:
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_1706_02740_gb300 as sft
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        leg = run_batched_workload if args.only == "batched" else run_serving_workload
+        print(json.dumps({args.only: leg(args, dev, sft)}), flush=True)
         return
     if world > 1:
         import torch

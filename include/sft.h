@@ -275,6 +275,16 @@ sft_status sft_residual_energy(sft_plan_t plan, const void* f_dev, const void* c
                                const int32_t* count_dev, double* out_dev, void* stream);
 
 /*
+ * enable = 1: later sft_execute calls of this plan (with non-NULL outputs) replay its kernel
+ * launches as one CUDA graph, captured at the first such call on a private stream (capturing runs
+ * nothing): one graph launch instead of a dozen kernel launches, so the device no longer waits on
+ * the host between stages.  Each call still uploads its own pointers first (stream-ordered), so
+ * inputs and outputs may change from call to call.  Per-stage profiling is off while graphs are
+ * on.  enable = 0 returns to direct launches.  Results are identical either way.
+ */
+sft_status sft_plan_graph(sft_plan_t plan, int32_t enable);
+
+/*
  * Per-stage timing of this plan's executions with CUDA events recorded on the execution stream
  * between the stages (enable = 1 creates the events, 0 releases them).  Stages: 0 resampling,
  * 1 chirp-convolution DFTs, 2 residues + CRT, 3 vote + medians, 4 selections, 5 re-estimation.

@@ -109,6 +109,7 @@ EXPORTS = {
                                              ctypes.POINTER(ctypes.c_size_t)]),
     "sft_last_error": (ctypes.c_char_p, []),
     "sft_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "sft_plan_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "sft_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int32)]),
     "sft_plan_launches": (ctypes.c_int64, [ctypes.c_void_p]),
@@ -271,6 +272,11 @@ def sft_plan_info(plan: Plan) -> dict:
 
 
 STAGES = ("resample", "chirp_dft", "identify", "vote", "select", "refine")
+
+
+def sft_plan_graph(plan: Plan, enable: bool = True):
+    """Replay the plan's launches as a CUDA graph in later sft_execute calls."""
+    _check(load().sft_plan_graph(plan.handle, 1 if enable else 0))
 
 
 def sft_plan_profile(plan: Plan, enable: bool = True):

@@ -226,6 +226,7 @@ sft_status sft_plan(sft_plan_t* out, int64_t N, int32_t s, const sft_variant* v,
 
 sft_status sft_plan_destroy(sft_plan_t plan) {
   if (!plan) return SFT_OK;
+  if (plan->P.solo) sft_batch_destroy(plan->P.solo);
   sft::profile_release(plan->P.prof);
   sft::free_plan(&plan->P);
   delete plan;
@@ -276,6 +277,15 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
     sft::set_error("f is not aligned to its element size");
     return SFT_EINVAL;
   }
+  if (P.graph_on && all) {
+    // replay of the plan's captured launches (its batch of one), after this call's pointer upload
+    const int64_t before = sft_batch_launches(P.solo);
+    void* cw = out_coefs_dev;
+    const sft_status st = sft_batch_execute(P.solo, &f_dev, &out_freqs_dev, &cw, &out_count_dev,
+                                            stream);
+    P.launches += sft_batch_launches(P.solo) - before;
+    return st;
+  }
   sft::BatchView bv;
   memset(&bv, 0, sizeof(bv));
   bv.plans = P.d_dev;
@@ -293,6 +303,19 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
     sft::set_error(std::string("CUDA launch failed: ") + cudaGetErrorString(e));
     return SFT_ECUDA;
   }
+  return SFT_OK;
+}
+
+sft_status sft_plan_graph(sft_plan_t plan, int32_t enable) {
+  if (!plan) { sft::set_error("plan is NULL"); return SFT_EINVAL; }
+  Plan& P = plan->P;
+  if (enable && !P.solo) {
+    sft_plan_t one = plan;
+    const sft_status st = sft_batch_create(&P.solo, &one, 1);
+    if (st != SFT_OK) return st;
+    sft_batch_graph(P.solo, 1);
+  }
+  P.graph_on = enable != 0;
   return SFT_OK;
 }
 

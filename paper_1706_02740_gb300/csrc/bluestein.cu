@@ -337,8 +337,7 @@ cudaError_t launch_MB(const BatchView& bv, const LaunchSet& ls, cudaStream_t st,
   const int G = ls.tune.dft_per_cta[cls];
   const int threads = (M / 16) * G;
   const size_t smem = (size_t)G * padded_len<M>() * sizeof(C);
-  cudaError_t e = cudaFuncSetAttribute(bluestein_kernel<R, M, MINB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dynamic_smem<bluestein_kernel<R, M, MINB>>(smem);
   if (e != cudaSuccess) return e;
   BatchView v = bv;
   v.blk = ls.blk[kStBluestein0 + cls];

@@ -209,11 +209,8 @@ cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t
   group_winners_kernel<<<ls.blocks[kStOne], 256, 0, st>>>(v);
   v.blk = ls.blk[kStReest];
   const size_t smem = (size_t)(kReChunk + ls.pmax) * sizeof(float2);
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(reestimate_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const cudaError_t e = ensure_dynamic_smem<reestimate_kernel>(smem);
+  if (e != cudaSuccess) return e;
   reestimate_kernel<<<ls.blocks[kStReest], kReChunk, smem, st>>>(v);
   v.blk = ls.blk[kStRefine];
   refine_values_kernel<<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);

@@ -62,8 +62,11 @@ __device__ __forceinline__ void decode_node(const DevPlan& d, int64_t node, int&
   }
   const int rnd = (2 * G >= 3 * PP) ? 2 : ((2 * G >= PP) ? 1 : 0);
   g.d0 = G - rnd * PP;
+  // I = floor(k1 N / p) + floor(k2 N / t) < 2N, so jp < 2N + 2: two reductions suffice (N >= 2)
   int64_t jp = I + rnd;
-  while (jp >= d.N) jp -= d.N;
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    if (jp >= d.N) jp -= d.N;
   g.jp = jp;
   g.PP = PP;
 }

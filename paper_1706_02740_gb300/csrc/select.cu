@@ -285,9 +285,6 @@ __global__ void __launch_bounds__(64) zero_kernel(BatchView bv) {
   for (int i = threadIdx.x; i < d.nq + 4; i += 64) d.counters[i] = 0;
 }
 
-cudaError_t set_smem(const void* fn) {
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
-}
 
 BatchView with_blk(const BatchView& bv, const LaunchSet& ls, int kind);
 
@@ -307,8 +304,8 @@ cudaError_t launch_zero(const BatchView& bv, const LaunchSet& ls, cudaStream_t s
 }
 
 cudaError_t launch_select(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
-  cudaError_t e = set_smem((const void*)shift_select);
-  if (e == cudaSuccess) e = set_smem((const void*)global_select);
+  cudaError_t e = ensure_dynamic_smem<shift_select>(kSortSmem);
+  if (e == cudaSuccess) e = ensure_dynamic_smem<global_select>(kSortSmem);
   if (e != cudaSuccess) return e;
   shift_select<<<ls.blocks[kStShift], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStShift));
   ++*launched;
@@ -329,7 +326,7 @@ cudaError_t launch_select(const BatchView& bv, const LaunchSet& ls, cudaStream_t
 
 cudaError_t launch_finalize(const BatchView& bv, const LaunchSet& ls, cudaStream_t st,
                             int* launched) {
-  cudaError_t e = set_smem((const void*)finalize_sorted);
+  cudaError_t e = ensure_dynamic_smem<finalize_sorted>(kSortSmem);
   if (e != cudaSuccess) return e;
   finalize_sorted<<<ls.blocks[kStOne], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStOne));
   ++*launched;

@@ -120,6 +120,7 @@ struct Slot {                        // one batched execution in flight
   size_t bytes = 0;
   bool busy = false;
   bool done = false;                 // set by the completion callback (under the server mutex)
+  bool dead = false;                 // its stream failed: never used again
   Clock::time_point t_done;
   std::vector<int64_t> reqs;
   std::vector<Entry*> plans;
@@ -266,6 +267,32 @@ cudaError_t launch_slot(Server& S, Slot& sl, const std::vector<Request*>& rq, in
   return cudaLaunchHostFunc(sl.st, on_slot_done, &sl);
 }
 
+// Wait on the scheduler's condition until pred() holds.  Every 20 ms without progress the busy
+// slots' streams are queried (outside the lock): a stream in an error state will never run its
+// completion callback, so its slot is marked dead and finished, and its requests fail.
+template <typename Pred>
+void wait_or_poll(Server& S, std::unique_lock<std::mutex>& lk, Pred pred) {
+  while (!pred()) {
+    if (S.cv.wait_for(lk, std::chrono::milliseconds(20)) != std::cv_status::timeout) continue;
+    std::vector<Slot*> busy;
+    for (Slot* sl : S.slots)
+      if (sl->busy && !sl->done) busy.push_back(sl);
+    if (busy.empty()) continue;
+    lk.unlock();
+    std::vector<Slot*> failed;
+    for (Slot* sl : busy) {
+      const cudaError_t e = cudaStreamQuery(sl->st);
+      if (e != cudaSuccess && e != cudaErrorNotReady) failed.push_back(sl);
+    }
+    lk.lock();
+    for (Slot* sl : failed) {
+      sl->dead = true;
+      sl->done = true;
+      sl->t_done = Clock::now();
+    }
+  }
+}
+
 void scheduler(Server* Sp) {
   Server& S = *Sp;
   cudaSetDevice(S.device);
@@ -278,11 +305,20 @@ void scheduler(Server* Sp) {
       for (int64_t id : sl->reqs) {
         auto it = S.reqs.find(id);
         if (it == S.reqs.end()) continue;
-        it->second.state = 2;
         it->second.t_done = sl->t_done;
-        ++S.stats.completed;
+        if (sl->dead) {
+          it->second.state = 3;
+          it->second.status = SFT_ECUDA;
+          ++S.stats.failed;
+        } else {
+          it->second.state = 2;
+          ++S.stats.completed;
+        }
       }
-      for (Entry* e : sl->plans) release_plan(S, e);
+      // plans of a failed stream may still be referenced by work the device never finished:
+      // they stay out of the idle list (the server is unusable after a device fault anyway)
+      if (!sl->dead)
+        for (Entry* e : sl->plans) release_plan(S, e);
       sl->reqs.clear();
       sl->plans.clear();
       sl->busy = sl->done = false;
@@ -290,16 +326,34 @@ void scheduler(Server* Sp) {
     }
     if (retired) S.done_cv.notify_all();
     Slot* free_slot = nullptr;
-    bool any_busy = false;
+    bool any_busy = false, any_alive = false;
     for (Slot* sl : S.slots) {
+      if (sl->dead) continue;
+      any_alive = true;
       if (sl->busy) any_busy = true;
       else if (!free_slot) free_slot = sl;
     }
+    if (!any_alive) {
+      // every stream failed: fail what is queued
+      for (int64_t id : S.queue) {
+        Request& r = S.reqs[id];
+        r.state = 3;
+        r.status = SFT_ECUDA;
+        r.t_done = Clock::now();
+        ++S.stats.failed;
+      }
+      S.queue.clear();
+      S.done_cv.notify_all();
+      if (S.stop) break;
+      wait_or_poll(S, lk, [&] { return S.stop || !S.queue.empty(); });
+      continue;
+    }
     if (S.stop && S.queue.empty() && !any_busy) break;
     if (!free_slot || S.queue.empty()) {
-      S.cv.wait(lk, [&] {
+      wait_or_poll(S, lk, [&] {
         bool busy = false, idle = false;
         for (Slot* sl : S.slots) {
+          if (sl->dead) continue;
           if (sl->busy && sl->done) return true;
           (sl->busy ? busy : idle) = true;
         }
@@ -391,7 +445,7 @@ void scheduler(Server* Sp) {
     if (!failed.empty() || ce != cudaSuccess) S.done_cv.notify_all();
     if (arq.empty() && !deferred.empty()) {
       // nothing could start: wait for running work to finish (it frees memory)
-      S.cv.wait(lk, [&] {
+      wait_or_poll(S, lk, [&] {
         bool busy = false;
         for (Slot* sl : S.slots) {
           if (sl->busy && sl->done) return true;

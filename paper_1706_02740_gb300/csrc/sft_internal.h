@@ -36,7 +36,7 @@ struct Pooled {
   int32_t pad;
 };
 
-// Everything a kernel needs about a plan; passed by value.
+// Everything a kernel needs about a plan (read by the kernels from device memory).
 struct DevPlan {
   int64_t N;
   int32_t s, kappa, K, nT, nq, nsub;
@@ -230,6 +230,8 @@ struct Plan {
   std::vector<void*> allocations;
   DeviceMemory* mem = nullptr;   // nullptr: allocations came from cudaMalloc
   int device = 0;
+  sft_batch_t solo = nullptr;    // batch of this plan alone, for CUDA-graph execution
+  bool graph_on = false;
 };
 
 // Kernel launch wrappers: one launch per stage for all signals of bv (each returns
@@ -254,6 +256,25 @@ int signal_blocks(const DevPlan& d, int kind, const sft_tuning& t);
 LaunchSet single_launch_set(const DevPlan& d);
 cudaError_t run_stages(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
                        cudaStream_t st, cudaEvent_t* ev, int* launched);
+
+#ifdef __CUDACC__
+// Raise kernel KERNEL's dynamic shared-memory limit to at least `bytes` on the current device,
+// calling the runtime only when the limit must grow.  The kernel itself is the template argument,
+// so every kernel keeps its own record (kernels of one signature share a type, not a record).
+template <auto KERNEL>
+cudaError_t ensure_dynamic_smem(size_t bytes) {
+  constexpr int kDevices = 64;
+  static int granted[kDevices] = {};            // bytes granted so far (updates are idempotent)
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kDevices && granted[dev] >= (int)bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < kDevices) granted[dev] = (int)bytes;
+  return e;
+}
+#endif
 
 cudaEvent_t* profile_slot(Profiler& pr);
 sft_status profile_enable(Profiler& pr, int enable);

@@ -213,3 +213,31 @@ def test_invalid_tunings_are_rejected_and_change_nothing():
     batch.destroy()
     for p in plans:
         p.destroy()
+
+
+def test_plan_graph_replay_equals_direct_execution():
+    import torch
+    N, s = 65521, 12
+    sigs = [make_signal(N, s, 1300 + i, "unit", 30.0) for i in range(3)]
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in sigs]
+    plan = sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=5.0, seed=8))
+    direct = []
+    for f in fs:
+        w, c, n = sft.execute_torch(plan, f)
+        torch.cuda.synchronize()
+        direct.append((w.cpu().numpy(), c.cpu().numpy(), int(n.item())))
+    sft.sft_plan_graph(plan, True)
+    l0 = sft.sft_plan_launches(plan)
+    for rep in range(2):
+        for f, (rw, rc, rn) in zip(fs, direct):
+            w, c, n = sft.execute_torch(plan, f)          # fresh output buffers every call
+            torch.cuda.synchronize()
+            assert int(n.item()) == rn
+            assert np.array_equal(w.cpu().numpy(), rw) and np.array_equal(c.cpu().numpy(), rc)
+    per = (sft.sft_plan_launches(plan) - l0) / 6
+    assert per >= 10 and per == int(per)
+    sft.sft_plan_graph(plan, False)
+    w, c, n = sft.execute_torch(plan, fs[0])
+    torch.cuda.synchronize()
+    assert np.array_equal(c.cpu().numpy(), direct[0][1])
+    plan.destroy()

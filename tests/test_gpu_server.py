@@ -173,3 +173,30 @@ def test_invalid_requests_fail_without_stopping_the_server():
     _check_equal(outs, _alone(shapes, fs))
     assert srv.stats()["failed"] == 2
     srv.destroy()
+
+
+def test_bursts_on_concurrent_streams_keep_every_result_exact():
+    """Many requests at once: batches on three streams overlap, and each stream's launch records
+    are rewritten before every batch while the other streams' kernels run."""
+    import torch
+    shapes = [(2 ** 14, 6), (65521, 12), (2 ** 16, 8), (3 ** 10, 20), (2 ** 17, 40),
+              (100003, 9), (2 ** 15 + 3, 30), (2 ** 18, 64), (3 ** 9, 16), (2 ** 13, 4),
+              (40009, 25), (2 ** 16 + 1, 33)]
+    fs = _inputs(shapes, 2500)
+    ref = _alone(shapes, fs)
+    srv = sft.Server(mem_budget=2 << 30, max_batch=8, max_inflight=3,
+                     variant=sft.sft_variant_init(**VARIANT))
+    order = [i % len(shapes) for i in range(240)]
+    for burst in range(2):
+        outs = _outputs([shapes[i] for i in order])
+        ids = _submit(srv, [shapes[i] for i in order], [fs[i] for i in order], outs)
+        for rid in ids:
+            assert srv.wait(rid, 60000) == sft.SFT_OK
+        for (w, c, n), i in zip(outs, order):
+            rw, rc, rn = ref[i]
+            assert int(n.item()) == rn
+            assert np.array_equal(w.cpu().numpy(), rw) and np.array_equal(c.cpu().numpy(), rc)
+        assert max(srv.query(r)["batch_size"] for r in ids) >= 4
+        for rid in ids:
+            srv.release(rid)
+    srv.destroy()
