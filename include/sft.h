@@ -56,6 +56,16 @@ typedef enum { SFT_IN_C64 = 0, SFT_IN_C128 = 1 } sft_input_type;
  *             c1 = beta sqrt(ln N)/N, L = ceil(N/(alpha sqrt(ln N))), ceil(alpha sqrt(ln N)/2) shifts.
  *  K, c_p     number of prime moduli p_j of the inner SFT and their size, p_j >= c_p * s.
  *  seed       selects the primes (the randomized inner SFT reads a random subset of moduli).
+ *  deterministic
+ *             0: the randomized inner SFT (K primes drawn by `seed` from the 4K smallest primes
+ *             >= max(ceil(c_p s), 5)).  1: the deterministic inner SFT (the paper's Algorithm 3
+ *             of the cited work, Lemma SFT_Ident_Coef_Est_in_Noise): the K smallest primes
+ *             >= max(ceil(c_p s), 5) with K = 2 (s - 1) L + 1, L = floor(log_{p_1}(N - 1)).  Two
+ *             distinct frequencies of B differ by less than N, so they share a residue modulo at
+ *             most L of the primes; every frequency of an s-sparse spectrum then sits alone in its
+ *             bin for a strict majority of the primes, and an exactly s-sparse input is recovered
+ *             exactly whatever the input (O(s^2 log N) samples).  The given K and seed are
+ *             ignored; SFT_EINVAL if K would exceed SFT_MAX_K.
  *  precision  SFT_FP32: window sums and DFTs in FP32 with FP32 accumulation, phases reduced exactly
  *             as integers; the s winners are then re-estimated from the samples with exact
  *             twiddles and compensated accumulation, medians and division in FP64.
@@ -71,6 +81,8 @@ typedef struct {
   double alpha;
   double beta;
   uint64_t seed;
+  int32_t deterministic;
+  int32_t reserved;
 } sft_variant;
 
 /*
@@ -85,7 +97,7 @@ sft_status sft_variant_theorem(sft_variant* v, int64_t N, double r);
 typedef struct sft_plan_s* sft_plan_t;
 
 /* Plan description returned by sft_plan_info (host memory, filled by the library). */
-#define SFT_MAX_K 15
+#define SFT_MAX_K 512
 #define SFT_MAX_SMALL 12
 #define SFT_MAX_SHIFTS 32
 typedef struct {
@@ -150,6 +162,13 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
  */
 sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                              int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);
+
+/* Host only: the moduli of the deterministic inner SFT (sft_variant.deterministic = 1) for N, s,
+ * c_p: the K smallest primes >= max(ceil(c_p s), 5), K = 2 (s - 1) floor(log_{p_1}(N - 1)) + 1,
+ * written to primes_out (room for SFT_MAX_K) with *K_out = K, and the small moduli as for
+ * sft_choose_moduli.  SFT_EINVAL on bad arguments or when K would exceed SFT_MAX_K. */
+sft_status sft_choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t* primes_out,
+                                           int32_t* K_out, int32_t* small_out, int32_t* n_small_out);
 
 /*
  * Batches: the transforms of n signals, each with its own plan, with one kernel launch per stage
@@ -391,7 +410,7 @@ sft_status sft_server_destroy(sft_server_t server);
  * 2 <= n <= 8191 (prime or not), in FP32, on `stream`.
  *
  * The kernel's tables (chirp, filter spectrum, FFT twiddles) and its launch record live in one
- * fixed 324 KiB array in
+ * fixed 340 KiB array in
  * device memory that the library declares statically: every GPU that loads the library holds it
  * until the process exits, and nothing is allocated at any call.  The first call on a device looks
  * up that array's address and builds the tables for n on `stream`; a later call with another n

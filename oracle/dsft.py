@@ -86,6 +86,23 @@ def choose_primes(s: int, K: int, c_p: float, seed: int) -> list[int]:
     return sorted(pool[:K])
 
 
+def deterministic_primes(N: int, s: int, c_p: float) -> list[int]:
+    """The deterministic inner SFT's moduli (Algorithm 3 of the cited work, first paragraph of
+    Lemma SFT_Ident_Coef_Est_in_Noise): the K smallest primes >= max(ceil(c_p * s), 5) with
+    K = 2 (s - 1) L + 1, where L is the largest integer with p_1^L <= N - 1.  A product of L + 1 of
+    these primes exceeds N - 1, so two distinct frequencies of B (which differ by less than N) share
+    a residue modulo at most L of them; with s frequencies each one is alone in its bin for at
+    least K - (s - 1) L > K / 2 of the primes."""
+    lo = max(int(math.ceil(c_p * s)), 5)
+    p1 = primes_from(lo, 1)[0]
+    L, pw = 0, p1
+    while pw <= N - 1:
+        L += 1
+        pw *= p1
+    K = 2 * (s - 1) * L + 1
+    return primes_from(lo, K)
+
+
 def choose_small_moduli(N: int, primes: list[int]) -> list[int]:
     """Smallest primes t (ascending), none equal to a p_j, until p_1 * prod(t) >= N, so that the
     CRT residue system of every p_j has a modulus M_j = p_j * prod(t) >= N (unique w in B)."""
@@ -126,7 +143,7 @@ def ceil_half(N: int) -> int:
 
 def make_plan(N: int, s: int, kappa: int = 6, alpha: float = 1.5, beta: float = 1.5,
               K: int = 5, c_p: float = 3.0, seed: int = 0, primes=None, small=None,
-              n_shifts: int | None = None) -> Plan:
+              n_shifts: int | None = None, deterministic: bool = False) -> Plan:
     """c1 = beta sqrt(ln N) / N, c2 = alpha sqrt(ln N) / 2, L = ceil(N / (alpha sqrt(ln N))),
     q_j = -ceil(N/2) + 1 + (2j - 1) L for j = 1..ceil(c2)  (Algorithm 1)."""
     if N < 2 or not (1 <= s <= N):
@@ -141,7 +158,7 @@ def make_plan(N: int, s: int, kappa: int = 6, alpha: float = 1.5, beta: float = 
         raise ValueError("the bands [q-L, q+L) do not cover B")
     shifts = [-ceil_half(N) + 1 + (2 * j - 1) * L for j in range(1, nq + 1)]
     if primes is None:
-        primes = choose_primes(s, K, c_p, seed)
+        primes = deterministic_primes(N, s, c_p) if deterministic else choose_primes(s, K, c_p, seed)
     primes = sorted(int(p) for p in primes)
     if small is None:
         small = choose_small_moduli(N, primes)

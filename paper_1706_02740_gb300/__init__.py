@@ -17,7 +17,7 @@ SFT_OK, SFT_EINVAL, SFT_ENOMEM, SFT_ECUDA, SFT_ETIMEOUT, SFT_EBUSY = range(6)
 SFT_DMSFT4, SFT_DMSFT6 = 4, 6
 SFT_FP32, SFT_FP64 = 0, 1
 SFT_IN_C64, SFT_IN_C128 = 0, 1
-SFT_MAX_K, SFT_MAX_SMALL, SFT_MAX_SHIFTS = 15, 12, 32
+SFT_MAX_K, SFT_MAX_SMALL, SFT_MAX_SHIFTS = 512, 12, 32
 BUF_SAMPLES, BUF_BINS, BUF_CAND, BUF_RESID, BUF_COUNTERS, BUF_VOTED = range(6)
 
 _STATUS = {0: "SFT_OK", 1: "SFT_EINVAL", 2: "SFT_ENOMEM", 3: "SFT_ECUDA", 4: "SFT_ETIMEOUT",
@@ -33,7 +33,8 @@ class SftError(RuntimeError):
 class sft_variant(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("input", ctypes.c_int32), ("K", ctypes.c_int32), ("c_p", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("deterministic", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sft_plan_desc(ctypes.Structure):
@@ -145,6 +146,11 @@ EXPORTS = {
     "sft_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sft_server_stats)]),
     "sft_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sft_batch_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "sft_choose_moduli_deterministic": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                                       ctypes.POINTER(ctypes.c_int64),
+                                                       ctypes.POINTER(ctypes.c_int32),
+                                                       ctypes.POINTER(ctypes.c_int32),
+                                                       ctypes.POINTER(ctypes.c_int32)]),
     "sft_choose_moduli": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_double, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_int64),
@@ -257,6 +263,17 @@ def sft_choose_moduli(N: int, s: int, K: int = 5, c_p: float = 3.0, seed: int = 
     _check(load().sft_choose_moduli(int(N), int(s), int(K), float(c_p), int(seed) & (2**64 - 1),
                                     pr, sm, ctypes.byref(ns)))
     return list(pr), list(sm[: ns.value])
+
+
+def sft_choose_moduli_deterministic(N: int, s: int, c_p: float = 3.0):
+    """Host-only: the (primes, small moduli) of the deterministic inner SFT."""
+    pr = (ctypes.c_int64 * SFT_MAX_K)()
+    k = ctypes.c_int32()
+    sm = (ctypes.c_int32 * SFT_MAX_SMALL)()
+    ns = ctypes.c_int32()
+    _check(load().sft_choose_moduli_deterministic(int(N), int(s), float(c_p), pr, ctypes.byref(k),
+                                                  sm, ctypes.byref(ns)))
+    return list(pr[: k.value]), list(sm[: ns.value])
 
 
 def sft_plan_info(plan: Plan) -> dict:

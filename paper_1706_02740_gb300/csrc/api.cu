@@ -86,6 +86,7 @@ LaunchSet single_launch_set(const DevPlan& d) {
     ls.blk[k] = nullptr;
   }
   ls.pmax = d.pmax;
+  ls.kmax = d.K;
   return ls;
 }
 
@@ -186,6 +187,8 @@ sft_status sft_variant_init(sft_variant* v) {
   v->alpha = 1.5;
   v->beta = 1.5;
   v->seed = 0;
+  v->deterministic = 0;
+  v->reserved = 0;
   return SFT_OK;
 }
 
@@ -334,6 +337,11 @@ int64_t sft_plan_launches(sft_plan_t plan) { return plan ? plan->P.launches : 0;
 sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                              int64_t* primes_out, int32_t* small_out, int32_t* n_small_out) {
   return sft::choose_moduli(N, s, K, c_p, seed, primes_out, small_out, n_small_out);
+}
+
+sft_status sft_choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t* primes_out,
+                                           int32_t* K_out, int32_t* small_out, int32_t* n_small_out) {
+  return sft::choose_moduli_deterministic(N, s, c_p, primes_out, K_out, small_out, n_small_out);
 }
 
 const char* sft_last_error(void) { return sft::g_last_error.c_str(); }

@@ -238,7 +238,11 @@ sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n
   B.d0 = a;
   B.ls.tune = default_tuning();
   B.ls.pmax = 0;
-  for (int i = 0; i < n; ++i) B.ls.pmax = std::max(B.ls.pmax, ps[i]->d.pmax);
+  B.ls.kmax = 0;
+  for (int i = 0; i < n; ++i) {
+    B.ls.pmax = std::max(B.ls.pmax, ps[i]->d.pmax);
+    B.ls.kmax = std::max(B.ls.kmax, ps[i]->d.K);
+  }
   std::vector<int32_t> prefix;
   if (!make_prefixes(ps, B.ls.tune, prefix, B.ls.blocks)) {
     delete h;

@@ -399,14 +399,14 @@ namespace {
 constexpr int kNoAllocMaxN = 8191;           // longest transform: 2n - 1 <= 16384
 constexpr int kNoAllocMaxM = 16384;
 constexpr int kNoAllocChirp = 8192;
-constexpr size_t kNoAllocHead = 4096;        // the launch's plan record
+constexpr size_t kNoAllocHead = (sizeof(DevPlan) + 4095) / 4096 * 4096;   // the launch's plan record
 static_assert(sizeof(DevPlan) <= kNoAllocHead, "plan record must fit the head of the array");
 constexpr size_t kNoAllocBytes =
     kNoAllocHead + sizeof(float2) * ((size_t)kNoAllocChirp + 2 * (size_t)kNoAllocMaxM);
 constexpr int kMaxDevices = 64;
 
-// plan record [4 KiB] | chirp [8192] | filter spectrum [16384] | twiddles [16384] (complex64):
-// 324 KiB in all
+// plan record [20 KiB] | chirp [8192] | filter spectrum [16384] | twiddles [16384] (complex64):
+// 340 KiB in all
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
@@ -569,6 +569,7 @@ extern "C" sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_d
   LaunchSet ls;
   memset(&ls, 0, sizeof(ls));
   ls.tune = default_tuning();
+  ls.kmax = 1;
   int lg = 0;
   while ((1 << lg) < M) ++lg;
   ls.blocks[kStBluestein0 + lg - 6] = bluestein_blocks(d, M, ls.tune.dft_per_cta[lg - 6]);

@@ -40,8 +40,13 @@ __device__ __forceinline__ int mod_p(int64_t w, int p) {
 __device__ __forceinline__ void decode_bin(const DevPlan& d, int64_t gid, int& qi, int& j, int& b) {
   qi = (int)(gid / d.Ptot);
   const int bin = (int)(gid - (int64_t)qi * d.Ptot);
-  j = 0;
-  while (j + 1 < d.K && bin >= d.poff[j + 1]) ++j;
+  int lo = 0, hi = d.K;                  // the prime whose bin range holds `bin`
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (d.poff[mid] <= bin) lo = mid;
+    else hi = mid;
+  }
+  j = lo;
   b = bin - d.poff[j];
 }
 
@@ -139,7 +144,8 @@ __global__ void __launch_bounds__(kBinMaxThreads) identify_kernel(BatchView bv) 
   d.cand[gid] = (w > -((N + 1) / 2)) ? w : kNoFreq;
 }
 
-template <typename R>
+// KCAP: capacity of the per-thread arrays (kFewK in registers, or kMaxK for many primes).
+template <typename R, int KCAP>
 __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   int lb, nb;
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   decode_bin(d, gid, qi, j, b);
   const int64_t* cq = d.cand + (int64_t)qi * d.Ptot;
   int cnt = 0, jmin = d.K;
-  int bb[kMaxK];
+  int bb[KCAP];
   for (int jj = 0; jj < d.K; ++jj) {
     bb[jj] = mod_p(w, d.p[jj]);
     if (cq[d.poff[jj] + bb[jj]] == w) {
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   }
   if (cnt < d.K / 2 + 1 || jmin != j) return;
   const C* Zq = reinterpret_cast<const C*>(d.bins) + (int64_t)qi * d.m;
-  R re[kMaxK], im[kMaxK];
+  R re[KCAP], im[KCAP];
   for (int jj = 0; jj < d.K; ++jj) {
     const C y = Zq[d.nodeoff[jj] + bb[jj]];
     re[jj] = y.x;
@@ -171,8 +177,8 @@ __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   const double sg = (w & 1) ? -1.0 : 1.0;
   Voted rec;
   rec.w = w;
-  rec.zre = sg * median_of<kMaxK>(re, d.K);
-  rec.zim = sg * median_of<kMaxK>(im, d.K);
+  rec.zre = sg * median_of<KCAP>(re, d.K);
+  rec.zim = sg * median_of<KCAP>(im, d.K);
   rec.votes = cnt;
   rec.jmin = jmin;
   const int slot = atomicAdd(d.counters + qi, 1);
@@ -198,8 +204,15 @@ cudaError_t launch_vote(const DevPlan& d0, const BatchView& bv, const LaunchSet&
   if (grid == 0) return cudaSuccess;
   BatchView v = bv;
   v.blk = ls.blk[kStBins];
-  if (d0.prec == SFT_FP32) vote_kernel<float><<<grid, ls.tune.bin_threads, 0, st>>>(v);
-  else vote_kernel<double><<<grid, ls.tune.bin_threads, 0, st>>>(v);
+  const int t = ls.tune.bin_threads;
+  const bool few = ls.kmax <= kFewK;
+  if (d0.prec == SFT_FP32) {
+    if (few) vote_kernel<float, kFewK><<<grid, t, 0, st>>>(v);
+    else vote_kernel<float, kMaxK><<<grid, t, 0, st>>>(v);
+  } else {
+    if (few) vote_kernel<double, kFewK><<<grid, t, 0, st>>>(v);
+    else vote_kernel<double, kMaxK><<<grid, t, 0, st>>>(v);
+  }
   return cudaGetLastError();
 }
 

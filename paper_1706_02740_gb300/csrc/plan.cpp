@@ -76,6 +76,23 @@ std::vector<int32_t> choose_primes(int32_t s, int K, double c_p, uint64_t seed) 
 }
 
 // Smallest primes t, none equal to a p_j, until p_1 * prod(t) >= N.
+// The deterministic inner SFT's moduli: the K smallest primes >= max(ceil(c_p s), 5) with
+// K = 2 (s - 1) L + 1, L = floor(log_{p_1}(N - 1)) (the largest L with p_1^L <= N - 1).
+std::vector<int32_t> deterministic_primes(int64_t N, int32_t s, double c_p, int* K_out) {
+  int64_t n = std::max<int64_t>((int64_t)ceil(c_p * (double)s), 5);
+  while (!is_prime(n)) ++n;
+  const int64_t p1 = n;
+  int64_t L = 0;
+  for (__int128 pw = p1; pw <= (__int128)(N - 1); pw *= p1) ++L;
+  const int64_t K = 2 * (int64_t)(s - 1) * L + 1;
+  *K_out = K > (int64_t)kMaxK ? -1 : (int)K;
+  std::vector<int32_t> out;
+  if (*K_out < 0) return out;
+  for (int64_t m = p1; (int)out.size() < K; ++m)
+    if (is_prime(m)) out.push_back((int32_t)m);
+  return out;
+}
+
 std::vector<int32_t> choose_small(int64_t N, const std::vector<int32_t>& primes) {
   std::vector<int32_t> T;
   int64_t prod = primes[0];
@@ -164,7 +181,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   // ---- moduli
   std::vector<int32_t> primes;
   if (primes_in) {
-    if (n_primes < 1 || n_primes > kMaxK) { set_error("n_primes must be 1..15"); return SFT_EINVAL; }
+    if (n_primes < 1 || n_primes > kMaxK) { set_error("n_primes must be 1.." + std::to_string(kMaxK)); return SFT_EINVAL; }
     for (int i = 0; i < n_primes; ++i) {
       if (primes_in[i] < 2 || primes_in[i] > (1 << 20) || !is_prime(primes_in[i])) {
         set_error("primes must be primes in [2, 2^20]"); return SFT_EINVAL;
@@ -175,8 +192,16 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
     if (std::adjacent_find(primes.begin(), primes.end()) != primes.end()) {
       set_error("primes must be distinct"); return SFT_EINVAL;
     }
+  } else if (v->deterministic) {
+    if (v->c_p * (double)s > 1.0e6) { set_error("c_p * s too large"); return SFT_EINVAL; }
+    int Kd = 0;
+    primes = deterministic_primes(N, s, v->c_p, &Kd);
+    if (Kd < 0) {
+      set_error("deterministic mode needs more than " + std::to_string(kMaxK) + " primes here");
+      return SFT_EINVAL;
+    }
   } else {
-    if (v->K < 1 || v->K > kMaxK) { set_error("K must be 1..15"); return SFT_EINVAL; }
+    if (v->K < 1 || v->K > kMaxK) { set_error("K must be 1.." + std::to_string(kMaxK)); return SFT_EINVAL; }
     if (v->c_p * (double)s > 1.0e6) { set_error("c_p * s too large"); return SFT_EINVAL; }
     primes = choose_primes(s, v->K, v->c_p, v->seed);
   }
@@ -409,6 +434,25 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   P->alpha = v->alpha; P->beta = v->beta; P->seed = v->seed;
   P->shifts = shifts; P->primes = primes; P->small = small;
   cudaGetDevice(&P->device);
+  return SFT_OK;
+}
+
+sft_status choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t* primes_out,
+                                       int32_t* K_out, int32_t* small_out, int32_t* n_small_out) {
+  if (!primes_out || !K_out || !small_out || !n_small_out) { set_error("NULL output"); return SFT_EINVAL; }
+  if (N < 2 || s < 1 || s > N || !(c_p > 0.0) || c_p * (double)s > 1.0e6) {
+    set_error("need N >= 2, 1 <= s <= N, c_p > 0");
+    return SFT_EINVAL;
+  }
+  int K = 0;
+  std::vector<int32_t> pr = deterministic_primes(N, s, c_p, &K);
+  if (K < 0) { set_error("deterministic mode needs more than " + std::to_string(kMaxK) + " primes here"); return SFT_EINVAL; }
+  std::vector<int32_t> sm = choose_small(N, pr);
+  if ((int)sm.size() > kMaxT) { set_error("too many small moduli"); return SFT_EINVAL; }
+  for (int j = 0; j < K; ++j) primes_out[j] = pr[j];
+  *K_out = K;
+  for (size_t l = 0; l < sm.size(); ++l) small_out[l] = sm[l];
+  *n_small_out = (int32_t)sm.size();
   return SFT_OK;
 }
 

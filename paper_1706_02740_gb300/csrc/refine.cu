@@ -163,6 +163,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // Refined coefficient of winner r, written back into winners[r].
+// KCAP: capacity of the per-thread arrays (kFewK in registers, or kMaxK for many primes).
+template <int KCAP>
 __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView bv) {
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView
   const int r = lb * kRefineThreads + threadIdx.x;
   if (r >= n) return;
   Pooled pw = d.winners[r];
-  double re[kMaxK], im[kMaxK];
+  double re[KCAP], im[KCAP];
   const float4* part = reinterpret_cast<const float4*>(d.ybuf);
   for (int jj = 0; jj < d.K; ++jj) {
     const int p = d.p[jj];
@@ -191,8 +193,8 @@ __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView
     re[jj] = ((double)hr + (double)lr) * inv_p;
     im[jj] = ((double)hi + (double)li) * inv_p;
   }
-  const double mre = median_of<kMaxK>(re, d.K);
-  const double mim = median_of<kMaxK>(im, d.K);
+  const double mre = median_of<KCAP>(re, d.K);
+  const double mim = median_of<KCAP>(im, d.K);
   const double sg = (pw.w & 1) ? -1.0 : 1.0;
   const double x = d.c1 * (double)(pw.w - d.q[pw.qi]);
   const double inv_ghat = kSqrt2Pi * exp(0.5 * x * x);
@@ -213,7 +215,8 @@ cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t
   if (e != cudaSuccess) return e;
   reestimate_kernel<<<ls.blocks[kStReest], kReChunk, smem, st>>>(v);
   v.blk = ls.blk[kStRefine];
-  refine_values_kernel<<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
+  if (ls.kmax <= kFewK) refine_values_kernel<kFewK><<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
+  else refine_values_kernel<kMaxK><<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 

@@ -35,8 +35,16 @@ struct NodeGeom {
 // so the nearest grid index (ties up) is j' = I + round(G / P) and d0 = kN - j'P = G - round(G/P) P,
 // all in 32-bit integer arithmetic (no 64-bit division).
 __device__ __forceinline__ void decode_node(const DevPlan& d, int64_t node, int& j, int& k1, NodeGeom& g) {
-  j = 0;
-  while (j + 1 < d.K && node >= d.nodeoff[j + 1]) ++j;
+  {
+    // the prime whose node range holds `node` (binary search: K may be large)
+    int lo = 0, hi = d.K;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (d.nodeoff[mid] <= node) lo = mid;
+      else hi = mid;
+    }
+    j = lo;
+  }
   const int p = d.p[j];
   const int local = (int)(node - d.nodeoff[j]);
   const int sub = local / p;

@@ -11,7 +11,8 @@
 
 namespace sft {
 
-constexpr int kMaxK = SFT_MAX_K;          // prime moduli
+constexpr int kMaxK = SFT_MAX_K;          // prime moduli (the deterministic inner SFT needs many)
+constexpr int kFewK = 16;                 // per-thread median arrays in registers up to this K
 constexpr int kMaxT = SFT_MAX_SMALL;      // small moduli
 constexpr int kMaxQ = SFT_MAX_SHIFTS;     // shifts
 constexpr int kMaxKappa = 48;             // window half-width
@@ -171,6 +172,7 @@ struct LaunchSet {
   int32_t blocks[kStCount];
   const int32_t* blk[kStCount];
   int32_t pmax;               // largest prime over the signals (shared-memory sizing)
+  int32_t kmax;               // most prime moduli of any signal (per-thread median arrays)
   sft_tuning tune;            // launch geometry (block shapes; never changes results)
 };
 
@@ -288,6 +290,8 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
 void free_plan(Plan* P);
 sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                          int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);
+sft_status choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t* primes_out,
+                                       int32_t* K_out, int32_t* small_out, int32_t* n_small_out);
 
 // Thread-local error text.
 void set_error(const std::string& msg);

@@ -35,9 +35,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_sizes_match_header_layout():
-    # sft_variant: 4 x int32, 3 x double, uint64
-    assert ctypes.sizeof(sft.sft_variant) == 48
-    assert ctypes.sizeof(sft.sft_plan_desc) == 8 + 6 * 4 + 15 * 8 + 12 * 4 + 32 * 8 + 8 + 8 + 8 + 16
+    # sft_variant: 4 x int32, 3 x double, uint64, 2 x int32
+    assert ctypes.sizeof(sft.sft_variant) == 56
+    assert sft.SFT_MAX_K == 512
+    assert ctypes.sizeof(sft.sft_plan_desc) == 8 + 6 * 4 + 512 * 8 + 12 * 4 + 32 * 8 + 8 + 8 + 8 + 16
 
 
 def test_tuning_layout_and_defaults(lib):
@@ -51,7 +52,7 @@ def test_tuning_layout_and_defaults(lib):
 
 
 def test_server_structs_and_config_defaults(lib):
-    assert ctypes.sizeof(sft.sft_server_config) == 8 + 4 + 4 + 48 + 13 * 4 + 4   # + tail padding
+    assert ctypes.sizeof(sft.sft_server_config) == 8 + 4 + 4 + 56 + 13 * 4 + 4   # + tail padding
     assert ctypes.sizeof(sft.sft_request_info) == 4 * 4 + 2 * 8
     assert ctypes.sizeof(sft.sft_server_stats) == 8 * 8 + 3 * 8 + 2 * 4
     cfg = sft.sft_server_config()
@@ -93,7 +94,7 @@ def test_theorem_variant_rejects_out_of_range(lib, N, r):
 def test_variant_defaults(lib):
     v = sft.sft_variant_init()
     assert (v.kappa, v.precision, v.input, v.K) == (6, 0, 0, 5)
-    assert (v.c_p, v.alpha, v.beta, v.seed) == (3.0, 1.5, 1.5, 0)
+    assert (v.c_p, v.alpha, v.beta, v.seed, v.deterministic) == (3.0, 1.5, 1.5, 0, 0)
 
 
 @pytest.mark.parametrize("N,s,K,c_p,seed", [(2 ** 16, 8, 5, 4.0, 0), (2 ** 22, 64, 5, 3.0, 7),

@@ -241,3 +241,36 @@ def test_plan_graph_replay_equals_direct_execution():
     torch.cuda.synchronize()
     assert np.array_equal(c.cpu().numpy(), direct[0][1])
     plan.destroy()
+
+
+def test_mixed_batch_sample_matches_oracle():
+    """The mixed-size batched workload (N log-uniform over [2^18, 2^24], a quarter at other
+    lengths including primes; s uniform over [16, 512]; unit magnitudes; SNR 20 dB; complex64):
+    a seeded 64-signal sample run as one batch on the FP32 path, every member against the oracle on
+    the same input.  As at the other full sizes, frequencies at the vote threshold may differ
+    between FP32 and FP64 decisions; they must be few and weak."""
+    import torch
+    from synth.device_signals import make_device_signal
+    from synth.signals import draw_batch_shapes
+    from tests.test_gpu_fullsize import _compare
+    shapes = draw_batch_shapes(64, 4064)
+    plans, fs = [], []
+    for i, (N, s) in enumerate(shapes):
+        f, _, _ = make_device_signal(N, s, 4064 + i, "unit", 20.0, "cuda")
+        fs.append(f)
+        plans.append(sft.sft_plan(N, s, sft.sft_variant_init(kappa=6, K=5, c_p=3.0, seed=i)))
+    torch.backends.cuda.cufft_plan_cache[0].clear()
+    batch = sft.Batch(plans)
+    outs = sft.execute_batch_torch(batch, fs)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for p, f, (w, c, n), (N, s) in zip(plans, fs, outs, shapes):
+        info = p.info()
+        g = {"freqs": w.cpu().numpy(), "coefs": c.cpu().numpy(), "count": int(n.item())}
+        res = O.dsft(f.cpu().numpy().astype(np.complex128), U.oracle_plan(info, N, s))
+        _, _, err = _compare(g, res, 1e-5, floor=0.3, max_diff_frac=0.05)
+        worst = max(worst, err)
+    assert worst <= 1e-5
+    batch.destroy()
+    for p in plans:
+        p.destroy()

@@ -217,3 +217,38 @@ def test_repeated_execution_is_deterministic():
         else:
             assert np.array_equal(cur[0], first[0]) and np.array_equal(cur[1], first[1])
     plan.destroy()
+
+
+@pytest.mark.parametrize("N,s,c_p", [(3 ** 7, 3, 2.0), (2 ** 12, 4, 2.0), (2 ** 14, 6, 2.0)])
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_deterministic_inner_sft_matches_oracle_and_recovers_exactly(N, s, c_p, prec):
+    """The deterministic inner SFT (K = 2 (s - 1) floor(log_{p_1}(N - 1)) + 1 consecutive primes:
+    13, 19 and 31 here, beyond the register path's 16) on random and adversarial spectra (all
+    frequencies congruent modulo the first primes): output equal to the oracle's and to the
+    generating spectrum."""
+    import torch
+    from synth.signals import samples_from_spectrum
+    v = sft.sft_variant_init(precision=prec, c_p=c_p, deterministic=1, input=1)
+    plan = sft.sft_plan(N, s, v)
+    info = plan.info()
+    assert info["primes"] == O.deterministic_primes(N, s, c_p)
+    oplan = O.make_plan(N, s, kappa=info["kappa"], c_p=c_p, deterministic=True)
+    assert oplan.primes == info["primes"] and oplan.small == info["small"]
+    B = np.arange(-((N + 1) // 2) + 1, N // 2 + 1, dtype=np.int64)
+    rng = np.random.default_rng(N + s)
+    step = info["primes"][0] * info["primes"][1]
+    step = step if step * (s - 1) < N // 2 else info["primes"][0]
+    spectra = [np.array([(i - s // 2) * step for i in range(s)], dtype=np.int64),
+               rng.choice(B, size=s, replace=False)]
+    for w in spectra:
+        coef = np.exp(2j * np.pi * rng.random(s))
+        f = samples_from_spectrum(N, w, coef)
+        gw, gc, gn = sft.execute_torch(plan, torch.from_numpy(f).cuda())
+        torch.cuda.synchronize()
+        n = int(gn.item())
+        res = O.dsft(f, oplan)
+        assert sorted(res.freqs.tolist()) == sorted(w.tolist())
+        assert n == s
+        U.assert_same_output(gw.cpu().numpy()[:n], gc.cpu().numpy()[:n], res.freqs, res.coefs,
+                             1e-5 if prec == U.FP32 else 1e-11)
+    plan.destroy()
