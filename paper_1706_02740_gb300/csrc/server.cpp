@@ -371,6 +371,13 @@ void scheduler(Server* Sp) {
     }
     std::vector<Request*> rq;
     for (int64_t id : take) rq.push_back(&S.reqs[id]);   // records stay put until released
+    // Claim the slot before its work exists: its completion callback may fire before this thread
+    // takes the lock again, and must find the slot busy with `done` clear so the completion is
+    // not overwritten.
+    free_slot->busy = true;
+    free_slot->done = false;
+    free_slot->reqs.clear();
+    free_slot->plans.clear();
     lk.unlock();
 
     std::vector<int64_t> admitted, deferred;
@@ -420,10 +427,8 @@ void scheduler(Server* Sp) {
         arq[i]->reused = was_reused[i];
       }
       if (ce == cudaSuccess) {
-        free_slot->busy = true;
-        free_slot->done = false;
+        // busy since the claim; `done` may already be set by the completion callback
         free_slot->reqs = admitted;
-        free_slot->plans.clear();
         for (Request* r : arq) {
           r->state = 1;
           r->t_launch = now;
@@ -434,6 +439,7 @@ void scheduler(Server* Sp) {
         S.stats.max_batch_seen = std::max(S.stats.max_batch_seen, (int32_t)arq.size());
       } else {
         cudaGetLastError();
+        free_slot->busy = free_slot->done = false;
         for (Request* r : arq) {
           r->state = 3;
           r->status = SFT_ECUDA;
@@ -442,6 +448,8 @@ void scheduler(Server* Sp) {
           ++S.stats.failed;
         }
       }
+    } else {
+      free_slot->busy = free_slot->done = false;      // nothing was launched: release the claim
     }
     if (!failed.empty() || ce != cudaSuccess) S.done_cv.notify_all();
     if (arq.empty() && !deferred.empty()) {

@@ -200,3 +200,23 @@ def test_bursts_on_concurrent_streams_keep_every_result_exact():
         for rid in ids:
             srv.release(rid)
     srv.destroy()
+
+
+def test_batches_that_finish_before_the_scheduler_looks_again_are_not_lost():
+    """Tiny requests one at a time: each batch can complete (its callback firing) before the
+    scheduler retakes its lock after launching; every completion must still be seen."""
+    shapes = [(2 ** 10, 2), (3 ** 6, 2), (1021, 3)]
+    fs = _inputs(shapes, 2600)
+    ref = _alone(shapes, fs)
+    srv = sft.Server(mem_budget=256 << 20, max_batch=4, max_inflight=3,
+                     variant=sft.sft_variant_init(**VARIANT))
+    for rep in range(300):
+        i = rep % len(shapes)
+        outs = _outputs(shapes[i:i + 1])
+        rid = _submit(srv, shapes[i:i + 1], fs[i:i + 1], outs)[0]
+        assert srv.wait(rid, 20000) == sft.SFT_OK
+        if rep % 50 == 0:
+            _check_equal(outs, ref[i:i + 1])
+        srv.release(rid)
+    assert srv.stats()["completed"] == 300
+    srv.destroy()
