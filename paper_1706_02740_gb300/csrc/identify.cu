@@ -102,8 +102,10 @@ __device__ int residue_any(int t, C z0, const C* Zl, int64_t p, const C* twl, in
   return bestr;
 }
 
+// The FP32 build is held to 64 registers (two 512-thread CTAs, 32 warps per SM: the kernel waits on
+// its sub-bin loads, so more warps in flight help); the FP64 build would spill there.
 template <typename R>
-__global__ void __launch_bounds__(kBinMaxThreads) identify_kernel(BatchView bv) {
+__global__ void __launch_bounds__(kBinMaxThreads, sizeof(R) == 4 ? 2 : 1) identify_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
