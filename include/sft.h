@@ -114,7 +114,8 @@ typedef struct {
   int64_t L;                          /* band half-width ceil(N/(alpha sqrt(ln N))) */
   double c1;                          /* Gaussian width beta sqrt(ln N)/N */
   int64_t nodes;                      /* distinct nodes m = n_sub * sum_j p_j */
-  int32_t fft_size;                   /* power-of-two length of the chirp convolutions */
+  int32_t fft_size;                   /* chirp-convolution length: the smallest 2^k >= 64 or
+                                         3 2^k >= 96 that is >= 2 p_K - 1 */
   int32_t precision;
   int32_t input;
   int32_t reserved;

@@ -72,8 +72,10 @@ int signal_blocks(const DevPlan& d, int kind, const sft_tuning& tu) {
     case kStReest: return d.prec == SFT_FP32 ? d.nq * d.K * d.nchunk : 0;
     case kStRefine: return d.prec == SFT_FP32 ? (d.s + kRefineThreads - 1) / kRefineThreads : 0;
     default:
-      if (kind >= kStBluestein0 && kind < kStCount)
-        return bluestein_blocks(d, 64 << (kind - kStBluestein0), tu.dft_per_cta[kind - kStBluestein0]);
+      if (kind >= kStBluestein0 && kind < kStCount) {
+        const int M = fft_stage_length(kind);
+        return bluestein_blocks(d, M, tu.dft_per_cta[fft_tune_class(M)]);
+      }
       return 0;
   }
 }

@@ -382,7 +382,9 @@ sft_status sft_batch_autotune(sft_batch_t batch, const void* const* f_devs,
   }
   // chirp convolution: transforms per CTA of every length class present, then the FP32 8192 build
   for (int c = 0; c < 9 && s == SFT_OK; ++c) {
-    if (B.ls.blocks[kStBluestein0 + c] == 0) continue;
+    // the class of 2^(c+6) and that of 3 2^(c+4), which has as many threads per transform
+    if (B.ls.blocks[kStBluestein0 + c] == 0 && (c == 0 || B.ls.blocks[kStBluestein3 + c - 1] == 0))
+      continue;
     const int M = 64 << c, hi = M >= 4096 ? 1 : 4096 / M;
     if (hi == 1) continue;
     cands.clear();

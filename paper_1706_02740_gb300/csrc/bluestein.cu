@@ -3,14 +3,14 @@
 //
 // Each p_j is prime, so the length-p DFT is taken as a chirp convolution (Bluestein): with
 // w_n = e^{-pi i n^2 / p},  E_c = (1/p) w_c sum_k (h_k w_k) conj(w_{c-k}),  a linear convolution
-// done as a cyclic one of power-of-two length M >= 2p - 1:
+// done as a cyclic one of length M >= 2p - 1, M = 2^k or 3 2^k (whichever is smaller):
 //     E = w . conj( FFT( conj( FFT(h w, zero padded) . V ) ) ),
 // V = FFT(conj(w) wrapped) / (M p) precomputed per prime in FP64 on the host (the inverse FFT is the
 // forward one between two conjugations).  One transform lives in shared memory; the FFT is an
-// in-place Stockham schedule whose passes hold 16 complex values per thread in registers: a
-// radix-2 first pass, radix-16 passes, then one radix 2/4/8 pass where M needs it, with twiddles
-// read from exactly rounded per-pass tables.  Since p <= M/2, the first FFT's radix-2 pass only
-// duplicates its input and is skipped.
+// in-place Stockham schedule whose passes hold at most 16 complex values per thread in registers:
+// a radix-2 first pass, radix-16 passes, then the radix 2/4/8 (or 3/6/12, and 12 then 2) passes
+// that M needs, with twiddles read from exactly rounded per-pass tables.  Since p <= M/2, the
+// first FFT's radix-2 pass only duplicates its input and is skipped.
 // The shared-memory layout inserts one pad element after every 16 (index n -> n + n/16), so the
 // strided stores of the short-span passes hit distinct banks.
 #include <stdint.h>
@@ -33,6 +33,8 @@ template <int M> constexpr int padded_len() { return M + M / 16; }
 constexpr double kC8 = 0.92387953251128674;
 constexpr double kS8 = 0.38268343236508977;
 constexpr double kH = 0.70710678118654752;
+// sqrt(3)/2, the sine of the radix-3 butterfly.
+constexpr double kS3 = 0.86602540378443865;
 
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
@@ -86,6 +88,54 @@ template <typename C> struct DFT<8, C> {
     for (int k = 0; k < 4; ++k) {
       a[k] = cadd(e[k], o[k]);
       a[k + 4] = csub(e[k], o[k]);
+    }
+  }
+};
+// X0 = a0 + a1 + a2, X1,2 = a0 - (a1 + a2)/2 -/+ i (sqrt 3 / 2)(a1 - a2).
+template <typename C> struct DFT<3, C> {
+  __device__ static __forceinline__ void run(C* a) {
+    using R = decltype(a[0].x);
+    const C t = cadd(a[1], a[2]), d = csub(a[1], a[2]);
+    const C m = C{r_fma(t.x, (R)-0.5, a[0].x), r_fma(t.y, (R)-0.5, a[0].y)};
+    a[0] = cadd(a[0], t);
+    a[1] = C{r_fma(d.y, (R)kS3, m.x), r_fma(d.x, -(R)kS3, m.y)};
+    a[2] = C{r_fma(d.y, -(R)kS3, m.x), r_fma(d.x, (R)kS3, m.y)};
+  }
+};
+// Prime-factor (Good-Thomas) forms, no twiddles: for R = R1 R2 with gcd(R1, R2) = 1, input
+// n = (R2 n1 + R1 n2) mod R and output k = (k1 R2 (R2^-1 mod R1) + k2 R1 (R1^-1 mod R2)) mod R
+// turn the length-R DFT into length-R1 DFTs over n1 and length-R2 DFTs over n2.
+// 6 = 2 x 3: n = (3 n1 + 2 n2) mod 6, k = (3 k1 + 4 k2) mod 6.
+template <typename C> struct DFT<6, C> {
+  __device__ static __forceinline__ void run(C* a) {
+    C u[3] = {a[0], a[2], a[4]}, v[3] = {a[3], a[5], a[1]};
+    DFT<3, C>::run(u);
+    DFT<3, C>::run(v);
+    // k = (3 k1 + 4 k2) mod 6 for k1 = 0, 1 and k2 = 0, 1, 2
+    a[0] = cadd(u[0], v[0]); a[3] = csub(u[0], v[0]);
+    a[4] = cadd(u[1], v[1]); a[1] = csub(u[1], v[1]);
+    a[2] = cadd(u[2], v[2]); a[5] = csub(u[2], v[2]);
+  }
+};
+// 12 = 3 x 4: n = (4 n1 + 3 n2) mod 12, k = (4 k1 + 9 k2) mod 12.
+template <typename C> struct DFT<12, C> {
+  __device__ static __forceinline__ void run(C* a) {
+    C y[3][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 3; ++n1) {
+      C t[4];
+#pragma unroll
+      for (int n2 = 0; n2 < 4; ++n2) t[n2] = a[(4 * n1 + 3 * n2) % 12];
+      DFT<4, C>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) y[n1][k2] = t[k2];
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      C t[3] = {y[0][k2], y[1][k2], y[2][k2]};
+      DFT<3, C>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 3; ++k1) a[(4 * k1 + 9 * k2) % 12] = t[k1];
     }
   }
 };
@@ -146,6 +196,16 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C
   constexpr int base = fft_tw_offset(M, SPAN);
   if constexpr (RAD == 2) {
     v[1] = cmul(v[1], __ldg(W + base + k));
+  } else if constexpr (RAD == 3) {
+    v[1] = cmul(v[1], __ldg(W + base + k));
+    v[2] = cmul(v[2], __ldg(W + base + SPAN + k));
+  } else if constexpr (RAD == 6) {
+    const C w1 = __ldg(W + base + k), P = __ldg(W + base + 3 * SPAN + k);   // w, w^4
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], __ldg(W + base + SPAN + k));
+    v[3] = cmul(v[3], __ldg(W + base + 2 * SPAN + k));
+    v[4] = cmul(v[4], P);
+    v[5] = cmul(v[5], cmul(P, w1));
   } else {
     const C w1 = __ldg(W + base + k), w2 = __ldg(W + base + SPAN + k),
             w3 = __ldg(W + base + 2 * SPAN + k);
@@ -167,7 +227,8 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C
 // Item i in [0, M/RAD): takes element i + r M/RAD, applies the twiddles e^{-2 pi i r k / (SPAN RAD)}
 // (k = i mod SPAN), takes a radix-RAD DFT and puts element (i - k) RAD + k + r SPAN.  All reads of
 // the pass finish before any shared-memory write (barrier), so the pass is in place.  Each of the
-// TPT threads of the transform handles M / (RAD TPT) items.
+// TPT threads of the transform handles M / (RAD TPT) items, rounded up (a radix-16 pass of a
+// length 3 2^k has 3/4 of an item per thread: the rest of the threads only wait at the barrier).
 //
 // LOAD == kFromInput is the first pass after the radix-2 first pass of a transform whose input
 // x vanishes from p <= M/2 on: that radix-2 pass only duplicates (y[2i] = y[2i + 1] = x[i]), so it
@@ -178,13 +239,16 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C
 template <typename C, int M, int RAD, int SPAN, int TPT, int LOAD, int STORE>
 __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict__ W,
                                               const ChirpIO<C>& io) {
-  constexpr int ITEMS = M / RAD / TPT;
+  constexpr int NI = M / RAD;              // items of the pass
+  constexpr int ITEMS = (NI + TPT - 1) / TPT;
+  constexpr bool EVEN = NI % TPT == 0;
   constexpr int STRIDE = M / RAD;          // input stride of an item's elements
   C v[ITEMS * RAD];
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     const int i = lt + it * TPT;
-    const int k = i & (SPAN - 1);
+    const int k = i % SPAN;
+    if (!EVEN && i >= NI) continue;
     if (LOAD == kFromInput) {
       // element n = i + r STRIDE reads x[n / 2] = x[(i >> 1) + r STRIDE / 2] (STRIDE is even)
       const int m0 = i >> 1, pm0 = pad16(m0);
@@ -210,7 +274,8 @@ __device__ __forceinline__ void stockham_pass(C* s, int lt, const C* __restrict_
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     const int i = lt + it * TPT;
-    const int k = i & (SPAN - 1);
+    const int k = i % SPAN;
+    if (!EVEN && i >= NI) continue;
     const int j0 = (i - k) * RAD + k;
     if (STORE == kToOutput) {
 #pragma unroll
@@ -251,6 +316,7 @@ struct FFTPasses<C, M, M, TPT, LOAD, STORE> {
 template <typename C, int M, int TPT>
 __device__ __forceinline__ void radix2_first(C* s, int lt) {
   constexpr int ITEMS = M / 2 / TPT;
+  static_assert(ITEMS * TPT == M / 2, "whole items per thread");
   C v[2 * ITEMS];
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
@@ -271,16 +337,16 @@ __device__ __forceinline__ void radix2_first(C* s, int lt) {
   __syncthreads();
 }
 
-// A CTA holds blockDim.x / (M/16) transforms, at most max(M/16, 256) threads.  MINB is the
-// builds' CTAs-per-SM target: FP32 transforms are limited to 64 (M = 8192, MINB = 2) or
-// 128 (M <= 4096) registers.
-template <int M> constexpr int dft_max_threads() { return (M / 16) > 256 ? (M / 16) : 256; }
+// A CTA holds blockDim.x / fft_tpt(M) transforms, at most max(fft_tpt(M), 256) threads.  MINB is
+// the builds' CTAs-per-SM target: FP32 transforms are limited to 64 (M = 6144 or 8192, MINB = 2)
+// or 128 (M <= 4096) registers.
+template <int M> constexpr int dft_max_threads() { return fft_tpt(M) > 256 ? fft_tpt(M) : 256; }
 
 template <typename R, int M, int MINB>
 __global__ void __launch_bounds__(dft_max_threads<M>(), MINB)
 bluestein_kernel(BatchView bv) {
   using C = typename Cx<R>::T;
-  constexpr int TPT = M / 16;                      // threads per transform
+  constexpr int TPT = fft_tpt(M);                  // threads per transform
   const int G = blockDim.x / TPT;                  // transforms per CTA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -308,17 +374,17 @@ bluestein_kernel(BatchView bv) {
   const C* W = reinterpret_cast<const C*>(d.fftw);
   C* s = buf + g * padded_len<M>();
   const ChirpIO<C> io{in, chirp, vhat, out, active ? p : 0};
-  // p <= M/2: at most 8 input elements per thread.  (The unroll factors of this and the filter
-  // sweep are the largest that keep the FP32 builds free of register spills.)
+  // p <= M/2: at most 8 (or 6) input elements per thread.  (The unroll factors of this and the
+  // filter sweep are the largest that keep the FP32 builds free of register spills.)
 #pragma unroll 4
-  for (int it = 0; it < 8; ++it) {
+  for (int it = 0; it < M / 2 / TPT; ++it) {
     const int n = lt + it * TPT;
     if (n < io.p) s[pad16(n)] = cmul(__ldg(in + n), __ldg(chirp + n));
   }
   __syncthreads();
   FFTPasses<C, M, 2, TPT, kFromInput, kToSmem>::run(s, lt, W, io);
 #pragma unroll 8
-  for (int it = 0; it < 16; ++it) {
+  for (int it = 0; it < M / TPT; ++it) {
     const int n = lt + it * TPT;
     s[pad16(n)] = cconj(cmul(s[pad16(n)], __ldg(vhat + n)));
   }
@@ -326,21 +392,19 @@ bluestein_kernel(BatchView bv) {
   radix2_first<C, M, TPT>(s, lt);
   FFTPasses<C, M, 2, TPT, kFromSmem, kToOutput>::run(s, lt, W, io);
 }
-template <int M> constexpr int log2_of() { return M <= 1 ? 0 : 1 + log2_of<M / 2>(); }
-
 template <typename R, int M, int MINB>
 cudaError_t launch_MB(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, int* launched) {
   using C = typename Cx<R>::T;
-  constexpr int cls = log2_of<M>() - 6;
-  const unsigned grid = (unsigned)ls.blocks[kStBluestein0 + cls];
+  const int stage = fft_stage(M);
+  const unsigned grid = (unsigned)ls.blocks[stage];
   if (grid == 0) return cudaSuccess;
-  const int G = ls.tune.dft_per_cta[cls];
-  const int threads = (M / 16) * G;
+  const int G = ls.tune.dft_per_cta[fft_tune_class(M)];
+  const int threads = fft_tpt(M) * G;
   const size_t smem = (size_t)G * padded_len<M>() * sizeof(C);
   cudaError_t e = ensure_dynamic_smem<bluestein_kernel<R, M, MINB>>(smem);
   if (e != cudaSuccess) return e;
   BatchView v = bv;
-  v.blk = ls.blk[kStBluestein0 + cls];
+  v.blk = ls.blk[stage];
   bluestein_kernel<R, M, MINB><<<grid, threads, smem, st>>>(v);
   if (launched) ++*launched;
   return cudaGetLastError();
@@ -351,7 +415,7 @@ cudaError_t launch_M(const BatchView& bv, const LaunchSet& ls, cudaStream_t st, 
   if constexpr (sizeof(R) == 4 && M == 8192) {
     if (!ls.tune.dft_two_ctas) return launch_MB<R, M, 1>(bv, ls, st, launched);
   }
-  constexpr int MINB = (sizeof(R) == 4 && M <= 8192) ? 2 : 1;
+  constexpr int MINB = (sizeof(R) == 4 && fft_tpt(M) <= 512) ? 2 : 1;
   return launch_MB<R, M, MINB>(bv, ls, st, launched);
 }
 
@@ -368,6 +432,15 @@ cudaError_t launch_prec(const BatchView& bv, const LaunchSet& ls, cudaStream_t s
   if (e == cudaSuccess) e = launch_M<R, 8192>(bv, ls, st, launched);
   if constexpr (sizeof(R) == 4)
     if (e == cudaSuccess) e = launch_M<R, 16384>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 96>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 192>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 384>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 768>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 1536>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 3072>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 6144>(bv, ls, st, launched);
+  if constexpr (sizeof(R) == 4)
+    if (e == cudaSuccess) e = launch_M<R, 12288>(bv, ls, st, launched);
   return e;
 }
 

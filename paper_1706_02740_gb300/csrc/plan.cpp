@@ -105,9 +105,8 @@ std::vector<int32_t> choose_small(int64_t N, const std::vector<int32_t>& primes)
   return T;
 }
 
-// In-place iterative radix-2 FFT (forward, exp(-2 pi i n k / M)), M a power of two, used once per
-// plan to transform the chirp filter.
-void host_fft(std::vector<cd>& a) {
+// In-place iterative radix-2 FFT (forward, exp(-2 pi i n k / M)), M a power of two.
+void host_fft_pow2(std::vector<cd>& a) {
   const size_t M = a.size();
   for (size_t i = 1, j = 0; i < M; ++i) {
     size_t bit = M >> 1;
@@ -126,6 +125,28 @@ void host_fft(std::vector<cd>& a) {
       }
     }
   }
+}
+
+cd expi_turns(int64_t num, int64_t den);
+
+// Forward FFT of length M = 2^k or 3 2^k, used once per plan to transform the chirp filter.  For
+// M = 3 M', one decimation in time: with A_r the length-M' transforms of a[3n + r],
+// X[k + M' u] = sum_r e^{-2 pi i r (k + M' u) / M} A_r[k], u = 0, 1, 2.
+void host_fft(std::vector<cd>& a) {
+  const size_t M = a.size();
+  if (M % 3 != 0) { host_fft_pow2(a); return; }
+  const size_t Mp = M / 3;
+  std::vector<cd> A[3];
+  for (int r = 0; r < 3; ++r) {
+    A[r].resize(Mp);
+    for (size_t n = 0; n < Mp; ++n) A[r][n] = a[3 * n + r];
+    host_fft_pow2(A[r]);
+  }
+  for (size_t k = 0; k < Mp; ++k)
+    for (int u = 0; u < 3; ++u) {
+      const int64_t kk = (int64_t)(k + Mp * u);
+      a[kk] = A[0][k] + expi_turns(-kk, (int64_t)M) * A[1][k] + expi_turns(-2 * kk, (int64_t)M) * A[2][k];
+    }
 }
 
 cd expi_turns(int64_t num, int64_t den) {
@@ -234,14 +255,12 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   for (int32_t t : small) nsub += t - 1;
   if (nsub > kMaxSub) { set_error("too many node subsets (sum of t_l - 1 must be < 128)"); return SFT_EINVAL; }
   const int32_t pmax = primes.back();
-  int M = 64;
-  while (M < 2 * pmax - 1) M <<= 1;
-  if (M > (fp64 ? kMaxFFT64 : kMaxFFT32)) {
+  const int M = fft_length(2 * (int64_t)pmax - 1, fp64 ? kMaxFFT64 : kMaxFFT32);
+  if (M == 0) {
     set_error(fp64 ? "FP64 plans need every p_j <= 4096" : "FP32 plans need every p_j <= 8192");
     return SFT_EINVAL;
   }
-  int logM = 0;
-  while ((1 << logM) < M) ++logM;
+  const int logM = fft_log2(M);
 
   // ---- fill the device-plan scalars
   d.N = N; d.s = s; d.kappa = v->kappa; d.K = K; d.nT = nT; d.nq = (int32_t)nq; d.nsub = nsub;

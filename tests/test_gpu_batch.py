@@ -110,10 +110,11 @@ def _tuning_variants(prec):
 
 
 def _mixed_plans(prec):
-    # the last member has p >= 3000, so the FP32 path also uses the M = 8192 length class
-    shapes = SHAPES + [(2 ** 18, 1000)]
+    # the last two members have p near 3000 and 3600: chirp lengths 6144 and (FP32) 8192, next to
+    # the small lengths 96 .. 512 of the others, of both kinds (2^k and 3 2^k)
+    shapes = SHAPES + [(2 ** 18, 1000), (2 ** 18, 1200)]
     plans = [sft.sft_plan(N, s, sft.sft_variant_init(precision=prec, K=5,
-                                                     c_p=3.0 if s == 1000 else 6.0, seed=i))
+                                                     c_p=3.0 if s >= 1000 else 6.0, seed=i))
              for i, (N, s) in enumerate(shapes)]
     sigs = _signals(shapes, 700)
     return shapes, plans, sigs

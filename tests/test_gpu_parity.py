@@ -97,6 +97,44 @@ def test_stages_and_output_match_oracle(case, prec):
     assert np.all(g["freqs"][n:] == 0) and np.all(g["coefs"][n:] == 0)
 
 
+# Chirp-convolution lengths 3 2^k: last passes of radix 3, 6, 12, and 12 then 2; the largest prime
+# of each plan is the largest below M/2 (the edge of the skipped first radix-2 pass).
+LENGTHS_3 = [(96, [37, 41, 47]), (192, [67, 89]), (384, [131, 191]), (768, [257, 383]),
+             (1536, [521, 761]), (3072, [1031, 1531]), (6144, [2053, 3067]), (12288, [4099, 6143])]
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+@pytest.mark.parametrize("M,primes", LENGTHS_3)
+def test_three_times_power_of_two_lengths_match_oracle(M, primes, prec):
+    if prec == U.FP64 and M > 6144:
+        pytest.skip("FP64 chirp convolutions stop at length 8192")
+    N, s = 2 ** 14, 4
+    sig = make_signal(N, s, M, "unit", 30.0)
+    f32 = as_complex64(sig.f)
+    f = upcast(f32)
+    g = U.run_gpu(sft, N, s, f32 if prec == U.FP32 else f, prec, 6, len(primes), 3.0, 0,
+                  primes=primes, keep=True)
+    info, plan = g["info"], g["plan"]
+    assert info["fft_size"] == M
+    oplan = U.oracle_plan(info, N, s)
+    _, bins, _, _ = U.debug_arrays(sft, plan, info)
+    plan.destroy()
+    tol = 2e-6 if prec == U.FP32 else 1e-13
+    for qi, q in enumerate(info["shifts"]):
+        for j, p in enumerate(primes):
+            Z = U.subbins(info, bins[qi], j)
+            Y = O.measure(f, oplan, q, p)
+            bmax = np.max(np.abs(Y))
+            assert np.max(np.abs(Z[0] - Y)) <= tol * bmax
+            for l, t in enumerate(info["small"]):
+                Xr = U.folded_subbins(info, Z, l)
+                X = O.measure(f, oplan, q, p * t)
+                b = np.arange(p)
+                for r in range(t):
+                    u = ((r - b) * pow(p, -1, t)) % t
+                    assert np.max(np.abs(Xr[r] - X[b + p * u])) <= tol * bmax
+
+
 @pytest.mark.parametrize("prec", [U.FP32, U.FP64])
 def test_config1_recovers_truth(prec):
     """Configuration 1 (N = 2^16, s = 8, unit magnitudes, no noise): the exact support, against
