@@ -50,30 +50,77 @@ __device__ __forceinline__ void decode_bin(const DevPlan& d, int64_t gid, int& q
   b = bin - d.poff[j];
 }
 
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
+
 // Residue of bin b modulo a small modulus T: argmax over r of |X_r|^2 with
 // X_r = sum_{k2 < T} Z_{k2}[b] e^{-2 pi i k2 r / T} (the 1/T factor does not change the argmax);
 // exact ties go to the smaller sub-bin index u = (r - b) p^{-1} mod T.
+// For odd T the terms k2 and T - k2 are paired: with A_k = z_k + z_{T-k}, B_k = z_k - z_{T-k},
+// c = cos(2 pi k r / T), s = sin(2 pi k r / T),
+//     X_r = z_0 + sum_k (c A_k - i s B_k),   X_{T-r} = z_0 + sum_k (c A_k + i s B_k),
+// so each pair (r, T - r) costs two real-by-complex sums of (T-1)/2 terms instead of two complex
+// sums of T - 1.  The comparison (largest |X|^2, then smallest u) does not depend on the order in
+// which the r are visited.
 template <int T, typename C, typename R>
 __device__ __forceinline__ int residue_t(C z0, const C* Zl, int64_t p, const C* twl, int bt, int pinv) {
-  C z[T], tw[T];
+  C z[T];
   z[0] = z0;
 #pragma unroll
   for (int k2 = 1; k2 < T; ++k2) z[k2] = Zl[(int64_t)k2 * p];
-#pragma unroll
-  for (int k = 0; k < T; ++k) tw[k] = __ldg(twl + k);
   R best = (R)-1;
   int bestu = 1 << 30, bestr = 0;
-#pragma unroll
-  for (int r = 0; r < T; ++r) {
-    C X = z[0];
-#pragma unroll
-    for (int k2 = 1; k2 < T; ++k2) X = cadd(X, cmul(z[k2], tw[(k2 * r) % T]));
+  auto consider = [&](const C& X, int r, int u) {
     const R m2 = X.x * X.x + X.y * X.y;
-    const int u = (((r - bt) % T + T) % T) * pinv % T;
     if (m2 > best || (m2 == best && u < bestu)) {
       best = m2;
       bestu = u;
       bestr = r;
+    }
+  };
+  const int u0 = ((T - bt) % T) * pinv % T;      // u of r = 0; u of r +/- 1 moves by +/- pinv
+  if constexpr (T == 2) {
+    consider(cadd(z[0], z[1]), 0, u0);
+    consider(csub(z[0], z[1]), 1, (u0 + pinv) % 2);
+  } else {
+    constexpr int H = (T - 1) / 2;
+    // cos and sin of 2 pi m / T for m = 1..H from the table e^{-2 pi i m / T} (m > H follows by
+    // symmetry: cos(2 pi (T - m) / T) = cos(2 pi m / T), sin(2 pi (T - m) / T) = -sin(2 pi m / T))
+    R cs[H + 1], sn[H + 1];
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+      const C w = __ldg(twl + m);
+      cs[m] = w.x;
+      sn[m] = -w.y;
+    }
+    C A[H + 1], B[H + 1];
+    C X0 = z[0];
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+      A[k] = cadd(z[k], z[T - k]);
+      B[k] = csub(z[k], z[T - k]);
+      X0 = cadd(X0, A[k]);
+    }
+    consider(X0, 0, u0);
+    int up = u0, un = u0;
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      C P = z[0], Q = czero<C>();
+#pragma unroll
+      for (int k = 1; k <= H; ++k) {
+        const int m = (k * r) % T;
+        const R c = m <= H ? cs[m] : cs[T - m], s = m <= H ? sn[m] : -sn[T - m];
+        P.x = r_fma(A[k].x, c, P.x);
+        P.y = r_fma(A[k].y, c, P.y);
+        Q.x = r_fma(B[k].x, s, Q.x);
+        Q.y = r_fma(B[k].y, s, Q.y);
+      }
+      up += pinv;
+      if (up >= T) up -= T;
+      un -= pinv;
+      if (un < 0) un += T;
+      consider(C{P.x + Q.y, P.y - Q.x}, r, up);           // X_r = P - i Q
+      consider(C{P.x - Q.y, P.y + Q.x}, T - r, un);       // X_{T-r} = P + i Q
     }
   }
   return bestr;

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
   const float2* Wp = d.wp32 + (int64_t)jj * d.pmax;
   for (int i = threadIdx.x; i < p; i += kReChunk) Wt[i] = __ldg(Wp + i);
   __syncthreads();
-  float4* part = reinterpret_cast<float4*>(d.ybuf) + (int64_t)c * d.s * d.K;
+  float4* part = reinterpret_cast<float4*>(d.ybuf);
   const float4* S4 = reinterpret_cast<const float4*>(S);
   for (int t = threadIdx.x; t < cnt; t += kReChunk) {
     const int r = d.wlist[beg + t];
@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
       ib += b16;
       if (ib >= p) ib -= p;
     }
-    part[(int64_t)r * d.K + jj] = make_float4(sr, cr, si, ci);
+    // partials of (winner, prime) are contiguous over the chunks: [r][K][nchunk]
+    part[((int64_t)r * d.K + jj) * d.nchunk + c] = make_float4(sr, cr, si, ci);
   }
 }
 
@@ -177,17 +178,26 @@ __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView
   for (int jj = 0; jj < d.K; ++jj) {
     const int p = d.p[jj];
     const int nc = (p + kReChunk - 1) / kReChunk;
-    // double-single accumulation of the chunk partials (hi, lo) for the real and imaginary parts
+    const float4* pc = part + ((int64_t)r * d.K + jj) * d.nchunk;
+    // double-single accumulation of the chunk partials (hi, lo) for the real and imaginary parts,
+    // in chunk order; the loads of four chunks are issued together
     float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
-    for (int c = 0; c < nc; ++c) {
-      const float4 v = part[((int64_t)c * d.s + r) * d.K + jj];
-      float s, e;
-      two_sum(hr, v.x, s, e);
-      lr += e + v.y;
-      two_sum(s, lr, hr, lr);
-      two_sum(hi, v.z, s, e);
-      li += e + v.w;
-      two_sum(s, li, hi, li);
+    for (int c0 = 0; c0 < nc; c0 += 4) {
+      float4 v4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v4[u] = c0 + u < nc ? pc[c0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (c0 + u >= nc) break;
+        const float4 v = v4[u];
+        float s, e;
+        two_sum(hr, v.x, s, e);
+        lr += e + v.y;
+        two_sum(s, lr, hr, lr);
+        two_sum(hi, v.z, s, e);
+        li += e + v.w;
+        two_sum(s, li, hi, li);
+      }
     }
     const double inv_p = 1.0 / (double)p;
     re[jj] = ((double)hr + (double)lr) * inv_p;

@@ -85,7 +85,7 @@ struct DevPlan {
   Voted* voted;               // [nq][vcap]
   Pooled* pool;               // [nq * s]
   Pooled* winners;            // [s]
-  double2* ybuf;              // [nchunk][s][K] partial sums of the re-estimated bins
+  double2* ybuf;              // [s][K][nchunk] partial sums of the re-estimated bins
   int32_t* wlist;             // [s] winner indices grouped by shift
   int32_t* woff;              // [nq + 1] start of each shift's group in wlist
   double* epart;              // [kEnergyBlocks] partial sums of |f|^2 (residual-energy check)
