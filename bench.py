@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--s", type=int, default=S_DEFAULT)
-    ap.add_argument("--batch", type=int, default=16, help="SFTs per step (one batched execution)")
+    ap.add_argument("--batch", type=int, default=64, help="SFTs per step (one batched execution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inputs", type=int, default=N_INPUTS,
                     help="distinct resident inputs that rotate (each N complex64)")

@@ -6,12 +6,12 @@
 // is recomputed directly from the same filtered samples with twiddles e^{-2 pi i ((k b) mod p_j) / p_j}
 // taken as products of two exactly rounded table entries.
 //
-// Work layout: one CTA per (shift, prime, chunk of kReChunk samples).  The CTA stages its chunk and
-// the prime's twiddle table in shared memory, and each thread sums the chunk against one winner's
-// twiddles in blocks of 16 terms: the block's twiddles factor as w^{(k0 + 16 m) b} w^{j b}, so a
-// thread reads its 16 powers w^{j b} once per chunk and one block factor per 16 terms (exactly
-// rounded table entries both), takes FMA sums within blocks and adds the block values with
-// compensation (Neumaier), in FP32.  The chunk partials, kept as
+// Work layout: one CTA of kReThreads threads per (shift, prime, chunk of kReChunk samples).  The
+// CTA stages its chunk and the prime's twiddle table in shared memory, and each thread sums the
+// chunk against one winner's twiddles in blocks of 16 terms: the block's twiddles factor as
+// w^{(k0 + 16 m) b} w^{j b}, so a thread reads its 16 powers w^{j b} once per chunk and one block
+// factor per 16 terms (exactly rounded table entries both), takes FMA sums within blocks and adds
+// the block values with compensation (Neumaier), in FP32.  The chunk partials, kept as
 // (sum, compensation) pairs, are combined exactly enough in double-single arithmetic.  The
 // componentwise medians (eq. GSFT_Estimate), the sign (-1)^w and the division by g_hat_{w - q}
 // (Lemma Periodic_Gaussian_FC) are done in FP64, spread over many CTAs.  All integer indexing is
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) group_winners_kernel(BatchView bv) {
   for (int r = threadIdx.x; r < n; r += 256) d.wlist[atomicAdd(&cur[d.winners[r].qi], 1)] = r;
 }
 
-__global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
+__global__ void __launch_bounds__(kReThreads) reestimate_kernel(BatchView bv) {
   // [kReChunk] samples of this chunk, then the prime's [p] twiddles: each thread walks its own
   // residue sequence (k b) mod p, so the table reads scatter across the warp; shared memory serves
   // them with a few bank conflicts where the cached global table would take one line per lane.
@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(kReChunk) reestimate_kernel(BatchView bv) {
   float2* S = sm_re;
   float2* Wt = sm_re + kReChunk;
   const float2* src = reinterpret_cast<const float2*>(d.samples) + (int64_t)qi * d.m + d.nodeoff[jj];
-  if (threadIdx.x < klen) S[threadIdx.x] = src[k0 + threadIdx.x];
+  for (int i = threadIdx.x; i < klen; i += kReThreads) S[i] = src[k0 + i];
   const float2* Wp = d.wp32 + (int64_t)jj * d.pmax;
-  for (int i = threadIdx.x; i < p; i += kReChunk) Wt[i] = __ldg(Wp + i);
+  for (int i = threadIdx.x; i < p; i += kReThreads) Wt[i] = __ldg(Wp + i);
   __syncthreads();
   float4* part = reinterpret_cast<float4*>(d.ybuf);
   const float4* S4 = reinterpret_cast<const float4*>(S);
-  for (int t = threadIdx.x; t < cnt; t += kReChunk) {
+  for (int t = threadIdx.x; t < cnt; t += kReThreads) {
     const int r = d.wlist[beg + t];
     const int b = mod_p32(d.winners[r].w, p);
     // The chunk's sum in blocks of 16 consecutive k = k0 + 16 m + j:
@@ -223,7 +223,7 @@ cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t
   const size_t smem = (size_t)(kReChunk + ls.pmax) * sizeof(float2);
   const cudaError_t e = ensure_dynamic_smem<reestimate_kernel>(smem);
   if (e != cudaSuccess) return e;
-  reestimate_kernel<<<ls.blocks[kStReest], kReChunk, smem, st>>>(v);
+  reestimate_kernel<<<ls.blocks[kStReest], kReThreads, smem, st>>>(v);
   v.blk = ls.blk[kStRefine];
   if (ls.kmax <= kFewK) refine_values_kernel<kFewK><<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
   else refine_values_kernel<kMaxK><<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);

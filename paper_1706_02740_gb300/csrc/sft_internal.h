@@ -91,7 +91,8 @@ struct DevPlan {
   double* epart;              // [kEnergyBlocks] partial sums of |f|^2 (residual-energy check)
 };
 
-constexpr int kReChunk = 256;   // samples per re-estimation CTA
+constexpr int kReChunk = 512;   // samples per re-estimation CTA (the prime's table is staged once per chunk)
+constexpr int kReThreads = 256; // its threads: one winner each per round
 constexpr int kResampleMaxThreads = 512;      // largest CTA of the kappa = 4 / 6 resampling kernel
 constexpr int kResampleGenericThreads = 128;
 constexpr int kBinMaxThreads = 512;    // identify / vote: one thread per bin, at most 512 per CTA
