@@ -114,8 +114,9 @@ typedef struct {
   int64_t L;                          /* band half-width ceil(N/(alpha sqrt(ln N))) */
   double c1;                          /* Gaussian width beta sqrt(ln N)/N */
   int64_t nodes;                      /* distinct nodes m = n_sub * sum_j p_j */
-  int32_t fft_size;                   /* chirp-convolution length: the smallest 2^k >= 64 or
-                                         3 2^k >= 96 that is >= 2 p_K - 1 */
+  int32_t fft_size;                   /* chirp-convolution length: the smallest of 2^k >= 64,
+                                         3 2^k >= 96, 5 2^k >= 640, 7 2^k >= 896 that is
+                                         >= 2 p_K - 1 */
   int32_t precision;
   int32_t input;
   int32_t reserved;

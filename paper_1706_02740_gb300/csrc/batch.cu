@@ -382,9 +382,11 @@ sft_status sft_batch_autotune(sft_batch_t batch, const void* const* f_devs,
   }
   // chirp convolution: transforms per CTA of every length class present, then the FP32 8192 build
   for (int c = 0; c < 9 && s == SFT_OK; ++c) {
-    // the class of 2^(c+6) and that of 3 2^(c+4), which has as many threads per transform
-    if (B.ls.blocks[kStBluestein0 + c] == 0 && (c == 0 || B.ls.blocks[kStBluestein3 + c - 1] == 0))
-      continue;
+    // the lengths with as many threads per transform as 2^(c+6) (2^k and r 2^k share an entry)
+    bool present = false;
+    for (int k = kStBluestein0; k < kStCount; ++k)
+      present |= B.ls.blocks[k] > 0 && fft_tune_class(fft_stage_length(k)) == c;
+    if (!present) continue;
     const int M = 64 << c, hi = M >= 4096 ? 1 : 4096 / M;
     if (hi == 1) continue;
     cands.clear();

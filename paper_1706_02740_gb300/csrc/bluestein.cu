@@ -3,14 +3,16 @@
 //
 // Each p_j is prime, so the length-p DFT is taken as a chirp convolution (Bluestein): with
 // w_n = e^{-pi i n^2 / p},  E_c = (1/p) w_c sum_k (h_k w_k) conj(w_{c-k}),  a linear convolution
-// done as a cyclic one of length M >= 2p - 1, M = 2^k or 3 2^k (whichever is smaller):
+// done as a cyclic one of length M >= 2p - 1, M = r 2^k with r = 1, 3, 5 or 7 (the smallest):
 //     E = w . conj( FFT( conj( FFT(h w, zero padded) . V ) ) ),
 // V = FFT(conj(w) wrapped) / (M p) precomputed per prime in FP64 on the host (the inverse FFT is the
 // forward one between two conjugations).  One transform lives in shared memory; the FFT is an
 // in-place Stockham schedule whose passes hold at most 16 complex values per thread in registers:
-// a radix-2 first pass, radix-16 passes, then the radix 2/4/8 (or 3/6/12, and 12 then 2) passes
-// that M needs, with twiddles read from exactly rounded per-pass tables.  Since p <= M/2, the
-// first FFT's radix-2 pass only duplicates its input and is skipped.
+// a radix-2 first pass, radix-16 passes, then the passes that M needs (radix 2/4/8, or 3/6/12,
+// 5/10 or 7/14, possibly followed by a radix 2 or 4), with twiddles read from exactly rounded
+// per-pass tables.  The radix 5 and 7 butterflies pair the terms k and T - k (real cosine and sine
+// sums); 6, 10, 12 and 14 are prime-factor compositions without internal twiddles.  Since
+// p <= M/2, the first FFT's radix-2 pass only duplicates its input and is skipped.
 // The shared-memory layout inserts one pad element after every 16 (index n -> n + n/16), so the
 // strided stores of the short-span passes hit distinct banks.
 #include <stdint.h>
@@ -35,6 +37,15 @@ constexpr double kS8 = 0.38268343236508977;
 constexpr double kH = 0.70710678118654752;
 // sqrt(3)/2, the sine of the radix-3 butterfly.
 constexpr double kS3 = 0.86602540378443865;
+// cos(2 pi m / T) and sin(2 pi m / T), m = 1..(T-1)/2, of the radix-5 and radix-7 butterflies.
+__host__ __device__ constexpr double odd_cos(int T, int m) {
+  return T == 5 ? (m == 1 ? 0.30901699437494742 : -0.80901699437494742)
+                : (m == 1 ? 0.62348980185873353 : m == 2 ? -0.22252093395631440 : -0.90096886790241913);
+}
+__host__ __device__ constexpr double odd_sin(int T, int m) {
+  return T == 5 ? (m == 1 ? 0.95105651629515357 : 0.58778525229247313)
+                : (m == 1 ? 0.78183148246802981 : m == 2 ? 0.97492791218182361 : 0.43388373911755812);
+}
 
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
@@ -102,6 +113,48 @@ template <typename C> struct DFT<3, C> {
     a[2] = C{r_fma(d.y, -(R)kS3, m.x), r_fma(d.x, (R)kS3, m.y)};
   }
 };
+// Odd prime T = 5, 7 with the terms k and T - k paired: A_k = a_k + a_{T-k}, B_k = a_k - a_{T-k},
+//     X_r = a_0 + sum_k (cos(2 pi k r / T) A_k - i sin(2 pi k r / T) B_k),
+//     X_{T-r} = a_0 + sum_k (cos(2 pi k r / T) A_k + i sin(2 pi k r / T) B_k),   k, r = 1..(T-1)/2.
+template <int T, typename C>
+__device__ __forceinline__ void dft_odd_prime(C* a) {
+  using R = decltype(a[0].x);
+  constexpr int H = (T - 1) / 2;
+  C A[H + 1], B[H + 1];
+  C X0 = a[0];
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    A[k] = cadd(a[k], a[T - k]);
+    B[k] = csub(a[k], a[T - k]);
+    X0 = cadd(X0, A[k]);
+  }
+  C out[T];
+  out[0] = X0;
+#pragma unroll
+  for (int r = 1; r <= H; ++r) {
+    C P = a[0], Q = C{(R)0, (R)0};
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+      const int m = (k * r) % T;
+      const R c = (R)(m <= H ? odd_cos(T, m) : odd_cos(T, T - m));
+      const R sn = (R)(m <= H ? odd_sin(T, m) : -odd_sin(T, T - m));
+      P.x = r_fma(A[k].x, c, P.x);
+      P.y = r_fma(A[k].y, c, P.y);
+      Q.x = r_fma(B[k].x, sn, Q.x);
+      Q.y = r_fma(B[k].y, sn, Q.y);
+    }
+    out[r] = C{P.x + Q.y, P.y - Q.x};          // P - i Q
+    out[T - r] = C{P.x - Q.y, P.y + Q.x};      // P + i Q
+  }
+#pragma unroll
+  for (int r = 0; r < T; ++r) a[r] = out[r];
+}
+template <typename C> struct DFT<5, C> {
+  __device__ static __forceinline__ void run(C* a) { dft_odd_prime<5>(a); }
+};
+template <typename C> struct DFT<7, C> {
+  __device__ static __forceinline__ void run(C* a) { dft_odd_prime<7>(a); }
+};
 // Prime-factor (Good-Thomas) forms, no twiddles: for R = R1 R2 with gcd(R1, R2) = 1, input
 // n = (R2 n1 + R1 n2) mod R and output k = (k1 R2 (R2^-1 mod R1) + k2 R1 (R1^-1 mod R2)) mod R
 // turn the length-R DFT into length-R1 DFTs over n1 and length-R2 DFTs over n2.
@@ -116,6 +169,30 @@ template <typename C> struct DFT<6, C> {
     a[4] = cadd(u[1], v[1]); a[1] = csub(u[1], v[1]);
     a[2] = cadd(u[2], v[2]); a[5] = csub(u[2], v[2]);
   }
+};
+// 2T = 2 x T (T = 5, 7): n = (T n1 + 2 n2) mod 2T, k = (T k1 + 2 (2^-1 mod T) k2) mod 2T.
+template <int T, typename C>
+__device__ __forceinline__ void dft_two_odd(C* a) {
+  constexpr int N = 2 * T, I2 = (T + 1) / 2;     // 2^-1 mod T
+  C u[T], v[T];
+#pragma unroll
+  for (int n2 = 0; n2 < T; ++n2) {
+    u[n2] = a[(2 * n2) % N];
+    v[n2] = a[(T + 2 * n2) % N];
+  }
+  DFT<T, C>::run(u);
+  DFT<T, C>::run(v);
+#pragma unroll
+  for (int k2 = 0; k2 < T; ++k2) {
+    a[(2 * I2 * k2) % N] = cadd(u[k2], v[k2]);
+    a[(T + 2 * I2 * k2) % N] = csub(u[k2], v[k2]);
+  }
+}
+template <typename C> struct DFT<10, C> {
+  __device__ static __forceinline__ void run(C* a) { dft_two_odd<5>(a); }
+};
+template <typename C> struct DFT<14, C> {
+  __device__ static __forceinline__ void run(C* a) { dft_two_odd<7>(a); }
 };
 // 12 = 3 x 4: n = (4 n1 + 3 n2) mod 12, k = (4 k1 + 9 k2) mod 12.
 template <typename C> struct DFT<12, C> {
@@ -199,13 +276,6 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C
   } else if constexpr (RAD == 3) {
     v[1] = cmul(v[1], __ldg(W + base + k));
     v[2] = cmul(v[2], __ldg(W + base + SPAN + k));
-  } else if constexpr (RAD == 6) {
-    const C w1 = __ldg(W + base + k), P = __ldg(W + base + 3 * SPAN + k);   // w, w^4
-    v[1] = cmul(v[1], w1);
-    v[2] = cmul(v[2], __ldg(W + base + SPAN + k));
-    v[3] = cmul(v[3], __ldg(W + base + 2 * SPAN + k));
-    v[4] = cmul(v[4], P);
-    v[5] = cmul(v[5], cmul(P, w1));
   } else {
     const C w1 = __ldg(W + base + k), w2 = __ldg(W + base + SPAN + k),
             w3 = __ldg(W + base + 2 * SPAN + k);
@@ -213,12 +283,12 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C
     v[2] = cmul(v[2], w2);
     v[3] = cmul(v[3], w3);
 #pragma unroll
-    for (int a = 1; a < RAD / 4; ++a) {
+    for (int a = 1; 4 * a < RAD; ++a) {
       const C P = __ldg(W + base + (2 + a) * SPAN + k);     // w^{4a}
       v[4 * a] = cmul(v[4 * a], P);
-      v[4 * a + 1] = cmul(v[4 * a + 1], cmul(P, w1));
-      v[4 * a + 2] = cmul(v[4 * a + 2], cmul(P, w2));
-      v[4 * a + 3] = cmul(v[4 * a + 3], cmul(P, w3));
+      if (4 * a + 1 < RAD) v[4 * a + 1] = cmul(v[4 * a + 1], cmul(P, w1));
+      if (4 * a + 2 < RAD) v[4 * a + 2] = cmul(v[4 * a + 2], cmul(P, w2));
+      if (4 * a + 3 < RAD) v[4 * a + 3] = cmul(v[4 * a + 3], cmul(P, w3));
     }
   }
 }
@@ -233,6 +303,8 @@ __device__ __forceinline__ void apply_twiddles(const C* __restrict__ W, int k, C
 // LOAD == kFromInput is the first pass after the radix-2 first pass of a transform whose input
 // x vanishes from p <= M/2 on: that radix-2 pass only duplicates (y[2i] = y[2i + 1] = x[i]), so it
 // is never run and this pass reads y[n] = x[n / 2] from the first p entries of shared memory.
+// (Forming x = h w from global memory inside this pass instead of a staging sweep measured slower:
+// length 6144, 589 against 480 us per 16 SFTs.)
 // Offsets of an item's elements: (a + 16 e) >> 4 = (a >> 4) + e, so when the element stride d is
 // a multiple of 16, pad16(a + r d) = pad16(a) + r (d + d / 16): one padded base per item and
 // compile-time offsets instead of a shift and an add per access.
@@ -374,8 +446,8 @@ bluestein_kernel(BatchView bv) {
   const C* W = reinterpret_cast<const C*>(d.fftw);
   C* s = buf + g * padded_len<M>();
   const ChirpIO<C> io{in, chirp, vhat, out, active ? p : 0};
-  // p <= M/2: at most 8 (or 6) input elements per thread.  (The unroll factors of this and the
-  // filter sweep are the largest that keep the FP32 builds free of register spills.)
+  // p <= M/2: at most 8 (or 7, 6, 5) input elements per thread.  (The unroll factors of this and
+  // the filter sweep are the largest that keep the FP32 builds free of register spills.)
 #pragma unroll 4
   for (int it = 0; it < M / 2 / TPT; ++it) {
     const int n = lt + it * TPT;
@@ -383,6 +455,9 @@ bluestein_kernel(BatchView bv) {
   }
   __syncthreads();
   FFTPasses<C, M, 2, TPT, kFromInput, kToSmem>::run(s, lt, W, io);
+  // the filter product, conjugated, in its own sweep: folded into the radix-2 pass below it adds
+  // sixteen loads in flight per thread (spills at 64 registers) and, fenced to fewer, measured
+  // slower (length 6144: 675 against 480 us per 16 SFTs)
 #pragma unroll 8
   for (int it = 0; it < M / TPT; ++it) {
     const int n = lt + it * TPT;
@@ -439,8 +514,19 @@ cudaError_t launch_prec(const BatchView& bv, const LaunchSet& ls, cudaStream_t s
   if (e == cudaSuccess) e = launch_M<R, 1536>(bv, ls, st, launched);
   if (e == cudaSuccess) e = launch_M<R, 3072>(bv, ls, st, launched);
   if (e == cudaSuccess) e = launch_M<R, 6144>(bv, ls, st, launched);
-  if constexpr (sizeof(R) == 4)
+  if (e == cudaSuccess) e = launch_M<R, 640>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 1280>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 2560>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 5120>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 896>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 1792>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 3584>(bv, ls, st, launched);
+  if (e == cudaSuccess) e = launch_M<R, 7168>(bv, ls, st, launched);
+  if constexpr (sizeof(R) == 4) {
     if (e == cudaSuccess) e = launch_M<R, 12288>(bv, ls, st, launched);
+    if (e == cudaSuccess) e = launch_M<R, 10240>(bv, ls, st, launched);
+    if (e == cudaSuccess) e = launch_M<R, 14336>(bv, ls, st, launched);
+  }
   return e;
 }
 

@@ -129,23 +129,25 @@ void host_fft_pow2(std::vector<cd>& a) {
 
 cd expi_turns(int64_t num, int64_t den);
 
-// Forward FFT of length M = 2^k or 3 2^k, used once per plan to transform the chirp filter.  For
-// M = 3 M', one decimation in time: with A_r the length-M' transforms of a[3n + r],
-// X[k + M' u] = sum_r e^{-2 pi i r (k + M' u) / M} A_r[k], u = 0, 1, 2.
+// Forward FFT of length M = r 2^k (r = 1, 3, 5, 7), used once per plan to transform the chirp
+// filter.  For r > 1, one decimation in time: with A_t the length-M' (M' = M / r) transforms of
+// a[r n + t], X[k + M' u] = sum_t e^{-2 pi i t (k + M' u) / M} A_t[k], u = 0..r-1.
 void host_fft(std::vector<cd>& a) {
   const size_t M = a.size();
-  if (M % 3 != 0) { host_fft_pow2(a); return; }
-  const size_t Mp = M / 3;
-  std::vector<cd> A[3];
-  for (int r = 0; r < 3; ++r) {
-    A[r].resize(Mp);
-    for (size_t n = 0; n < Mp; ++n) A[r][n] = a[3 * n + r];
-    host_fft_pow2(A[r]);
+  const int r = fft_odd((int)M);
+  if (r == 1) { host_fft_pow2(a); return; }
+  const size_t Mp = M / r;
+  std::vector<std::vector<cd>> A(r, std::vector<cd>(Mp));
+  for (int t = 0; t < r; ++t) {
+    for (size_t n = 0; n < Mp; ++n) A[t][n] = a[r * n + t];
+    host_fft_pow2(A[t]);
   }
   for (size_t k = 0; k < Mp; ++k)
-    for (int u = 0; u < 3; ++u) {
+    for (int u = 0; u < r; ++u) {
       const int64_t kk = (int64_t)(k + Mp * u);
-      a[kk] = A[0][k] + expi_turns(-kk, (int64_t)M) * A[1][k] + expi_turns(-2 * kk, (int64_t)M) * A[2][k];
+      cd x = A[0][k];
+      for (int t = 1; t < r; ++t) x += expi_turns(-(int64_t)t * kk, (int64_t)M) * A[t][k];
+      a[kk] = x;
     }
 }
 

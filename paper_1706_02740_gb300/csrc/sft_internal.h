@@ -44,7 +44,7 @@ struct DevPlan {
   int32_t prec, input;
   int64_t m;                  // distinct nodes: nsub * sum_j p_j
   int32_t Ptot;               // sum_j p_j
-  int32_t fftM, fftLog2;      // chirp convolution length (2^k or 3 2^k), floor(log2 fftM)
+  int32_t fftM, fftLog2;      // chirp convolution length (r 2^k, r = 1, 3, 5, 7), floor(log2 fftM)
   int32_t p[kMaxK];
   int64_t nodeoff[kMaxK + 1]; // first node of prime j
   int32_t poff[kMaxK + 1];    // first bin of prime j
@@ -165,7 +165,9 @@ enum StageKind {
   kStFinalRank,      // rank fallback of the final order
   kStBluestein0,     // + log2(M) - 6: one per power-of-two chirp-convolution length 64..16384
   kStBluestein3 = kStBluestein0 + 9,   // + log2(M / 96): lengths M = 3 2^k, 96..12288
-  kStCount = kStBluestein3 + 8
+  kStBluestein5 = kStBluestein3 + 8,   // + log2(M / 640): lengths M = 5 2^k, 640..10240
+  kStBluestein7 = kStBluestein5 + 5,   // + log2(M / 896): lengths M = 7 2^k, 896..14336
+  kStCount = kStBluestein7 + 5
 };
 
 // Host-side description of one execution's launches: total blocks of each stage and the device
@@ -182,23 +184,37 @@ struct LaunchSet {
 sft_tuning default_tuning();
 bool tuning_valid(const sft_tuning& t, std::string* why);
 
-// The chirp convolution's FFT length M is a power of two 2^k or three times one, 3 2^k, the
-// smallest of these >= 2p - 1 (fft_length); threads per transform fft_tpt(M) = M/16 or M/12.
-// After the radix-2 first pass (no twiddles) the passes run at sub-transform lengths
-// SPAN = 2, 2 R_1, ... with radix R = fft_radix(M, SPAN) until SPAN = M: radix 16 while at least
-// 16 (or 48 when a factor 3 remains) is left, then the rest: 2, 4 or 8, or 3, 6 or 12 (24 left
-// is taken as 12, then 2).  The pass at SPAN owns fft_tw_rows(R) rows of SPAN entries: row t,
-// column k holds e^{-2 pi i e_t k / (SPAN R)} with exponents e_t = 1, 2, 3, 4, 8, 12 (those below
-// R); every power r = 4a + c < R is then one product (w^4)^a w^c of two entries.  The rows of all
-// passes are stored one after the other (fft_tw_offset); together they hold fewer than M entries.
-__host__ __device__ constexpr int fft_radix(int M, int span) {
-  return (M / span) % 3 != 0 ? ((M / span) >= 16 ? 16 : (M / span))
-         : (M / span) % 48 == 0 ? 16 : (M / span) == 24 ? 12 : (M / span);
+// The chirp convolution's FFT length M is r 2^k with r in {1, 3, 5, 7}: the smallest such length
+// >= 2p - 1 (fft_length).  After the radix-2 first pass (no twiddles) the passes run at
+// sub-transform lengths SPAN = 2, 2 R_1, ... with radix R = fft_radix(M, SPAN) until SPAN = M:
+// radix 16 while at least 16 r is left, then the largest r 2^j <= 16 that divides what is left
+// (r = 3: 3, 6, 12; r = 5: 5, 10; r = 7: 7, 14; r = 1: 2, 4, 8), then a last radix 2 or 4 where
+// M needs it.  Threads per transform fft_tpt(M) = M / R_r, R_r the largest r 2^j <= 16 (16, 12,
+// 10 or 14), so no pass holds more than 16 values per thread.  The pass at SPAN owns
+// fft_tw_rows(R) rows of SPAN entries: row t, column k holds e^{-2 pi i e_t k / (SPAN R)} with
+// exponents e_t = 1, 2, 3, 4, 8, 12 (those below R); every power r' = 4a + c < R is then one
+// product (w^4)^a w^c of two entries.  The rows of all passes are stored one after the other
+// (fft_tw_offset); together they hold fewer than M entries.
+__host__ __device__ constexpr int fft_odd(int M) {
+  return M % 7 == 0 ? 7 : M % 5 == 0 ? 5 : M % 3 == 0 ? 3 : 1;
 }
-__host__ __device__ constexpr int fft_tpt(int M) { return M % 3 == 0 ? M / 12 : M / 16; }
+__host__ __device__ constexpr int fft_odd_radix(int r) {   // the largest r 2^j <= 16
+  int R = r;
+  while (2 * R <= 16) R *= 2;
+  return R;
+}
+__host__ __device__ constexpr int fft_radix(int M, int span) {
+  const int rem = M / span, r = fft_odd(M);
+  if (r == 1 || rem % r != 0) return rem >= 16 ? 16 : rem;
+  if (rem % (16 * r) == 0) return 16;
+  int R = r;
+  while (2 * R <= 16 && rem % (2 * R) == 0) R *= 2;
+  return R;
+}
+__host__ __device__ constexpr int fft_tpt(int M) { return M / fft_odd_radix(fft_odd(M)); }
 __host__ __device__ constexpr int fft_log2(int x) { return x <= 1 ? 0 : 1 + fft_log2(x / 2); }
 __host__ __device__ constexpr int fft_tw_rows(int R) {
-  return R >= 16 ? 6 : R == 12 ? 5 : (R == 8 || R == 6) ? 4 : R == 4 ? 3 : R == 3 ? 2 : 1;
+  return R >= 13 ? 6 : R >= 9 ? 5 : R >= 5 ? 4 : R == 4 ? 3 : R == 3 ? 2 : 1;
 }
 __host__ __device__ constexpr int fft_tw_exp(int t) { return t < 3 ? t + 1 : 4 * (t - 2); }
 __host__ __device__ constexpr int fft_tw_offset(int M, int span) {
@@ -207,26 +223,35 @@ __host__ __device__ constexpr int fft_tw_offset(int M, int span) {
   return off;
 }
 __host__ __device__ constexpr int fft_tw_entries(int M) { return fft_tw_offset(M, M); }
-// The smallest admissible length >= n (0 if none is <= maxM): 2^k >= 64 or 3 2^k >= 96.
+// The smallest admissible length >= n (0 if none is <= maxM): 2^k >= 64, 3 2^k >= 96,
+// 5 2^k >= 640 or 7 2^k >= 896.
 inline int fft_length(int64_t n, int maxM) {
   int64_t best = 0;
-  for (int64_t m = 64; m <= maxM; m <<= 1)
-    if (m >= n) { best = m; break; }
-  for (int64_t m = 96; m <= maxM; m <<= 1)
-    if (m >= n && (best == 0 || m < best)) { best = m; break; }
+  for (int64_t base : {64, 96, 640, 896})
+    for (int64_t m = base; m <= maxM; m <<= 1)
+      if (m >= n) {
+        if (best == 0 || m < best) best = m;
+        break;
+      }
   return (int)best;
 }
-// Launch class of a length: kStBluestein0 + log2(M) - 6 or kStBluestein3 + log2(M / 96), and the
-// entry of sft_tuning::dft_per_cta it takes (that of the power-of-two length with the same
-// threads per transform: 3 2^k shares with 2^(k+2)).
+// Launch class of a length (one stage kind per length), and the entry of sft_tuning::dft_per_cta
+// it takes: that of the power-of-two length with the same threads per transform.
 inline int fft_stage(int M) {
-  return M % 3 == 0 ? kStBluestein3 + fft_log2(M / 96) : kStBluestein0 + fft_log2(M) - 6;
+  switch (fft_odd(M)) {
+    case 3: return kStBluestein3 + fft_log2(M / 96);
+    case 5: return kStBluestein5 + fft_log2(M / 640);
+    case 7: return kStBluestein7 + fft_log2(M / 896);
+    default: return kStBluestein0 + fft_log2(M) - 6;
+  }
 }
-inline int fft_tune_class(int M) { return M % 3 == 0 ? fft_log2(M / 96) + 1 : fft_log2(M) - 6; }
+inline int fft_tune_class(int M) { return fft_log2(fft_tpt(M)) - 2; }
 inline int fft_stage_length(int kind) {
-  return kind >= kStBluestein3 ? 96 << (kind - kStBluestein3) : 64 << (kind - kStBluestein0);
+  if (kind >= kStBluestein7) return 896 << (kind - kStBluestein7);
+  if (kind >= kStBluestein5) return 640 << (kind - kStBluestein5);
+  if (kind >= kStBluestein3) return 96 << (kind - kStBluestein3);
+  return 64 << (kind - kStBluestein0);
 }
-
 int bluestein_blocks(const DevPlan& d, int M, int per_cta);   // chirp-convolution blocks of one signal
 int rank_blocks(const DevPlan& d, int kind);     // blocks of the rank fallbacks (0 when not needed)
 

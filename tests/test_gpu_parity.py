@@ -97,16 +97,22 @@ def test_stages_and_output_match_oracle(case, prec):
     assert np.all(g["freqs"][n:] == 0) and np.all(g["coefs"][n:] == 0)
 
 
-# Chirp-convolution lengths 3 2^k: last passes of radix 3, 6, 12, and 12 then 2; the largest prime
-# of each plan is the largest below M/2 (the edge of the skipped first radix-2 pass).
-LENGTHS_3 = [(96, [37, 41, 47]), (192, [67, 89]), (384, [131, 191]), (768, [257, 383]),
-             (1536, [521, 761]), (3072, [1031, 1531]), (6144, [2053, 3067]), (12288, [4099, 6143])]
+# Chirp-convolution lengths r 2^k, r = 3, 5, 7: last passes of radix 3, 6, 12 (12 then 2), 5, 10
+# (10 then 2 or 4), 7, 14 (14 then 2 or 4); the largest prime of each plan is the largest below
+# M/2 (the edge of the skipped first radix-2 pass), the smallest just above the next shorter length.
+LENGTHS_ODD = [(96, [37, 41, 47]), (192, [67, 89]), (384, [131, 191]), (768, [257, 383]),
+               (1536, [521, 761]), (3072, [1031, 1531]), (6144, [2053, 3067]),
+               (12288, [4099, 6143]),
+               (640, [257, 317]), (1280, [521, 631]), (2560, [1031, 1279]), (5120, [2053, 2557]),
+               (10240, [4099, 5119]),
+               (896, [389, 443]), (1792, [769, 887]), (3584, [1543, 1789]), (7168, [3079, 3583]),
+               (14336, [6151, 7159])]
 
 
 @pytest.mark.parametrize("prec", [U.FP32, U.FP64])
-@pytest.mark.parametrize("M,primes", LENGTHS_3)
-def test_three_times_power_of_two_lengths_match_oracle(M, primes, prec):
-    if prec == U.FP64 and M > 6144:
+@pytest.mark.parametrize("M,primes", LENGTHS_ODD)
+def test_mixed_radix_lengths_match_oracle(M, primes, prec):
+    if prec == U.FP64 and M > 8192:
         pytest.skip("FP64 chirp convolutions stop at length 8192")
     N, s = 2 ** 14, 4
     sig = make_signal(N, s, M, "unit", 30.0)
