@@ -16,6 +16,10 @@
  *  - Every pointer argument named *_dev is a CUDA device pointer on the current device; every
  *    other pointer is host memory.  The caller owns all buffers it passes; the plan owns its own
  *    device tables and scratch and frees them in sft_plan_destroy.
+ *  - An input signal (f_dev, f_devs[i]) may also be page-locked host memory that the device can
+ *    address (cudaHostAlloc / cudaMallocHost under unified addressing): the transform reads only
+ *    the 2 kappa + 1 samples around each node, so it then fetches those windows over the
+ *    CPU-GPU link instead of the whole signal being copied first.  Results are the same bits.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Execution entry
  *    points only enqueue work and return; results are valid after the stream is synchronised.
  *  - No entry point throws or aborts.  Each returns an sft_status; on failure the plan is left

@@ -400,11 +400,13 @@ def _batch_ptrs(fs, outs):
 
 
 def execute_batch_torch(batch: Batch, fs, stream=None, outs=None):
-    """Run a batch on CUDA tensors fs (one per plan); returns lists of device result tensors."""
+    """Run a batch on tensors fs (one per plan; CUDA, or pinned host memory); returns lists of
+    device result tensors."""
     import torch
+    dev = _cuda_device_of(fs[0])
     if outs is None:
-        outs = batch_outputs_torch(batch, fs[0].device)
-    st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
+        outs = batch_outputs_torch(batch, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
     batch.execute(*_batch_ptrs(fs, outs), st.cuda_stream)
     return outs
 
@@ -509,13 +511,25 @@ def sft_plan_debug_buffer(plan: Plan, which: int):
 # ---------------------------------------------------------------------------------------------
 # torch conveniences (allocation of outputs, pointers, current stream)
 # ---------------------------------------------------------------------------------------------
+def _cuda_device_of(f):
+    """The CUDA device a transform of tensor f runs on: f's own, or the current one when f is a
+    page-locked host tensor (which the device then reads over the host link)."""
+    import torch
+    if f.is_cuda:
+        return f.device
+    if not f.is_pinned():
+        raise SftError("a host input must be page-locked (pinned) memory")
+    return torch.device("cuda", torch.cuda.current_device())
+
+
 def execute_torch(plan: Plan, f, stream=None):
-    """Run sft_execute on a CUDA tensor f (complex64 or complex128); returns device tensors
-    (freqs int64 [s], coefs complex128 [s], count int32 [1]) on the same stream."""
+    """Run sft_execute on a tensor f (complex64 or complex128; CUDA, or pinned host memory);
+    returns device tensors (freqs int64 [s], coefs complex128 [s], count int32 [1]) on the same
+    stream."""
     import torch
     info = sft_plan_info(plan)
     s = info["s"]
-    dev = f.device
+    dev = _cuda_device_of(f)
     freqs = torch.empty(s, dtype=torch.int64, device=dev)
     coefs = torch.empty(s, dtype=torch.complex128, device=dev)
     count = torch.empty(1, dtype=torch.int32, device=dev)
