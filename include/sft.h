@@ -209,9 +209,10 @@ sft_status sft_batch_destroy(sft_batch_t batch);
  *                     more warps in flight for the gather; needs resample_threads <= 256);
  *                     0: the default build (64 registers on the FP32 path).
  *   bin_threads       bins per CTA of residue identification and vote: 64, 128, 256 or 512.
- *   dft_per_cta[c]    chirp-convolution transforms per CTA for the length class M = 64 << c
- *                     (c = 0..8); M/16 threads per transform and at most max(M/16, 256) threads
- *                     per CTA, so 1 <= dft_per_cta[c] <= max(1, 4096 / M).
+ *   dft_per_cta[c]    chirp-convolution transforms per CTA for the lengths with 4 << c threads
+ *                     per transform (c = 0..8): the power of two M = 64 << c, and 3 << (c + 4),
+ *                     5 << (c + 3), 7 << (c + 3) where the plan's primes choose those; at most
+ *                     max(M/16, 256) threads per CTA, so 1 <= dft_per_cta[c] <= max(1, 4096 / M).
  *   dft_two_ctas      FP32, M = 8192: 1 = the build limited to 64 registers so that two CTAs share
  *                     an SM; 0 = one CTA per SM with up to 128 registers.
  * sft_tuning_default fills the built-in choice (host only, no device call).

@@ -381,6 +381,7 @@ sft_status sft_batch_autotune(sft_batch_t batch, const void* const* f_devs,
     s = try_knob(best, cands, 0, 0);
   }
   // chirp convolution: transforms per CTA of every length class present, then the FP32 8192 build
+  // (one or two CTAs per SM)
   for (int c = 0; c < 9 && s == SFT_OK; ++c) {
     // the lengths with as many threads per transform as 2^(c+6) (2^k and r 2^k share an entry)
     bool present = false;

@@ -410,8 +410,8 @@ __device__ __forceinline__ void radix2_first(C* s, int lt) {
 }
 
 // A CTA holds blockDim.x / fft_tpt(M) transforms, at most max(fft_tpt(M), 256) threads.  MINB is
-// the builds' CTAs-per-SM target: FP32 transforms are limited to 64 (M = 6144 or 8192, MINB = 2)
-// or 128 (M <= 4096) registers.
+// the builds' CTAs-per-SM target: FP32 transforms of 512 threads (M = 5120 .. 8192, MINB = 2) are
+// limited to 64 registers, those of at most 256 threads (M <= 4096) to 128.
 template <int M> constexpr int dft_max_threads() { return fft_tpt(M) > 256 ? fft_tpt(M) : 256; }
 
 template <typename R, int M, int MINB>

@@ -163,7 +163,7 @@ enum StageKind {
   kStReest,          // shifts * K * chunks
   kStRefine,         // s / 64
   kStFinalRank,      // rank fallback of the final order
-  kStBluestein0,     // + log2(M) - 6: one per power-of-two chirp-convolution length 64..16384
+  kStBluestein0,     // + log2(M) - 6: chirp-convolution lengths 2^k, 64..16384
   kStBluestein3 = kStBluestein0 + 9,   // + log2(M / 96): lengths M = 3 2^k, 96..12288
   kStBluestein5 = kStBluestein3 + 8,   // + log2(M / 640): lengths M = 5 2^k, 640..10240
   kStBluestein7 = kStBluestein5 + 5,   // + log2(M / 896): lengths M = 7 2^k, 896..14336
