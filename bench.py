@@ -230,16 +230,16 @@ def source_digest(*names):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_tag, digest):
-    """Per-SFT DRAM bytes from the committed ncu summary of this kernel, if it was taken on the
-    current source (else None)."""
+def profiled_traffic(kernel_tag, digest, key="dram_bytes_per_sft"):
+    """A per-SFT counter (DRAM bytes by default) from the committed ncu summary of this kernel, if
+    it was taken on the current source (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m_src = re.search(r"source_digest:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"dram_bytes_per_sft:\s*([0-9.eE+]+)", text)
+    m_tr = re.search(key + r":\s*([0-9.eE+]+)", text)
     if not (m_src and m_tr) or m_src.group(1) != digest:
         return None
     return float(m_tr.group(1))
@@ -416,6 +416,17 @@ def run_ours(args, rank, world, local_rank):
                 "units": f"{B} SFTs x {info['n_shifts'] * info['n_sub'] * info['K']} transforms "
                          f"of length {info['fft_size']} per launch",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+        # the pipe that actually limits it: shared-memory wavefronts (ncu count per SFT of the
+        # same source, x B) per second against one 128-byte wavefront per SM per clock
+        wav = profiled_traffic("bluestein_n2p26_s1000",
+                               source_digest("bluestein.cu", "cplx.cuh", "sft_internal.h"),
+                               key="smem_wavefronts_per_sft")
+        if wav is not None:
+            wps = B * wav / (per_launch_us["chirp_dft"] * 1e-6)
+            peak_w = 152 * sm_mhz * 1e6
+            roof["smem"] = {"achieved_wavefronts_per_s": wps, "peak_wavefronts_per_s": peak_w,
+                            "frac": wps / peak_w,
+                            "source": "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum per SFT"}
     else:
         roof = dict(roof_gather)
 
