@@ -106,7 +106,10 @@ LENGTHS_ODD = [(96, [37, 41, 47]), (192, [67, 89]), (384, [131, 191]), (768, [25
                (640, [257, 317]), (1280, [521, 631]), (2560, [1031, 1279]), (5120, [2053, 2557]),
                (10240, [4099, 5119]),
                (896, [389, 443]), (1792, [769, 887]), (3584, [1543, 1789]), (7168, [3079, 3583]),
-               (14336, [6151, 7159])]
+               (14336, [6151, 7159]),
+               # the longest power-of-two lengths of each path, primes up to the limits (p <= 4096
+               # FP64, p <= 8192 FP32)
+               (8192, [3593, 4093]), (16384, [7177, 8191])]
 
 
 @pytest.mark.parametrize("prec", [U.FP32, U.FP64])
