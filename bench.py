@@ -324,12 +324,12 @@ def run_ours(args, rank, world, local_rank):
 
     def single_latency(graph):
         sft.sft_plan_graph(p0, graph)
-        for i in range(0 if args.timed_only else 3):
+        for i in range(0 if args.timed_only else 20):
             sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
                             stream.cuda_stream)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(0 if args.timed_only else 64)]
+              for _ in range(0 if args.timed_only else 128)]
         for i, (a, b) in enumerate(ev):
             a.record()
             sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
@@ -584,7 +584,8 @@ def run_ours(args, rank, world, local_rank):
         "config": dict(workload_config(args, B), tuning=tuning, graph=True),
         "latency_ms": {"p50": pct(single, 0.5), "p99": pct(single, 0.99),
                        "direct_launches_p50": pct(single_direct, 0.5),
-                       "what": "device time of one SFT executed alone (sft_execute, plan graph)"},
+                       "what": "device time of one SFT executed alone (sft_execute, plan graph; "
+                               "20 warm-ups, 128 timed, 16 rotating inputs)"},
         "step_ms": {"p50": pct(step_ms, 0.5), "p99": pct(step_ms, 0.99),
                     "what": f"one batched execution of {B} SFTs"},
         "stages_us_per_launch": per_launch_us,
