@@ -417,6 +417,7 @@ template <int M> constexpr int dft_max_threads() { return fft_tpt(M) > 256 ? fft
 template <typename R, int M, int MINB>
 __global__ void __launch_bounds__(dft_max_threads<M>(), MINB)
 bluestein_kernel(BatchView bv) {
+  pdl_begin();
   using C = typename Cx<R>::T;
   constexpr int TPT = fft_tpt(M);                  // threads per transform
   const int G = blockDim.x / TPT;                  // transforms per CTA
@@ -480,7 +481,7 @@ cudaError_t launch_MB(const BatchView& bv, const LaunchSet& ls, cudaStream_t st,
   if (e != cudaSuccess) return e;
   BatchView v = bv;
   v.blk = ls.blk[stage];
-  bluestein_kernel<R, M, MINB><<<grid, threads, smem, st>>>(v);
+  (void)launch_pdl(bluestein_kernel<R, M, MINB>, grid, threads, smem, st, v);
   if (launched) ++*launched;
   return cudaGetLastError();
 }
@@ -577,6 +578,7 @@ int g_noalloc_n[kMaxDevices];           // length the tables currently hold (0 =
 // and the wrapped conjugate chirp V (V[k] = V[M - k] = conj(w_k), zero elsewhere), in FP64 then
 // rounded.
 __global__ void noalloc_tables_kernel(int n, int M, float2* chirp, float2* V, float2* W) {
+  pdl_begin();
   const int entries = fft_tw_entries(M);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
     double s, c;
@@ -611,6 +613,7 @@ __global__ void noalloc_tables_kernel(int n, int M, float2* chirp, float2* V, fl
 // Filter spectrum: FFT_M(V) / (M n), one CTA, the same shared-memory Stockham passes.
 template <int M>
 __global__ void __launch_bounds__(M / 16) noalloc_filter_kernel(int n, float2* V, const float2* W) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s = reinterpret_cast<float2*>(smem_raw);
   constexpr int TPT = M / 16;
@@ -629,12 +632,12 @@ cudaError_t noalloc_build(int n, float2* base, cudaStream_t st) {
   float2* chirp = base;
   float2* V = base + kNoAllocChirp;
   float2* W = V + kNoAllocMaxM;
-  noalloc_tables_kernel<<<(M + 255) / 256, 256, 0, st>>>(n, M, chirp, V, W);
+  (void)launch_pdl(noalloc_tables_kernel, (M + 255) / 256, 256, 0, st, n, M, chirp, V, W);
   const size_t smem = (size_t)padded_len<M>() * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(noalloc_filter_kernel<M>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  noalloc_filter_kernel<M><<<1, M / 16, smem, st>>>(n, V, W);
+  (void)launch_pdl(noalloc_filter_kernel<M>, 1, M / 16, smem, st, n, V, W);
   return cudaGetLastError();
 }
 

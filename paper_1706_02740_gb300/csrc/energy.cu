@@ -48,6 +48,7 @@ __device__ double block_sum(double v) {
 
 __global__ void __launch_bounds__(kEnergyThreads) energy_partial_kernel(const DevPlan* dp,
                                                                        const void* f) {
+  pdl_begin();
   const DevPlan& d = *dp;
   const int64_t N = d.N;
   const int64_t tid = (int64_t)blockIdx.x * kEnergyThreads + threadIdx.x;
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_final_kernel(const DevP
                                                                      const double2* coefs,
                                                                      const int32_t* count,
                                                                      double* out) {
+  pdl_begin();
   const DevPlan& d = *dp;
   double e = threadIdx.x < kEnergyBlocks ? d.epart[threadIdx.x] : 0.0;
   e = block_sum(e);
@@ -128,9 +130,9 @@ extern "C" sft_status sft_residual_energy(sft_plan_t plan, const void* f_dev, co
     return SFT_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  energy_partial_kernel<<<kEnergyBlocks, kEnergyThreads, 0, st>>>(P->d_dev, f_dev);
-  energy_final_kernel<<<1, kEnergyThreads, 0, st>>>(P->d_dev, static_cast<const double2*>(coefs_dev),
-                                                   count_dev, out_dev);
+  (void)launch_pdl(energy_partial_kernel, kEnergyBlocks, kEnergyThreads, 0, st, P->d_dev, f_dev);
+  (void)launch_pdl(energy_final_kernel, 1, kEnergyThreads, 0, st, P->d_dev,
+                   static_cast<const double2*>(coefs_dev), count_dev, out_dev);
   P->launches += 2;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

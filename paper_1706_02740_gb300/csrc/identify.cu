@@ -153,6 +153,7 @@ __device__ int residue_any(int t, C z0, const C* Zl, int64_t p, const C* twl, in
 // its sub-bin loads, so more warps in flight help); the FP64 build would spill there.
 template <typename R>
 __global__ void __launch_bounds__(kBinMaxThreads, sizeof(R) == 4 ? 2 : 1) identify_kernel(BatchView bv) {
+  pdl_begin();
   using C = typename Cx<R>::T;
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(kBinMaxThreads, sizeof(R) == 4 ? 2 : 1) identi
 // KCAP: capacity of the per-thread arrays (kFewK in registers, or kMaxK for many primes).
 template <typename R, int KCAP>
 __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
+  pdl_begin();
   using C = typename Cx<R>::T;
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
@@ -242,8 +244,10 @@ cudaError_t launch_identify(const DevPlan& d0, const BatchView& bv, const Launch
   if (grid == 0) return cudaSuccess;
   BatchView v = bv;
   v.blk = ls.blk[kStBins];
-  if (d0.prec == SFT_FP32) identify_kernel<float><<<grid, ls.tune.bin_threads, 0, st>>>(v);
-  else identify_kernel<double><<<grid, ls.tune.bin_threads, 0, st>>>(v);
+  if (d0.prec == SFT_FP32)
+    (void)launch_pdl(identify_kernel<float>, grid, ls.tune.bin_threads, 0, st, v);
+  else
+    (void)launch_pdl(identify_kernel<double>, grid, ls.tune.bin_threads, 0, st, v);
   return cudaGetLastError();
 }
 
@@ -256,11 +260,11 @@ cudaError_t launch_vote(const DevPlan& d0, const BatchView& bv, const LaunchSet&
   const int t = ls.tune.bin_threads;
   const bool few = ls.kmax <= kFewK;
   if (d0.prec == SFT_FP32) {
-    if (few) vote_kernel<float, kFewK><<<grid, t, 0, st>>>(v);
-    else vote_kernel<float, kMaxK><<<grid, t, 0, st>>>(v);
+    if (few) (void)launch_pdl(vote_kernel<float, kFewK>, grid, t, 0, st, v);
+    else (void)launch_pdl(vote_kernel<float, kMaxK>, grid, t, 0, st, v);
   } else {
-    if (few) vote_kernel<double, kFewK><<<grid, t, 0, st>>>(v);
-    else vote_kernel<double, kMaxK><<<grid, t, 0, st>>>(v);
+    if (few) (void)launch_pdl(vote_kernel<double, kFewK>, grid, t, 0, st, v);
+    else (void)launch_pdl(vote_kernel<double, kMaxK>, grid, t, 0, st, v);
   }
   return cudaGetLastError();
 }

@@ -49,6 +49,7 @@ __device__ __forceinline__ int mod_p32(int64_t w, int p) {
 
 // Winner indices grouped by shift (one CTA per signal), for the re-estimation CTAs.
 __global__ void __launch_bounds__(256) group_winners_kernel(BatchView bv) {
+  pdl_begin();
   __shared__ int cnt[kMaxQ], cur[kMaxQ];
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(256) group_winners_kernel(BatchView bv) {
 }
 
 __global__ void __launch_bounds__(kReThreads) reestimate_kernel(BatchView bv) {
+  pdl_begin();
   // [kReChunk] samples of this chunk, then the prime's [p] twiddles: each thread walks its own
   // residue sequence (k b) mod p, so the table reads scatter across the warp; shared memory serves
   // them with a few bank conflicts where the cached global table would take one line per lane.
@@ -167,6 +169,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // KCAP: capacity of the per-thread arrays (kFewK in registers, or kMaxK for many primes).
 template <int KCAP>
 __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView bv) {
+  pdl_begin();
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int n = d.counters[d.nq + 2];
@@ -218,15 +221,17 @@ __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView
 cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t st) {
   BatchView v = bv;
   v.blk = ls.blk[kStOne];
-  group_winners_kernel<<<ls.blocks[kStOne], 256, 0, st>>>(v);
+  (void)launch_pdl(group_winners_kernel, ls.blocks[kStOne], 256, 0, st, v);
   v.blk = ls.blk[kStReest];
   const size_t smem = (size_t)(kReChunk + ls.pmax) * sizeof(float2);
   const cudaError_t e = ensure_dynamic_smem<reestimate_kernel>(smem);
   if (e != cudaSuccess) return e;
-  reestimate_kernel<<<ls.blocks[kStReest], kReThreads, smem, st>>>(v);
+  (void)launch_pdl(reestimate_kernel, ls.blocks[kStReest], kReThreads, smem, st, v);
   v.blk = ls.blk[kStRefine];
-  if (ls.kmax <= kFewK) refine_values_kernel<kFewK><<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
-  else refine_values_kernel<kMaxK><<<ls.blocks[kStRefine], kRefineThreads, 0, st>>>(v);
+  if (ls.kmax <= kFewK)
+    (void)launch_pdl(refine_values_kernel<kFewK>, ls.blocks[kStRefine], kRefineThreads, 0, st, v);
+  else
+    (void)launch_pdl(refine_values_kernel<kMaxK>, ls.blocks[kStRefine], kRefineThreads, 0, st, v);
   return cudaGetLastError();
 }
 

@@ -158,6 +158,7 @@ __device__ __forceinline__ void fetch_window(const DevPlan& d, const IN* f, int6
 template <int KAPPA, typename R, typename IN, int CAP>
 __global__ void __launch_bounds__(CAP ? 256 : kResampleMaxThreads, CAP ? 5 : (sizeof(R) == 4 ? 2 : 1))
 resample_kernel(BatchView bv) {
+  pdl_begin();
   using C = typename Cx<R>::T;
   constexpr int W = 2 * KAPPA + 1;
   int lb, nb;
@@ -198,6 +199,7 @@ resample_kernel(BatchView bv) {
 // Any window half-width up to kMaxKappa (theorem-parameter mode): scalar loads, runtime loops.
 template <typename R, typename IN>
 __global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_generic(BatchView bv) {
+  pdl_begin();
   using C = typename Cx<R>::T;
   int lb, nb;
   const int b = batch_signal(bv, lb, nb);
@@ -237,13 +239,13 @@ cudaError_t launch_typed(const DevPlan& d0, const BatchView& bv, const LaunchSet
   const int t = ls.tune.resample_threads;
   const bool cap = ls.tune.resample_regcap != 0;
   if (d0.kappa == 6) {
-    if (cap) resample_kernel<6, R, IN, 1><<<grid, t, 0, st>>>(v);
-    else resample_kernel<6, R, IN, 0><<<grid, t, 0, st>>>(v);
+    if (cap) (void)launch_pdl(resample_kernel<6, R, IN, 1>, grid, t, 0, st, v);
+    else (void)launch_pdl(resample_kernel<6, R, IN, 0>, grid, t, 0, st, v);
   } else if (d0.kappa == 4) {
-    if (cap) resample_kernel<4, R, IN, 1><<<grid, t, 0, st>>>(v);
-    else resample_kernel<4, R, IN, 0><<<grid, t, 0, st>>>(v);
+    if (cap) (void)launch_pdl(resample_kernel<4, R, IN, 1>, grid, t, 0, st, v);
+    else (void)launch_pdl(resample_kernel<4, R, IN, 0>, grid, t, 0, st, v);
   } else {
-    resample_kernel_generic<R, IN><<<grid, kResampleGenericThreads, 0, st>>>(v);
+    (void)launch_pdl(resample_kernel_generic<R, IN>, grid, kResampleGenericThreads, 0, st, v);
   }
   return cudaGetLastError();
 }

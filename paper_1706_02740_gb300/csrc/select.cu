@@ -58,6 +58,7 @@ __device__ __forceinline__ uint64_t pkey(const Pooled& p) {
 }
 
 __global__ void __launch_bounds__(kSortThreads) shift_select(BatchView bv) {
+  pdl_begin();
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   const int qi = lb;
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(kSortThreads) shift_select(BatchView bv) {
 }
 
 __global__ void __launch_bounds__(kRankThreads) shift_select_rank(BatchView bv) {
+  pdl_begin();
   __shared__ uint64_t sm[kRankThreads];
   __shared__ int64_t sw[kRankThreads];
   int lb, nb;
@@ -132,6 +134,7 @@ __device__ __forceinline__ void set_count(const DevPlan& d, int n, int32_t* out_
 }
 
 __global__ void __launch_bounds__(kSortThreads) global_select(BatchView bv) {
+  pdl_begin();
   int lb, nb;
   const int b = batch_signal(bv, lb, nb);
   const DevPlan& d = bv.plans[b];
@@ -164,6 +167,7 @@ __global__ void __launch_bounds__(kSortThreads) global_select(BatchView bv) {
 }
 
 __global__ void __launch_bounds__(kRankThreads) global_select_rank(BatchView bv) {
+  pdl_begin();
   __shared__ uint64_t sm[kRankThreads];
   __shared__ int64_t sw[kRankThreads];
   int lb, nb;
@@ -200,6 +204,7 @@ __global__ void __launch_bounds__(kRankThreads) global_select_rank(BatchView bv)
 }
 
 __global__ void __launch_bounds__(kSortThreads) finalize_sorted(BatchView bv) {
+  pdl_begin();
   int lb, nb;
   const int b = batch_signal(bv, lb, nb);
   const DevPlan& d = bv.plans[b];
@@ -235,6 +240,7 @@ __global__ void __launch_bounds__(kSortThreads) finalize_sorted(BatchView bv) {
 }
 
 __global__ void __launch_bounds__(kRankThreads) finalize_rank(BatchView bv) {
+  pdl_begin();
   __shared__ uint64_t sm[kRankThreads];
   __shared__ int64_t sw[kRankThreads];
   int lb, nb;
@@ -280,6 +286,7 @@ __global__ void __launch_bounds__(kRankThreads) finalize_rank(BatchView bv) {
 
 // Per-signal counters (voted counts, pool count, winner count) start at zero.
 __global__ void __launch_bounds__(64) zero_kernel(BatchView bv) {
+  pdl_begin();
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
   for (int i = threadIdx.x; i < d.nq + 4; i += 64) d.counters[i] = 0;
@@ -299,7 +306,7 @@ BatchView with_blk(const BatchView& bv, const LaunchSet& ls, int kind) {
 }  // namespace
 
 cudaError_t launch_zero(const BatchView& bv, const LaunchSet& ls, cudaStream_t st) {
-  zero_kernel<<<ls.blocks[kStOne], 64, 0, st>>>(with_blk(bv, ls, kStOne));
+  (void)launch_pdl(zero_kernel, ls.blocks[kStOne], 64, 0, st, with_blk(bv, ls, kStOne));
   return cudaGetLastError();
 }
 
@@ -307,17 +314,19 @@ cudaError_t launch_select(const BatchView& bv, const LaunchSet& ls, cudaStream_t
   cudaError_t e = ensure_dynamic_smem<shift_select>(kSortSmem);
   if (e == cudaSuccess) e = ensure_dynamic_smem<global_select>(kSortSmem);
   if (e != cudaSuccess) return e;
-  shift_select<<<ls.blocks[kStShift], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStShift));
+  (void)launch_pdl(shift_select, ls.blocks[kStShift], kSortThreads, kSortSmem, st,
+                   with_blk(bv, ls, kStShift));
   ++*launched;
   if (ls.blocks[kStShiftRank] > 0) {
-    shift_select_rank<<<ls.blocks[kStShiftRank], kRankThreads, 0, st>>>(
+    (void)launch_pdl(shift_select_rank, ls.blocks[kStShiftRank], kRankThreads, 0, st,
         with_blk(bv, ls, kStShiftRank));
     ++*launched;
   }
-  global_select<<<ls.blocks[kStOne], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStOne));
+  (void)launch_pdl(global_select, ls.blocks[kStOne], kSortThreads, kSortSmem, st,
+                   with_blk(bv, ls, kStOne));
   ++*launched;
   if (ls.blocks[kStGlobalRank] > 0) {
-    global_select_rank<<<ls.blocks[kStGlobalRank], kRankThreads, 0, st>>>(
+    (void)launch_pdl(global_select_rank, ls.blocks[kStGlobalRank], kRankThreads, 0, st,
         with_blk(bv, ls, kStGlobalRank));
     ++*launched;
   }
@@ -328,10 +337,12 @@ cudaError_t launch_finalize(const BatchView& bv, const LaunchSet& ls, cudaStream
                             int* launched) {
   cudaError_t e = ensure_dynamic_smem<finalize_sorted>(kSortSmem);
   if (e != cudaSuccess) return e;
-  finalize_sorted<<<ls.blocks[kStOne], kSortThreads, kSortSmem, st>>>(with_blk(bv, ls, kStOne));
+  (void)launch_pdl(finalize_sorted, ls.blocks[kStOne], kSortThreads, kSortSmem, st,
+                   with_blk(bv, ls, kStOne));
   ++*launched;
   if (ls.blocks[kStFinalRank] > 0) {
-    finalize_rank<<<ls.blocks[kStFinalRank], kRankThreads, 0, st>>>(with_blk(bv, ls, kStFinalRank));
+    (void)launch_pdl(finalize_rank, ls.blocks[kStFinalRank], kRankThreads, 0, st,
+                     with_blk(bv, ls, kStFinalRank));
     ++*launched;
   }
   return cudaGetLastError();

@@ -252,6 +252,40 @@ inline int fft_stage_length(int kind) {
   if (kind >= kStBluestein3) return 96 << (kind - kStBluestein3);
   return 64 << (kind - kStBluestein0);
 }
+// Programmatic dependent launch.  Every kernel of the library begins with pdl_begin(): it waits
+// until the kernel before it on the stream has completed and its writes are visible, then lets the
+// kernel after it be scheduled.  launch_pdl allows that overlap on streams that are not being
+// captured, so the next kernel's blocks are set up while this one's last blocks run (the wait
+// keeps every data dependence): one SFT through direct launches took 0.171 instead of 0.191 ms.
+// Launches captured into a CUDA graph are plain (the graph already closes the launch gaps; with
+// programmatic edges it measured 0.180 instead of 0.176 ms); pdl_begin() is then a no-op.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();           // (a refused query must not read as a launch failure)
+    cap = cudaStreamCaptureStatusActive;
+  }
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 int bluestein_blocks(const DevPlan& d, int M, int per_cta);   // chirp-convolution blocks of one signal
 int rank_blocks(const DevPlan& d, int kind);     // blocks of the rank fallbacks (0 when not needed)
 
