@@ -201,6 +201,16 @@ sft_status sft_batch_execute(sft_batch_t batch, const void* const* f_devs,
 sft_status sft_batch_destroy(sft_batch_t batch);
 
 /*
+ * One-shot form of the three calls above: a batch of plans[0..n) is built, executed on `stream`
+ * with the same arguments as sft_batch_execute, waited for, and its own device arrays are freed
+ * before the call returns (so, unlike the others, this call blocks the calling thread until the
+ * transforms are complete).  For repeated executions of the same plans create the batch once.
+ */
+sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
+                             int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
+                             int32_t* const* out_count_devs, int32_t n, void* stream);
+
+/*
  * Launch geometry of a batch's kernels.  It changes how work is split into CTAs, never what is
  * computed: every valid choice gives the same results, bit for bit.
  *   resample_threads  nodes per CTA of the kappa = 4 / 6 resampling kernel: 64, 128, 256 or 512
@@ -395,6 +405,11 @@ sft_status sft_server_query(sft_server_t server, sft_request_t id, sft_request_i
  * for an unknown handle.  A done request's results are complete in device memory and visible to
  * every stream. */
 sft_status sft_server_wait(sft_server_t server, sft_request_t id, int32_t timeout_ms);
+
+/* Non-blocking completion test: *done = 1 once the request has finished, else 0.  Returns SFT_OK
+ * while it is pending or when it is done, the request's own failure status when it failed, and
+ * SFT_EINVAL for an unknown handle or a NULL argument. */
+sft_status sft_server_poll(sft_server_t server, sft_request_t id, int32_t* done);
 
 /* Forget a finished request's record (SFT_EBUSY while it is queued or running). */
 sft_status sft_server_release(sft_server_t server, sft_request_t id);

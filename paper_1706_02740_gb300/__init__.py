@@ -123,6 +123,8 @@ EXPORTS = {
     "sft_batch_execute": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_void_p)] * 4
                           + [ctypes.c_void_p]),
     "sft_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sft_execute_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)] * 5
+                          + [ctypes.c_int32, ctypes.c_void_p]),
     "sft_batch_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "sft_batch_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int32)]),
@@ -142,6 +144,8 @@ EXPORTS = {
     "sft_server_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.POINTER(sft_request_info)]),
     "sft_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "sft_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int32)]),
     "sft_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "sft_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sft_server_stats)]),
     "sft_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -399,6 +403,14 @@ def _batch_ptrs(fs, outs):
             [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs])
 
 
+def sft_execute_batch(plans, f_ptrs, w_ptrs, c_ptrs, n_ptrs, stream: int = 0):
+    """One-shot batch over plans (blocks until the transforms are complete)."""
+    n = len(plans)
+    arrs = [(ctypes.c_void_p * n)(*[int(x) for x in ptrs])
+            for ptrs in ([p.handle for p in plans], f_ptrs, w_ptrs, c_ptrs, n_ptrs)]
+    _check(load().sft_execute_batch(*arrs, n, stream))
+
+
 def execute_batch_torch(batch: Batch, fs, stream=None, outs=None):
     """Run a batch on tensors fs (one per plan; CUDA, or pinned host memory); returns lists of
     device result tensors."""
@@ -459,6 +471,14 @@ class Server:
         failed).  Raises on timeout or an unknown handle."""
         _check(load().sft_server_wait(self.handle, int(rid), int(timeout_ms)))
         return self.query(rid)["status"]
+
+    def poll(self, rid: int) -> tuple[bool, int]:
+        """Non-blocking: (finished, status); status is SFT_OK unless the request failed."""
+        done = ctypes.c_int32(0)
+        st = load().sft_server_poll(self.handle, int(rid), ctypes.byref(done))
+        if not done.value:
+            _check(st)             # pending (SFT_OK) or an unknown handle (raises)
+        return bool(done.value), int(st)
 
     def release(self, rid: int):
         _check(load().sft_server_release(self.handle, int(rid)))

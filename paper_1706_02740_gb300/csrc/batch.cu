@@ -438,6 +438,22 @@ sft_status sft_batch_destroy(sft_batch_t batch) {
   return SFT_OK;
 }
 
+sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
+                             int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
+                             int32_t* const* out_count_devs, int32_t n, void* stream) {
+  sft_batch_t b = nullptr;
+  sft_status s = sft_batch_create(&b, plans, n);
+  if (s != SFT_OK) return s;
+  s = sft_batch_execute(b, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs, stream);
+  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  sft_batch_destroy(b);
+  if (s == SFT_OK && e != cudaSuccess) {
+    sft::set_error(std::string("sft_execute_batch: ") + cudaGetErrorString(e));
+    return SFT_ECUDA;
+  }
+  return s;
+}
+
 sft_status sft_batch_profile(sft_batch_t batch, int32_t enable) {
   if (!batch) { sft::set_error("batch is NULL"); return SFT_EINVAL; }
   return sft::profile_enable(batch->B.prof, enable);

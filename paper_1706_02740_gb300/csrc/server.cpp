@@ -603,6 +603,16 @@ sft_status sft_server_query(sft_server_t server, sft_request_t id, sft_request_i
   return SFT_OK;
 }
 
+sft_status sft_server_poll(sft_server_t server, sft_request_t id, int32_t* done) {
+  if (!done) { sft::set_error("sft_server_poll: NULL argument"); return SFT_EINVAL; }
+  *done = 0;
+  sft_request_info info;
+  const sft_status s = sft_server_query(server, id, &info);
+  if (s != SFT_OK) return s;
+  *done = info.state >= 2 ? 1 : 0;
+  return info.state == 3 ? (sft_status)info.status : SFT_OK;
+}
+
 sft_status sft_server_wait(sft_server_t server, sft_request_t id, int32_t timeout_ms) {
   using namespace sft;
   if (!server) { set_error("sft_server_wait: NULL server"); return SFT_EINVAL; }

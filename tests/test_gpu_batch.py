@@ -65,6 +65,31 @@ def test_heterogeneous_batch_equals_single_executions(prec):
         p.destroy()
 
 
+def test_one_shot_batch_equals_the_batch_object():
+    """sft_execute_batch (build, run, wait, free in one call) against a resident batch of the same
+    plans: identical bits."""
+    import torch
+    shapes = SHAPES[:4]
+    plans = [sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=6.0, seed=i))
+             for i, (N, s) in enumerate(shapes)]
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in _signals(shapes, 950)]
+    batch = sft.Batch(plans)
+    ref = sft.execute_batch_torch(batch, fs)
+    torch.cuda.synchronize()
+    batch.destroy()
+    outs = [(torch.empty(s, dtype=torch.int64, device="cuda"),
+             torch.empty(s, dtype=torch.complex128, device="cuda"),
+             torch.empty(1, dtype=torch.int32, device="cuda")) for _, s in shapes]
+    sft.sft_execute_batch(plans, [f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs],
+                          [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs],
+                          torch.cuda.current_stream().cuda_stream)
+    for (w, c, n), (rw, rc, rn) in zip(outs, ref):
+        assert int(n.item()) == int(rn.item())
+        assert torch.equal(w, rw) and torch.equal(c, rc)
+    for p in plans:
+        p.destroy()
+
+
 def test_batch_of_identical_shapes_with_rotating_inputs():
     import torch
     N, s, B = 2 ** 18, 50, 6

@@ -202,6 +202,29 @@ def test_bursts_on_concurrent_streams_keep_every_result_exact():
     srv.destroy()
 
 
+def test_poll_reports_pending_then_finished_without_blocking():
+    srv = sft.Server(mem_budget=256 << 20, max_batch=4, max_inflight=1,
+                     variant=sft.sft_variant_init(**VARIANT))
+    shapes = [(2 ** 16, 8)]
+    fs = _inputs(shapes, 2700)
+    outs = _outputs(shapes)
+    rid = _submit(srv, shapes, fs, outs)[0]
+    done, st = srv.poll(rid)
+    assert st == sft.SFT_OK                       # pending or already done, never an error here
+    assert srv.wait(rid, 60000) == sft.SFT_OK
+    assert srv.poll(rid) == (True, sft.SFT_OK)
+    import torch
+    f = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    o = _outputs([(16, 4)])[0]
+    bad = srv.submit(16, 0, f.data_ptr(), o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr())
+    srv.wait(bad, 60000)
+    assert srv.poll(bad) == (True, sft.SFT_EINVAL)     # a failed request: finished, with its reason
+    srv.release(rid)
+    with pytest.raises(sft.SftError):
+        srv.poll(rid)                                   # unknown once released
+    srv.destroy()
+
+
 def test_batches_that_finish_before_the_scheduler_looks_again_are_not_lost():
     """Tiny requests one at a time: each batch can complete (its callback firing) before the
     scheduler retakes its lock after launching; every completion must still be seen."""
