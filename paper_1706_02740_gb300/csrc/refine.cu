@@ -165,47 +165,36 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Refined coefficient of winner r, written back into winners[r].
-// KCAP: capacity of the per-thread arrays (kFewK in registers, or kMaxK for many primes).
-template <int KCAP>
-__global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView bv) {
-  pdl_begin();
-  int lb, nb;
-  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
-  const int n = d.counters[d.nq + 2];
-  const int r = lb * kRefineThreads + threadIdx.x;
-  if (r >= n) return;
-  Pooled pw = d.winners[r];
-  double re[KCAP], im[KCAP];
-  const float4* part = reinterpret_cast<const float4*>(d.ybuf);
-  for (int jj = 0; jj < d.K; ++jj) {
-    const int p = d.p[jj];
-    const int nc = (p + kReChunk - 1) / kReChunk;
-    const float4* pc = part + ((int64_t)r * d.K + jj) * d.nchunk;
-    // double-single accumulation of the chunk partials (hi, lo) for the real and imaginary parts,
-    // in chunk order; the loads of four chunks are issued together
-    float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
-    for (int c0 = 0; c0 < nc; c0 += 4) {
-      float4 v4[4];
+// Double-single sum, in chunk order, of one (winner, prime) bin's nc chunk partials (hi, lo) for
+// the real and imaginary parts, returned in FP64; the loads of four chunks are issued together.
+__device__ __forceinline__ void combine_chunks(const float4* pc, int nc, double& re, double& im) {
+  float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
+  for (int c0 = 0; c0 < nc; c0 += 4) {
+    float4 v4[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v4[u] = c0 + u < nc ? pc[c0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < 4; ++u) v4[u] = c0 + u < nc ? pc[c0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (c0 + u >= nc) break;
-        const float4 v = v4[u];
-        float s, e;
-        two_sum(hr, v.x, s, e);
-        lr += e + v.y;
-        two_sum(s, lr, hr, lr);
-        two_sum(hi, v.z, s, e);
-        li += e + v.w;
-        two_sum(s, li, hi, li);
-      }
+    for (int u = 0; u < 4; ++u) {
+      if (c0 + u >= nc) break;
+      const float4 v = v4[u];
+      float s, e;
+      two_sum(hr, v.x, s, e);
+      lr += e + v.y;
+      two_sum(s, lr, hr, lr);
+      two_sum(hi, v.z, s, e);
+      li += e + v.w;
+      two_sum(s, li, hi, li);
     }
-    const double inv_p = 1.0 / (double)p;
-    re[jj] = ((double)hr + (double)lr) * inv_p;
-    im[jj] = ((double)hi + (double)li) * inv_p;
   }
+  re = (double)hr + (double)lr;
+  im = (double)hi + (double)li;
+}
+
+// The refined coefficient of winner r from its K bins (FP64): componentwise medians, the sign
+// (-1)^w and the division by g_hat_{w - q}; written back into winners[r].
+template <int KCAP>
+__device__ __forceinline__ void finish_winner(const DevPlan& d, int r, double* re, double* im) {
+  Pooled pw = d.winners[r];
   const double mre = median_of<KCAP>(re, d.K);
   const double mim = median_of<KCAP>(im, d.K);
   const double sg = (pw.w & 1) ? -1.0 : 1.0;
@@ -214,6 +203,65 @@ __global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView
   pw.cre = sg * mre * inv_ghat;
   pw.cim = sg * mim * inv_ghat;
   d.winners[r] = pw;
+}
+
+// Refined coefficients of the kRefineThreads winners of a CTA, one thread per winner (any K up to
+// kMaxK).
+template <int KCAP>
+__global__ void __launch_bounds__(kRefineThreads) refine_values_kernel(BatchView bv) {
+  pdl_begin();
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
+  const int n = d.counters[d.nq + 2];
+  const int r = lb * kRefineThreads + threadIdx.x;
+  if (r >= n) return;
+  double re[KCAP], im[KCAP];
+  const float4* part = reinterpret_cast<const float4*>(d.ybuf);
+  for (int jj = 0; jj < d.K; ++jj) {
+    const int p = d.p[jj];
+    const int nc = (p + kReChunk - 1) / kReChunk;
+    combine_chunks(part + ((int64_t)r * d.K + jj) * d.nchunk, nc, re[jj], im[jj]);
+    const double inv_p = 1.0 / (double)p;
+    re[jj] *= inv_p;
+    im[jj] *= inv_p;
+  }
+  finish_winner<KCAP>(d, r, re, im);
+}
+
+// The same for K <= kFewK with the CTA's kRefineThreads x K (winner, prime) bins spread over
+// kRefineFewThreads threads, so the chunk loads of all of a winner's bins are in flight at once
+// (a lone transform's thousand winners otherwise wait on K rounds of loads each); the bins meet in
+// shared memory and one thread per winner finishes it.  Same arithmetic, same bits.
+constexpr int kRefineFewThreads = 256;
+__global__ void __launch_bounds__(kRefineFewThreads) refine_values_few_kernel(BatchView bv) {
+  pdl_begin();
+  __shared__ double sre[kRefineThreads * kFewK], sim[kRefineThreads * kFewK];
+  int lb, nb;
+  const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
+  const int n = d.counters[d.nq + 2];
+  const int r0 = lb * kRefineThreads;
+  const int K = d.K;
+  const float4* part = reinterpret_cast<const float4*>(d.ybuf);
+  for (int q = threadIdx.x; q < kRefineThreads * K; q += kRefineFewThreads) {
+    const int wl = q / K, jj = q - wl * K;
+    if (r0 + wl >= n) continue;
+    const int p = d.p[jj];
+    const int nc = (p + kReChunk - 1) / kReChunk;
+    double re, im;
+    combine_chunks(part + ((int64_t)(r0 + wl) * K + jj) * d.nchunk, nc, re, im);
+    const double inv_p = 1.0 / (double)p;
+    sre[wl * kFewK + jj] = re * inv_p;
+    sim[wl * kFewK + jj] = im * inv_p;
+  }
+  __syncthreads();
+  const int wl = threadIdx.x;
+  if (wl >= kRefineThreads || r0 + wl >= n) return;
+  double re[kFewK], im[kFewK];
+  for (int jj = 0; jj < K; ++jj) {
+    re[jj] = sre[wl * kFewK + jj];
+    im[jj] = sim[wl * kFewK + jj];
+  }
+  finish_winner<kFewK>(d, r0 + wl, re, im);
 }
 
 }  // namespace
@@ -229,7 +277,7 @@ cudaError_t launch_refine(const BatchView& bv, const LaunchSet& ls, cudaStream_t
   (void)launch_pdl(reestimate_kernel, ls.blocks[kStReest], kReThreads, smem, st, v);
   v.blk = ls.blk[kStRefine];
   if (ls.kmax <= kFewK)
-    (void)launch_pdl(refine_values_kernel<kFewK>, ls.blocks[kStRefine], kRefineThreads, 0, st, v);
+    (void)launch_pdl(refine_values_few_kernel, ls.blocks[kStRefine], kRefineFewThreads, 0, st, v);
   else
     (void)launch_pdl(refine_values_kernel<kMaxK>, ls.blocks[kStRefine], kRefineThreads, 0, st, v);
   return cudaGetLastError();
