@@ -205,6 +205,8 @@ sft_status sft_batch_destroy(sft_batch_t batch);
  * with the same arguments as sft_batch_execute, waited for, and its own device arrays are freed
  * before the call returns (so, unlike the others, this call blocks the calling thread until the
  * transforms are complete).  For repeated executions of the same plans create the batch once.
+ * Errors: those of sft_batch_create and sft_batch_execute (nothing runs), or SFT_ECUDA when the
+ * execution failed on the device.
  */
 sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
                              int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
