@@ -434,13 +434,16 @@ sft_status sft_server_destroy(sft_server_t server);
  * 2 <= n <= 8191 (prime or not), in FP32, on `stream`.
  *
  * The kernel's tables (chirp, filter spectrum, FFT twiddles) and its launch record live in one
- * fixed 340 KiB array in
- * device memory that the library declares statically: every GPU that loads the library holds it
- * until the process exits, and nothing is allocated at any call.  The first call on a device looks
- * up that array's address and builds the tables for n on `stream`; a later call with another n
- * rebuilds them.  Make that first call on each device before any stream capture.  All calls share
- * the array, so calls that overlap on the GPU (different streams, or different n in flight) race;
- * serialise them.  Returns SFT_EINVAL for n outside 2..8191, batch < 1 or NULL/misaligned buffers.
+ * fixed 340 KiB array in device memory that the library declares statically: every GPU that
+ * loads the library holds it until the process exits, and nothing is allocated at any call.  The
+ * first call on a device looks up that array's address, and the first call with a given n (on
+ * that device, since the last call with another n) builds the tables for n on `stream`.  Such a
+ * call must not be made while `stream` is being captured (it returns SFT_EINVAL then): make it
+ * before any capture.  Every call enqueues two kernels on `stream` (one writes the call's launch
+ * record into the array, the other runs the transforms) and copies nothing from host memory.
+ * All calls share the array, which keeps the last call's record and tables, so calls that
+ * overlap on the GPU (different streams, or another n while one is in flight) race; serialise
+ * them.  Returns SFT_EINVAL for n outside 2..8191, batch < 1 or NULL/misaligned buffers.
  */
 sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_dev, void* out_dev,
                            void* stream);

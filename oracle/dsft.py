@@ -294,6 +294,23 @@ def median_estimate(Y: list, primes: list, w: int) -> complex:
     return complex(parity_sign(w) * (np.median(vals.real) + 1j * np.median(vals.imag)))
 
 
+def majority_vote(cand: list, K: int):
+    """Vote of the identification step (Appendix B, "more than half of the j"): w counts once for
+    every modulus j one of whose bins reconstructed exactly w (cand[j][b] is the frequency bin b
+    of modulus j reconstructed, or None); the w found by more than half of the K moduli are kept.
+    Returns the kept frequencies, ascending, and how many moduli found each."""
+    found = {}
+    for jj, cj in enumerate(cand):
+        for w in cj:
+            if w is not None:
+                found.setdefault(int(w), set()).add(jj)
+    need = K // 2 + 1
+    voted = sorted(w for w, js in found.items() if len(js) >= need)
+    voted = np.array(voted, dtype=np.int64)
+    votes = np.array([len(found[int(w)]) for w in voted], dtype=np.int64)
+    return voted, votes
+
+
 def ussft_shift(f: np.ndarray, plan: Plan, q: int) -> ShiftResult:
     N, K = plan.N, plan.K
     Y, residues, margins, cand = [], [], [], []
@@ -324,18 +341,7 @@ def ussft_shift(f: np.ndarray, plan: Plan, q: int) -> ShiftResult:
             cj[bb] = to_band(wt, M, N)
         cand.append(cj)
 
-    # Vote: w counts once for every modulus whose bin w mod p_j reconstructed exactly w; keep the
-    # w found by more than half of the moduli (Appendix B, "more than half of the j").
-    found = {}
-    for jj, p in enumerate(plan.primes):
-        for bb in range(p):
-            w = cand[jj][bb]
-            if w is not None:
-                found.setdefault(w, set()).add(jj)
-    need = K // 2 + 1
-    voted = sorted(w for w, js in found.items() if len(js) >= need)
-    voted = np.array(voted, dtype=np.int64)
-    votes = np.array([len(found[int(w)]) for w in voted], dtype=np.int64)
+    voted, votes = majority_vote(cand, K)
 
     # Estimate: componentwise medians over all K moduli of the bin holding w (eq. GSFT_Estimate),
     # times (-1)^w because the nodes start at -pi (reading of the node sign).

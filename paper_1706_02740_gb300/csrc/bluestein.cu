@@ -627,6 +627,30 @@ __global__ void __launch_bounds__(M / 16) noalloc_filter_kernel(int n, float2* V
   for (int i = lt; i < M; i += TPT) V[i] = cscale(s[pad16(i)], scale);
 }
 
+// The launch record of one call, written on the device (the fields the chirp-convolution kernel
+// reads; the rest of the record stays zero).  Its arguments travel by value with the launch, so
+// the call copies nothing from host memory.
+__global__ void noalloc_record_kernel(DevPlan* rec, int n, int batch, int M, void* in, void* out,
+                                      const float2* base) {
+  pdl_begin();
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  rec->prec = SFT_FP32;
+  rec->K = 1;
+  rec->nsub = 1;
+  rec->nq = batch;
+  rec->p[0] = n;
+  rec->nodeoff[0] = 0;
+  rec->nodeoff[1] = n;
+  rec->m = n;
+  rec->pmax = n;
+  rec->fftM = M;
+  rec->samples = in;
+  rec->bins = out;
+  rec->chirp = base;
+  rec->vhat = base + kNoAllocChirp;
+  rec->fftw = base + kNoAllocChirp + kNoAllocMaxM;
+}
+
 template <int M>
 cudaError_t noalloc_build(int n, float2* base, cudaStream_t st) {
   float2* chirp = base;
@@ -693,6 +717,15 @@ extern "C" sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_d
   DevPlan* rec = reinterpret_cast<DevPlan*>(g_noalloc_ptr[dev]);
   float2* base = reinterpret_cast<float2*>(g_noalloc_ptr[dev] + kNoAllocHead);
   if (g_noalloc_n[dev] != n) {
+    // building the tables must run now, not in a graph that may never be launched
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+      (void)cudaGetLastError();
+      set_error("sft_dft_noalloc: the first call with a new length (which builds the tables) "
+                "must not be made while the stream is being captured");
+      return SFT_EINVAL;
+    }
     e = noalloc_build_any(n, M, base, st);
     if (e != cudaSuccess) {
       g_noalloc_n[dev] = 0;
@@ -701,29 +734,20 @@ extern "C" sft_status sft_dft_noalloc(int32_t n, int32_t batch, const void* in_d
     }
     g_noalloc_n[dev] = n;
   }
+  (void)launch_pdl(noalloc_record_kernel, 1, 32, 0, st, rec, (int)n, (int)batch, M,
+                   const_cast<void*>(in_dev), out_dev, (const float2*)base);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("sft_dft_noalloc: record launch failed: ") + cudaGetErrorString(e));
+    return SFT_ECUDA;
+  }
+  // the host's view of the same record, for the block count
   DevPlan d;
   memset(&d, 0, sizeof(d));
-  d.prec = SFT_FP32;
   d.K = 1;
   d.nsub = 1;
   d.nq = batch;
-  d.p[0] = n;
-  d.nodeoff[0] = 0;
-  d.nodeoff[1] = n;
-  d.m = n;
-  d.pmax = n;
   d.fftM = M;
-  d.samples = const_cast<void*>(in_dev);
-  d.bins = out_dev;
-  d.chirp = base;
-  d.vhat = base + kNoAllocChirp;
-  d.fftw = base + kNoAllocChirp + kNoAllocMaxM;
-  // the record travels to the array's head in stream order (a pageable copy: no allocation)
-  e = cudaMemcpyAsync(rec, &d, sizeof(d), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) {
-    set_error(std::string("sft_dft_noalloc: record copy failed: ") + cudaGetErrorString(e));
-    return SFT_ECUDA;
-  }
   BatchView bv;
   memset(&bv, 0, sizeof(bv));
   bv.plans = rec;

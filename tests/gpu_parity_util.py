@@ -96,17 +96,44 @@ def crt_band(b, residues, p, small, N):
     return O.to_band(wt, p * math.prod(small), N)
 
 
-def oracle_vote(cand_q, primes, K):
-    """Apply the vote rule to a candidate array (one shift)."""
+def cand_lists(cand_q, primes):
+    """One shift's GPU candidate array [sum p] as the oracle's per-modulus lists (None: no
+    frequency)."""
     offs = np.cumsum([0] + list(primes))
-    found = {}
-    for j, p in enumerate(primes):
-        for b in range(p):
-            w = int(cand_q[offs[j] + b])
-            if w != np.iinfo(np.int64).min:
-                found.setdefault(w, set()).add(j)
-    need = K // 2 + 1
-    return sorted(w for w, js in found.items() if len(js) >= need)
+    nofreq = np.iinfo(np.int64).min
+    return [[None if int(w) == nofreq else int(w) for w in cand_q[offs[j]:offs[j + 1]]]
+            for j in range(len(primes))]
+
+
+def oracle_vote(cand_q, primes, K):
+    """The oracle's vote applied to the GPU's candidates of one shift: {w: votes}."""
+    voted, votes = O.majority_vote(cand_lists(cand_q, primes), K)
+    return dict(zip(voted.tolist(), votes.tolist()))
+
+
+VOTED_DTYPE = np.dtype([("w", "<i8"), ("zre", "<f8"), ("zim", "<f8"), ("votes", "<i4"),
+                        ("jmin", "<i4")])
+
+
+def gpu_voted(sft, plan, info):
+    """The GPU vote's output, per shift: {w: (votes, z)} from the plan's voted lists."""
+    import torch
+    nq = info["n_shifts"]
+    counts = sft.debug_tensor(plan, sft.BUF_COUNTERS, torch.int32, (nq + 4,)).cpu().numpy()
+    _, nbytes = sft.sft_plan_debug_buffer(plan, sft.BUF_VOTED)
+    raw = sft.debug_tensor(plan, sft.BUF_VOTED, torch.uint8, (nbytes,)).cpu().numpy()
+    vcap = nbytes // (nq * VOTED_DTYPE.itemsize)
+    recs = raw.view(VOTED_DTYPE).reshape(nq, vcap)
+    out = []
+    for qi in range(nq):
+        n = int(counts[qi])
+        assert n <= vcap, "voted list overflowed"
+        r = recs[qi, :n]
+        d = {int(w): (int(v), complex(a, b)) for w, v, a, b in zip(r["w"], r["votes"], r["zre"],
+                                                                   r["zim"])}
+        assert len(d) == n, "a frequency was voted twice"
+        out.append(d)
+    return out
 
 
 def rel_err(a, b):
@@ -131,3 +158,58 @@ def assert_same_output(gw, gc, ow, oc, tol):
         for k in range(i + 1, len(gw)):
             if mo[k] > mo[i] * (1 + 2 * tol):
                 raise AssertionError(f"order differs: {gw[i]} before {gw[k]}")
+
+
+def explain_output_differences(g, res, cand, info, tol, margin=1e-3, log=None):
+    """Account for every frequency that only one side returns (the rule for FP decisions: integer
+    stages agree given the same residues, and residues agree wherever the oracle's decision margin
+    exceeds `margin`).  A frequency w returned by one side only is explained when
+
+    * decision: at some modulus j the GPU's candidate of bin w mod p_j (shift of w's band) differs
+      from the oracle's, and there the oracle's residue decision had no margin (some small modulus
+      with margin <= `margin`) or the bin had no energy (< `margin` of the shift's largest bin); or
+    * cut: the other side's output is full (s terms) and |c_w| is no larger than the other side's
+      weakest returned coefficient, within 2 tol (the s-th magnitude decides, in the path's
+      precision).
+
+    Returns [(w, side, reason)]; raises AssertionError on a difference neither explains.  `cand` is
+    the GPU's candidate array [n_shifts][sum p]."""
+    n = g["count"]
+    gmap = dict(zip(g["freqs"][:n].tolist(), g["coefs"][:n]))
+    omap = dict(zip(res.freqs.tolist(), res.coefs))
+    s = info["s"]
+    primes, L = info["primes"], info["L"]
+    offs = np.cumsum([0] + list(primes))
+    nofreq = np.iinfo(np.int64).min
+    gmin = min((abs(c) for c in gmap.values()), default=0.0)
+    omin = min((abs(c) for c in omap.values()), default=0.0)
+    out = []
+    for w in sorted(set(gmap) ^ set(omap)):
+        side = "gpu" if w in gmap else "oracle"
+        c = gmap[w] if w in gmap else omap[w]
+        reason = None
+        qi = [i for i, q in enumerate(info["shifts"]) if q - L <= w < q + L]
+        assert len(qi) == 1, (w, qi)
+        sr = res.shifts[qi[0]]
+        bmax = max(np.max(np.abs(y)) for y in sr.Y)
+        for j, p in enumerate(primes):
+            b = w % p
+            oc = nofreq if sr.cand[j][b] is None else sr.cand[j][b]
+            if int(cand[qi[0], offs[j] + b]) == oc:
+                continue
+            m = min((float(sr.margins[j][l][b]) for l in range(len(info["small"]))), default=1.0)
+            e = abs(sr.Y[j][b]) / bmax
+            if m <= margin or e < margin:
+                reason = f"decision at p={p} bin {b}: margin {m:.2e}, energy {e:.2e}"
+                break
+        if reason is None:
+            other_full = (len(omap) if side == "gpu" else len(gmap)) == s
+            other_min = omin if side == "gpu" else gmin
+            if other_full and abs(c) <= other_min * (1 + 2 * tol):
+                reason = f"cut: |c| {abs(c):.6e} vs other side's weakest {other_min:.6e}"
+        if reason is None:
+            raise AssertionError(f"unexplained difference: w={w} only on the {side} side, |c|={abs(c):.3e}")
+        out.append((w, side, reason))
+        if log is not None:
+            log(f"w={w} only on the {side} side: {reason}")
+    return out

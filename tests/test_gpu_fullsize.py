@@ -1,13 +1,15 @@
 """Parity at the benchmark sizes, through the C ABI, against the CPU oracle on the same input.
 
-* N = 2^26, s = 1000 (the precision study; the launch configuration bench.py times: FP32 path,
-  K = 5, c_p = 3, kappa = 6): the oracle runs in full (about 10 s).
+* N = 2^26, s = 1000 (the precision study: log-uniform magnitudes on [1e-2, 1], SNR 30 dB; the
+  launch configuration bench.py times: K = 5, c_p = 3, kappa = 6), trials 0..2 of its seeded
+  inputs, on the FP32 path and on the FP64 path; the oracle runs in full once per trial.
 * N = 2^22 and the prime N = 4194301, s = 64, SNR 20 dB: FP32 and FP64 paths.
 
-At these sizes the inputs are noisy, so a few candidates sit at the vote threshold or at the
-s-th magnitude, where FP32 and FP64 decisions may legitimately differ; such frequencies must be
-weak (below `floor`) and few.  Every frequency both sides return must agree within the path's
-tolerance (1e-5 relative FP32, 1e-11 FP64).
+Every frequency both sides return agrees within the path's tolerance (1e-5 relative FP32, 1e-11
+FP64).  A frequency only one side returns is accepted only with an explanation: a candidate that
+differs at a bin whose residue decision had no margin (oracle margin <= 1e-3, the rule for FP
+decisions), or the s-th magnitude cut (tests/gpu_parity_util.explain_output_differences); each
+one is printed.  The recovered support is also checked against the generating spectrum.
 """
 import numpy as np
 import pytest
@@ -29,33 +31,48 @@ def _lib():
     sft.load()
 
 
-def _compare(g, res, tol, floor, max_diff_frac):
+_ORACLE = {}
+
+
+def _oracle(key, f, info, N, s):
+    if key not in _ORACLE:
+        _ORACLE[key] = O.dsft(f, U.oracle_plan(info, N, s))
+    return _ORACLE[key]
+
+
+def _compare(g, res, cand, tol):
     n = g["count"]
-    gw, gc = g["freqs"][:n], g["coefs"][:n]
-    ow, oc = res.freqs, res.coefs
-    gmap = dict(zip(gw.tolist(), gc))
-    omap = dict(zip(ow.tolist(), oc))
+    gmap = dict(zip(g["freqs"][:n].tolist(), g["coefs"][:n]))
+    omap = dict(zip(res.freqs.tolist(), res.coefs))
     common = sorted(set(gmap) & set(omap))
-    diff = set(gmap) ^ set(omap)
-    assert len(diff) <= max_diff_frac * max(len(ow), 1), len(diff)
-    for w in diff:
-        c = gmap.get(w, omap.get(w))
-        assert abs(c) < floor, (w, abs(c))
+    expl = U.explain_output_differences(g, res, cand, g["info"], tol, log=print)
     a = np.array([gmap[w] for w in common])
     b = np.array([omap[w] for w in common])
     err = np.abs(a - b) / np.abs(b)
     assert np.max(err) <= tol, np.max(err)
-    return len(common), len(diff), float(np.max(err))
+    return len(common), expl, float(np.max(err))
 
 
-def test_precision_study_n2p26_s1000():
+def _run(N, s, f, prec, K, c_p, seed):
+    g = U.run_gpu(sft, N, s, f, prec, kappa=6, K=K, c_p=c_p, seed=seed, keep=True)
+    cand = U.debug_arrays(sft, g["plan"], g["info"])[2]
+    g["plan"].destroy()
+    return g, cand
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+@pytest.mark.parametrize("trial", [0, 1, 2])
+def test_precision_study_n2p26_s1000(trial, prec):
     N, s = 2 ** 26, 1000
-    sig = make_signal(N, s, 3000, "loguniform", 30.0)
+    sig = make_signal(N, s, 3000 + trial, "loguniform", 30.0)
     f32 = as_complex64(sig.f)
-    g = U.run_gpu(sft, N, s, f32, U.FP32, kappa=6, K=5, c_p=3.0, seed=1)
-    res = O.dsft(upcast(f32), U.oracle_plan(g["info"], N, s))
-    common, ndiff, err = _compare(g, res, 1e-5, floor=0.03, max_diff_frac=0.02)
-    # the recovered support against the generating spectrum
+    f = f32 if prec == U.FP32 else upcast(f32)
+    g, cand = _run(N, s, f, prec, 5, 3.0, 1 + trial)
+    res = _oracle(("c3", trial), upcast(f32), g["info"], N, s)
+    tol = 1e-5 if prec == U.FP32 else 1e-11
+    common, expl, err = _compare(g, res, cand, tol)
+    print(f"trial {trial} prec {prec}: common {common}, explained differences {len(expl)}, "
+          f"max rel err {err:.2e}")
     hits = len(set(g["freqs"][: g["count"]].tolist()) & set(sig.omega.tolist()))
     assert hits >= 0.95 * s
 
@@ -67,8 +84,8 @@ def test_config2_n2p22_and_prime(N, prec):
     sig = make_signal(N, s, 2000 + N % 7, "unit", 20.0)
     f32 = as_complex64(sig.f)
     f = f32 if prec == U.FP32 else upcast(f32)
-    g = U.run_gpu(sft, N, s, f, prec, kappa=6, K=5, c_p=3.0, seed=2)
-    res = O.dsft(upcast(f32), U.oracle_plan(g["info"], N, s))
-    _compare(g, res, 1e-5 if prec == U.FP32 else 1e-11, floor=0.3, max_diff_frac=0.05)
+    g, cand = _run(N, s, f, prec, 5, 3.0, 2)
+    res = _oracle(("c2", N), upcast(f32), g["info"], N, s)
+    _compare(g, res, cand, 1e-5 if prec == U.FP32 else 1e-11)
     hits = len(set(g["freqs"][: g["count"]].tolist()) & set(sig.omega.tolist()))
     assert hits >= s - 2

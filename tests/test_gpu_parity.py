@@ -48,6 +48,7 @@ def test_stages_and_output_match_oracle(case, prec):
     oplan = U.oracle_plan(info, N, s)
     assert oplan.shifts == info["shifts"] and oplan.L == info["L"]
     samples, bins, cand, resid = U.debug_arrays(sft, plan, info)
+    gvoted = U.gpu_voted(sft, plan, info)
     plan.destroy()
 
     # (a) resampling at every node, every shift
@@ -84,10 +85,27 @@ def test_stages_and_output_match_oracle(case, prec):
                 w = U.crt_band(b, resid[qi, offs[j] + b, :len(small)], p, small, N)
                 expect = np.iinfo(np.int64).min if w is None else w
                 assert cand[qi, offs[j] + b] == expect
-        # (c'') the vote re-run on the GPU's candidates reproduces the oracle's significant votes
+        # (d) the GPU's vote is the oracle's vote run on the GPU's own candidates: the same
+        #     frequencies with the same counts; its medians are the oracle's within the bins'
+        #     tolerance (a componentwise median moves by at most the largest input change)
         gv = U.oracle_vote(cand[qi], primes, len(primes))
-        sig_or = {int(w) for w, z in zip(sr.voted, sr.z) if abs(z) > 1e-3 * bmax}
-        assert sig_or <= set(gv)
+        assert {w: v for w, (v, _) in gvoted[qi].items()} == gv
+        for w, (_, z) in gvoted[qi].items():
+            assert abs(z - O.median_estimate(sr.Y, primes, w)) <= 2 * tol_b * bmax
+        # (d') against the oracle's own vote: a frequency kept (or counted) differently must have
+        #      a candidate that differs at a bin whose residue decision had no margin
+        ov = dict(zip(sr.voted.tolist(), sr.votes.tolist()))
+        for w in set(ov) | set(gv):
+            if ov.get(w) == gv.get(w):
+                continue
+            weak = False
+            for j, p in enumerate(primes):
+                b = w % p
+                oc = np.iinfo(np.int64).min if sr.cand[j][b] is None else sr.cand[j][b]
+                if cand[qi, offs[j] + b] != oc:
+                    m = min((sr.margins[j][l][b] for l in range(len(small))), default=1.0)
+                    weak |= m <= 1e-3 or abs(sr.Y[j][b]) < 1e-3 * bmax
+            assert weak, (w, ov.get(w), gv.get(w))
 
     # final output: same support and ordering, coefficients within tolerance
     n = g["count"]

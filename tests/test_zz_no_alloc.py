@@ -61,3 +61,53 @@ def test_noalloc_dft_matches_the_plan_measurements():
         sft.sft_dft_noalloc(8192, 1, x.data_ptr(), out.data_ptr(), 0)
     assert e.value.status == sft.SFT_EINVAL and "8191" in sft.sft_last_error()
     plan.destroy()
+
+
+@pytest.mark.parametrize("n", [2, 3, 64, 4096, 4097, 6000, 8191])
+def test_noalloc_dft_lengths_against_numpy(n):
+    """The ends of the accepted range (n = 2, and n = 8191 with its length-16384 convolution and
+    one-CTA filter build), powers of two, a composite length and a prime: three vectors per call
+    against numpy's DFT / n, within 1e-5 of the largest bin."""
+    import torch
+
+    import paper_1706_02740_gb300 as sft
+    from paper_1706_02740_gb300 import build
+
+    build.build()
+    sft.load()
+    rng = np.random.default_rng(n)
+    batch = 3
+    xn = (rng.standard_normal((batch, n)) + 1j * rng.standard_normal((batch, n))).astype(np.complex64)
+    x = torch.from_numpy(xn).cuda()
+    out = torch.empty_like(x)
+    sft.sft_dft_noalloc(n, batch, x.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    exact = np.fft.fft(xn.astype(np.complex128), axis=1) / n
+    scale = np.max(np.abs(exact))
+    assert np.max(np.abs(out.cpu().numpy() - exact)) <= 1e-5 * scale
+
+
+def test_noalloc_dft_length_changes_on_one_stream():
+    """Lengths alternating on one stream without a synchronisation between calls: each call's
+    tables are rebuilt in stream order before its transforms run."""
+    import torch
+
+    import paper_1706_02740_gb300 as sft
+    from paper_1706_02740_gb300 import build
+
+    build.build()
+    sft.load()
+    st = torch.cuda.Stream()
+    rng = np.random.default_rng(5)
+    cases = []
+    with torch.cuda.stream(st):
+        for n in [1531, 97, 1531, 8191, 97]:
+            xn = (rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))).astype(np.complex64)
+            x = torch.from_numpy(xn).to("cuda", non_blocking=False)
+            out = torch.empty_like(x)
+            sft.sft_dft_noalloc(n, 2, x.data_ptr(), out.data_ptr(), st.cuda_stream)
+            cases.append((xn, x, out))
+    st.synchronize()
+    for xn, _, out in cases:
+        exact = np.fft.fft(xn.astype(np.complex128), axis=1) / xn.shape[1]
+        assert np.max(np.abs(out.cpu().numpy() - exact)) <= 1e-5 * np.max(np.abs(exact))
