@@ -42,7 +42,7 @@ typedef enum {
   SFT_EINVAL = 1,    /* invalid argument or plan parameters */
   SFT_ENOMEM = 2,    /* device or host allocation failed (nothing leaked) */
   SFT_ECUDA = 3,     /* a CUDA runtime call failed */
-  SFT_ETIMEOUT = 4,  /* a bounded device wait ran out (status word set by a kernel) */
+  SFT_ETIMEOUT = 4,  /* a bounded wait ran out (sft_server_wait's time limit) */
   SFT_EBUSY = 5      /* server full: request not admitted */
 } sft_status;
 
@@ -74,6 +74,12 @@ typedef enum { SFT_IN_C64 = 0, SFT_IN_C128 = 1 } sft_input_type;
  *             as integers; the s winners are then re-estimated from the samples with exact
  *             twiddles and compensated accumulation, medians and division in FP64.
  *             SFT_FP64: every stage in FP64.
+ *  refine_fp64
+ *             FP32 path only (ignored for SFT_FP64): 1 (default) runs the re-estimation of the s
+ *             winners described above; 0 returns the FP32 medians divided by the filter's
+ *             coefficient as they are (three fewer kernels; the coefficients then carry the FP32
+ *             DFTs' rounding, about 1e-6 of the largest bin, instead of meeting 1e-5 relative).
+ *             Plans of one batch must agree on it.
  *  input      element type of f: SFT_IN_C64 (interleaved float re,im) or SFT_IN_C128 (double).
  */
 typedef struct {
@@ -86,7 +92,7 @@ typedef struct {
   double beta;
   uint64_t seed;
   int32_t deterministic;
-  int32_t reserved;
+  int32_t refine_fp64;
 } sft_variant;
 
 /*
@@ -127,7 +133,8 @@ typedef struct {
 } sft_plan_desc;
 
 /* Fill *v with the defaults: kappa 6 (DMSFT-6), FP32, complex64 input, K 5, c_p 3,
- * alpha = beta = 1.5, seed 0.  Returns SFT_EINVAL if v is NULL. */
+ * alpha = beta = 1.5, seed 0, randomized inner SFT, refine_fp64 1.  Returns SFT_EINVAL if v is
+ * NULL. */
 sft_status sft_variant_init(sft_variant* v);
 
 /*
@@ -139,6 +146,8 @@ sft_status sft_variant_init(sft_variant* v);
  *  small_moduli  NULL = the smallest primes, none equal to a p_j, until p_1 prod(t) >= N;
  *                else n_small pairwise-coprime moduli >= 2, coprime to every p_j, p_1 prod >= N.
  * Requires 2 <= N < 2^31, 1 <= s <= N, 2 kappa + 1 <= N, every p_j <= 8192 (FP32) or 4096 (FP64).
+ * (Theorem MainTHM is stated for s >= 2; s = 1 is accepted, since Algorithm 1 itself is defined
+ * for it: one term per shift, the largest kept.)
  * Allocates the plan's device tables and scratch on the current device (sft_plan_device_bytes).
  * On failure *out is set to NULL and nothing is leaked.
  */
@@ -201,12 +210,15 @@ sft_status sft_batch_execute(sft_batch_t batch, const void* const* f_devs,
 sft_status sft_batch_destroy(sft_batch_t batch);
 
 /*
- * One-shot form of the three calls above: a batch of plans[0..n) is built, executed on `stream`
- * with the same arguments as sft_batch_execute, waited for, and its own device arrays are freed
- * before the call returns (so, unlike the others, this call blocks the calling thread until the
- * transforms are complete).  For repeated executions of the same plans create the batch once.
- * Errors: those of sft_batch_create and sft_batch_execute (nothing runs), or SFT_ECUDA when the
- * execution failed on the device.
+ * One-shot form of the three calls above: the transforms of plans[0..n) with one launch per stage,
+ * enqueued on `stream` with the same arguments as sft_batch_execute; the call returns without
+ * waiting (results are valid after the stream is synchronised).  The call's own device array (the
+ * plans' records, block prefixes and pointer tables, about 20 KB per plan) comes from the
+ * stream-ordered allocator (cudaMallocAsync on `stream`) and is released in stream order after
+ * the last stage (cudaFreeAsync), so nothing outlives the call on the host.  It is not meant for
+ * stream capture.  For repeated executions of the same plans create a batch once (graph replay,
+ * tuning).  Errors: those of sft_batch_create and sft_batch_execute (nothing runs), or SFT_ENOMEM
+ * / SFT_ECUDA when the allocation or a launch fails.
  */
 sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
                              int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
@@ -292,7 +304,12 @@ sft_status sft_plan_info(sft_plan_t plan, sft_plan_desc* out);
  *   2 cand     int64 [n_shifts][sum_j p_j]: frequency identified in bin b of modulus p_j, or
  *              INT64_MIN when the CRT representative lies outside B.
  *   3 residues uint8 [n_shifts][sum_j p_j][n_small]: residue of bin b modulo each t_l.
- *   4 voted    per-shift voted lists: int32 count[n_shifts] then records (see csrc).
+ *   4 counters int32 [n_shifts + 4]: entry i < n_shifts is the length of shift i's voted list,
+ *              entry n_shifts the length of the pooled in-band list, n_shifts + 2 the winner
+ *              count.
+ *   5 voted    [n_shifts][capacity] records of 32 bytes: int64 frequency, double re and im of the
+ *              median estimate (with the (-1)^w factor), int32 vote count, int32 first prime index
+ *              that found it; shift i's first counters[i] records are valid, in no fixed order.
  * *bytes receives the buffer size.  Returns SFT_EINVAL for an unknown index.
  */
 sft_status sft_plan_debug_buffer(sft_plan_t plan, int32_t which, void** dev_ptr, size_t* bytes);

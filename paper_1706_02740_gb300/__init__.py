@@ -34,7 +34,7 @@ class sft_variant(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("input", ctypes.c_int32), ("K", ctypes.c_int32), ("c_p", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("deterministic", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("deterministic", ctypes.c_int32), ("refine_fp64", ctypes.c_int32)]
 
 
 class sft_plan_desc(ctypes.Structure):
@@ -404,7 +404,7 @@ def _batch_ptrs(fs, outs):
 
 
 def sft_execute_batch(plans, f_ptrs, w_ptrs, c_ptrs, n_ptrs, stream: int = 0):
-    """One-shot batch over plans (blocks until the transforms are complete)."""
+    """One-shot batch over plans, enqueued on `stream` (results valid after it is synchronised)."""
     n = len(plans)
     arrs = [(ctypes.c_void_p * n)(*[int(x) for x in ptrs])
             for ptrs in ([p.handle for p in plans], f_ptrs, w_ptrs, c_ptrs, n_ptrs)]

@@ -159,7 +159,7 @@ cudaError_t run_stages(const DevPlan& d0, const BatchView& bv, const LaunchSet& 
   mark(4);
   if (e == cudaSuccess) e = launch_select(bv, ls, st, launched);
   mark(5);
-  if (e == cudaSuccess && !fp64) { e = launch_refine(bv, ls, st); *launched += 3; }
+  if (e == cudaSuccess && !fp64 && d0.refine) { e = launch_refine(bv, ls, st); *launched += 3; }
   if (e == cudaSuccess) e = launch_finalize(bv, ls, st, launched);
   mark(6);
   return e;
@@ -190,7 +190,7 @@ sft_status sft_variant_init(sft_variant* v) {
   v->beta = 1.5;
   v->seed = 0;
   v->deterministic = 0;
-  v->reserved = 0;
+  v->refine_fp64 = 1;
   return SFT_OK;
 }
 

@@ -123,6 +123,35 @@ sft_status check_buffers(const Batch& B, const void* const* f_devs, int64_t* con
   return SFT_OK;
 }
 
+// The plans of a batch: non-NULL, each once, sharing precision, input type, kappa and the
+// refinement switch.
+sft_status check_plans(const char* who, const sft_plan_t* plans, int32_t n, std::vector<Plan*>& ps) {
+  if (!plans || n < 1 || n > (1 << 20)) {
+    set_error(std::string(who) + ": need plans and 1 <= n <= 2^20");
+    return SFT_EINVAL;
+  }
+  ps.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) { set_error(std::string(who) + ": NULL plan"); return SFT_EINVAL; }
+    ps[i] = sft_plan_internal(plans[i]);
+  }
+  const DevPlan& a = ps[0]->d;
+  for (int i = 0; i < n; ++i) {
+    const DevPlan& b = ps[i]->d;
+    if (b.prec != a.prec || b.input != a.input || b.kappa != a.kappa || b.refine != a.refine) {
+      set_error(std::string(who) + ": plans must share precision, input type, kappa and refine_fp64");
+      return SFT_EINVAL;
+    }
+  }
+  std::vector<Plan*> sorted(ps);
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+    set_error(std::string(who) + ": a plan may appear once (its scratch serves one signal)");
+    return SFT_EINVAL;
+  }
+  return SFT_OK;
+}
+
 sft_status execute(Batch& B, const void* const* f_devs, int64_t* const* out_freqs_devs,
                    void* const* out_coefs_devs, int32_t* const* out_count_devs, cudaStream_t st) {
   const int n = B.n;
@@ -204,32 +233,15 @@ extern "C" {
 
 sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n) {
   using namespace sft;
-  if (!out || !plans || n < 1 || n > (1 << 20)) {
-    set_error("sft_batch_create: need out, plans and 1 <= n <= 2^20");
+  if (!out) {
+    set_error("sft_batch_create: out is NULL");
     return SFT_EINVAL;
   }
   *out = nullptr;
-  std::vector<Plan*> ps(n);
-  for (int i = 0; i < n; ++i) {
-    if (!plans[i]) { set_error("sft_batch_create: NULL plan"); return SFT_EINVAL; }
-    ps[i] = sft_plan_internal(plans[i]);
-  }
+  std::vector<Plan*> ps;
+  const sft_status chk = check_plans("sft_batch_create", plans, n, ps);
+  if (chk != SFT_OK) return chk;
   const DevPlan& a = ps[0]->d;
-  for (int i = 0; i < n; ++i) {
-    const DevPlan& b = ps[i]->d;
-    if (b.prec != a.prec || b.input != a.input || b.kappa != a.kappa) {
-      set_error("sft_batch_create: plans must share precision, input type and kappa");
-      return SFT_EINVAL;
-    }
-  }
-  {
-    std::vector<Plan*> sorted(ps);
-    std::sort(sorted.begin(), sorted.end());
-    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
-      set_error("sft_batch_create: a plan may appear once (its scratch serves one signal)");
-      return SFT_EINVAL;
-    }
-  }
   sft_batch_s* h = new (std::nothrow) sft_batch_s();
   if (!h) { set_error("host allocation failed"); return SFT_ENOMEM; }
   Batch& B = h->B;
@@ -441,17 +453,81 @@ sft_status sft_batch_destroy(sft_batch_t batch) {
 sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
                              int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
                              int32_t* const* out_count_devs, int32_t n, void* stream) {
-  sft_batch_t b = nullptr;
-  sft_status s = sft_batch_create(&b, plans, n);
+  using namespace sft;
+  std::vector<Plan*> ps;
+  sft_status s = check_plans("sft_execute_batch", plans, n, ps);
   if (s != SFT_OK) return s;
-  s = sft_batch_execute(b, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs, stream);
-  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-  sft_batch_destroy(b);
-  if (s == SFT_OK && e != cudaSuccess) {
-    sft::set_error(std::string("sft_execute_batch: ") + cudaGetErrorString(e));
+  if (!f_devs || !out_freqs_devs || !out_coefs_devs || !out_count_devs) {
+    set_error("sft_execute_batch: NULL argument");
+    return SFT_EINVAL;
+  }
+  const DevPlan& d0 = ps[0]->d;
+  const size_t align = d0.input == SFT_IN_C64 ? 8 : 16;
+  for (int i = 0; i < n; ++i) {
+    if (!f_devs[i] || ((uintptr_t)f_devs[i] % align) || !out_freqs_devs[i] || !out_coefs_devs[i] ||
+        !out_count_devs[i]) {
+      set_error("sft_execute_batch: NULL or misaligned pointer for signal " + std::to_string(i));
+      return SFT_EINVAL;
+    }
+  }
+  LaunchSet ls;
+  memset(&ls, 0, sizeof(ls));
+  ls.tune = default_tuning();
+  for (int i = 0; i < n; ++i) {
+    ls.pmax = std::max(ls.pmax, ps[i]->d.pmax);
+    ls.kmax = std::max(ls.kmax, ps[i]->d.K);
+  }
+  std::vector<int32_t> prefix;
+  if (!make_prefixes(ps, ls.tune, prefix, ls.blocks)) {
+    set_error("sft_execute_batch: batch too large (a launch would exceed 2^31 - 1 blocks)");
+    return SFT_EINVAL;
+  }
+  // one device array: records | block prefixes | pointer tables, filled from one host image by a
+  // stream-ordered copy (pageable source: staged before the copy call returns)
+  const size_t o_prefix = align256(sizeof(DevPlan) * (size_t)n);
+  const size_t o_ptrs = align256(o_prefix + prefix.size() * sizeof(int32_t));
+  const size_t total = o_ptrs + 4 * (size_t)n * sizeof(void*);
+  std::vector<char> blob(total, 0);
+  for (int i = 0; i < n; ++i) memcpy(blob.data() + sizeof(DevPlan) * i, &ps[i]->d, sizeof(DevPlan));
+  memcpy(blob.data() + o_prefix, prefix.data(), prefix.size() * sizeof(int32_t));
+  void** hp = reinterpret_cast<void**>(blob.data() + o_ptrs);
+  for (int i = 0; i < n; ++i) {
+    hp[i] = const_cast<void*>(f_devs[i]);
+    hp[n + i] = out_freqs_devs[i];
+    hp[2 * n + i] = out_coefs_devs[i];
+    hp[3 * n + i] = out_count_devs[i];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  char* dev = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&dev, total, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("sft_execute_batch: cudaMallocAsync failed: ") + cudaGetErrorString(e));
+    return SFT_ENOMEM;
+  }
+  e = cudaMemcpyAsync(dev, blob.data(), total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < kStCount; ++k)
+      ls.blk[k] = reinterpret_cast<int32_t*>(dev + o_prefix) + (size_t)k * (n + 1);
+    void** dp = reinterpret_cast<void**>(dev + o_ptrs);
+    BatchView bv;
+    memset(&bv, 0, sizeof(bv));
+    bv.plans = reinterpret_cast<DevPlan*>(dev);
+    bv.n = n;
+    bv.f = const_cast<const void* const*>(dp);
+    bv.out_w = reinterpret_cast<int64_t* const*>(dp + n);
+    bv.out_c = reinterpret_cast<double2* const*>(dp + 2 * n);
+    bv.out_n = reinterpret_cast<int32_t* const*>(dp + 3 * n);
+    int launched = 0;
+    e = run_stages(d0, bv, ls, st, nullptr, &launched);
+  }
+  const cudaError_t ef = cudaFreeAsync(dev, st);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) {
+    set_error(std::string("sft_execute_batch: ") + cudaGetErrorString(e));
     return SFT_ECUDA;
   }
-  return s;
+  return SFT_OK;
 }
 
 sft_status sft_batch_profile(sft_batch_t batch, int32_t enable) {

@@ -267,6 +267,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   // ---- fill the device-plan scalars
   d.N = N; d.s = s; d.kappa = v->kappa; d.K = K; d.nT = nT; d.nq = (int32_t)nq; d.nsub = nsub;
   d.prec = v->precision; d.input = v->input;
+  d.refine = (v->precision == SFT_FP32 && v->refine_fp64) ? 1 : 0;
   d.fftM = M; d.fftLog2 = logM; d.pmax = pmax;
   int64_t sump = 0;
   for (int j = 0; j < K; ++j) {

@@ -42,6 +42,7 @@ struct DevPlan {
   int64_t N;
   int32_t s, kappa, K, nT, nq, nsub;
   int32_t prec, input;
+  int32_t refine;             // FP32 path: re-estimate the winners (sft_variant.refine_fp64)
   int64_t m;                  // distinct nodes: nsub * sum_j p_j
   int32_t Ptot;               // sum_j p_j
   int32_t fftM, fftLog2;      // chirp convolution length (r 2^k, r = 1, 3, 5, 7), floor(log2 fftM)

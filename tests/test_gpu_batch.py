@@ -66,8 +66,9 @@ def test_heterogeneous_batch_equals_single_executions(prec):
 
 
 def test_one_shot_batch_equals_the_batch_object():
-    """sft_execute_batch (build, run, wait, free in one call) against a resident batch of the same
-    plans: identical bits."""
+    """sft_execute_batch (stream-ordered: its device array is allocated and released on the
+    stream) against a resident batch of the same plans: identical bits, also for a second call
+    enqueued behind the first with the inputs reversed and no synchronisation between them."""
     import torch
     shapes = SHAPES[:4]
     plans = [sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=6.0, seed=i))
@@ -86,6 +87,25 @@ def test_one_shot_batch_equals_the_batch_object():
     for (w, c, n), (rw, rc, rn) in zip(outs, ref):
         assert int(n.item()) == int(rn.item())
         assert torch.equal(w, rw) and torch.equal(c, rc)
+    # two calls back to back on one stream: the second writes elsewhere, the first's outputs stay
+    st = torch.cuda.current_stream().cuda_stream
+    outs2 = [(torch.empty(s, dtype=torch.int64, device="cuda"),
+              torch.empty(s, dtype=torch.complex128, device="cuda"),
+              torch.empty(1, dtype=torch.int32, device="cuda")) for _, s in shapes]
+    rplans = plans[::-1]
+    batch_r = sft.Batch(rplans)
+    ref_r = sft.execute_batch_torch(batch_r, fs)     # plan i (reversed) on input i
+    torch.cuda.synchronize()
+    batch_r.destroy()
+    sft.sft_execute_batch(plans, [f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs],
+                          [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs], st)
+    sft.sft_execute_batch(rplans, [f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs2],
+                          [o[1].data_ptr() for o in outs2], [o[2].data_ptr() for o in outs2], st)
+    torch.cuda.synchronize()
+    for (w, c, n), (rw, rc, rn) in zip(outs, ref):
+        assert int(n.item()) == int(rn.item()) and torch.equal(w, rw) and torch.equal(c, rc)
+    for (w, c, n), (rw, rc, rn) in zip(outs2, ref_r):
+        assert int(n.item()) == int(rn.item()) and torch.equal(w, rw) and torch.equal(c, rc)
     for p in plans:
         p.destroy()
 

@@ -342,3 +342,28 @@ def test_input_in_pinned_host_memory_gives_the_same_bits(prec):
     assert torch.equal(outs[0][0], wd) and torch.equal(outs[0][1], cd)
     batch.destroy()
     plan.destroy()
+
+
+def test_fp32_path_without_refinement():
+    """refine_fp64 = 0: the FP32 path returns its FP32 medians divided by g_hat (no re-estimation
+    kernels): the same support as with refinement, coefficients within the FP32 DFTs' rounding
+    (2e-6 of the largest bin, amplified by 1/g_hat at most sqrt(2 pi) e^{1/2} towards the band
+    edges, i.e. below 2e-5 of the largest coefficient), three fewer launches."""
+    import torch
+    N, s = 2 ** 18, 24
+    sig = make_signal(N, s, 31, "loguniform", 40.0)
+    f = torch.from_numpy(as_complex64(sig.f)).cuda()
+    outs = {}
+    for refine in (1, 0):
+        plan = sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=5.0, seed=8, refine_fp64=refine))
+        w, c, n = sft.execute_torch(plan, f)
+        torch.cuda.synchronize()
+        nn = int(n.item())
+        outs[refine] = (w.cpu().numpy()[:nn], c.cpu().numpy()[:nn], sft.sft_plan_launches(plan))
+        plan.destroy()
+    (w1, c1, l1), (w0, c0, l0) = outs[1], outs[0]
+    assert sorted(w1.tolist()) == sorted(w0.tolist())
+    m1 = dict(zip(w1.tolist(), c1))
+    ref = np.array([m1[int(w)] for w in w0])
+    assert np.max(np.abs(c0 - ref)) <= 2e-5 * np.max(np.abs(ref))
+    assert l1 - l0 == 3
