@@ -87,19 +87,20 @@ def test_one_shot_batch_equals_the_batch_object():
     for (w, c, n), (rw, rc, rn) in zip(outs, ref):
         assert int(n.item()) == int(rn.item())
         assert torch.equal(w, rw) and torch.equal(c, rc)
-    # two calls back to back on one stream: the second writes elsewhere, the first's outputs stay
+    # two calls back to back on one stream, the second over the same plans and inputs in reverse
+    # order (each plan keeps its own input and output sizes): both results stay intact
     st = torch.cuda.current_stream().cuda_stream
+    rshapes, rplans, rfs = shapes[::-1], plans[::-1], fs[::-1]
     outs2 = [(torch.empty(s, dtype=torch.int64, device="cuda"),
               torch.empty(s, dtype=torch.complex128, device="cuda"),
-              torch.empty(1, dtype=torch.int32, device="cuda")) for _, s in shapes]
-    rplans = plans[::-1]
+              torch.empty(1, dtype=torch.int32, device="cuda")) for _, s in rshapes]
     batch_r = sft.Batch(rplans)
-    ref_r = sft.execute_batch_torch(batch_r, fs)     # plan i (reversed) on input i
+    ref_r = sft.execute_batch_torch(batch_r, rfs)
     torch.cuda.synchronize()
     batch_r.destroy()
     sft.sft_execute_batch(plans, [f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs],
                           [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs], st)
-    sft.sft_execute_batch(rplans, [f.data_ptr() for f in fs], [o[0].data_ptr() for o in outs2],
+    sft.sft_execute_batch(rplans, [f.data_ptr() for f in rfs], [o[0].data_ptr() for o in outs2],
                           [o[1].data_ptr() for o in outs2], [o[2].data_ptr() for o in outs2], st)
     torch.cuda.synchronize()
     for (w, c, n), (rw, rc, rn) in zip(outs, ref):
