@@ -33,7 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT, S_DEFAULT = 2 ** 26, 1000
-PLAN = dict(kappa=6, K=5, c_p=3.0, alpha=1.5, beta=1.5, seed=1)
+PLAN = dict(kappa=6, K=5, c_p=3.0, alpha=1.5, beta=1.5, seed=1, pool="all")
+POOLS = {"all": 0, "smooth": 1}
 METRIC = "SFTs/sec at N=2^26, s=1000 (p50/p99 latency, vs plain FP64 path and cuFFT; % HBM roofline)"
 N_INPUTS = 16
 FALLBACK_HBM_GBS = 6800.0
@@ -60,6 +61,9 @@ def parse():
     ap.add_argument("--study", choices=["sweep-n", "sweep-s", "noise"], default=None,
                     help="the paper's experiments instead of the bench line (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
+    ap.add_argument("--pool", choices=sorted(POOLS), default="all",
+                    help="prime pool of the plans: all primes, or those whose p - 1 is 13-smooth "
+                         "(Rader's form of the DFTs)")
     ap.add_argument("--precision-trials", type=int, default=10,
                     help="seeded inputs of the precision study compared with the oracle")
     ap.add_argument("--batched-signals", type=int, default=4096)
@@ -71,7 +75,8 @@ def workload_config(args, batch):
         "workload": f"precision study: N={args.N}, s={args.s}, complex64, |c| log-uniform "
                     "[1e-2,1], random phase, SNR 30 dB",
         "N": args.N, "s": args.s, "kappa": PLAN["kappa"], "K": PLAN["K"], "c_p": PLAN["c_p"],
-        "alpha": PLAN["alpha"], "beta": PLAN["beta"], "precision": "fp32 bulk + fp64 refine",
+        "alpha": PLAN["alpha"], "beta": PLAN["beta"], "prime_pool": PLAN["pool"],
+        "precision": "fp32 bulk + fp64 refine",
         "batch_per_step": batch,
         "l2": f"{args.inputs} rotating distinct inputs of {args.N * 8 >> 20} MiB (> 129 MB L2)",
     }
@@ -248,11 +253,15 @@ def profiled_traffic(kernel_tag, digest, key="dram_bytes_per_sft"):
 
 
 def dft_flops(info):
-    """Conventional flop count of the chirp-convolution stage per SFT: two length-M FFTs
-    (5 M log2 M each) plus the pointwise products, for every node subset of every prime and shift."""
+    """Conventional flop count of the DFT stage per SFT, for every node subset of every prime and
+    shift.  Chirp form: two length-M FFTs (5 M log2 M each) plus the pointwise products (6 M + 12 p).
+    Rader's form: two length-(p - 1) FFTs plus the product by V and the h_0 / p term (8 (p - 1))."""
     M = info["fft_size"]
-    per = 2 * 5 * M * math.log2(M) + 6 * M
-    return info["n_shifts"] * info["n_sub"] * sum(per + 12 * p for p in info["primes"])
+    if M == 0:
+        per = [2 * 5 * (p - 1) * math.log2(p - 1) + 8 * (p - 1) for p in info["primes"]]
+    else:
+        per = [2 * 5 * M * math.log2(M) + 6 * M + 12 * p for p in info["primes"]]
+    return info["n_shifts"] * info["n_sub"] * sum(per)
 
 
 # ------------------------------------------------------------------------------------------
@@ -296,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
     def variant(prec):
         return sft.sft_variant_init(precision=prec, kappa=PLAN["kappa"], K=PLAN["K"],
                                     c_p=PLAN["c_p"], alpha=PLAN["alpha"], beta=PLAN["beta"],
-                                    seed=PLAN["seed"])
+                                    seed=PLAN["seed"], pool=POOLS[PLAN["pool"]])
     plans = [sft.sft_plan(N, s, variant(sft.SFT_FP32)) for _ in range(B)]
     info = plans[0].info()
     batch = sft.Batch(plans)
@@ -410,21 +419,25 @@ def run_ours(args, rank, world, local_rank):
         alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         fl = B * dft_flops(info)
         ach = fl / (per_launch_us["chirp_dft"] * 1e-6) / 1e12
-        dft_traffic = profiled_traffic("bluestein_n2p26_s1000",
-                                       source_digest("bluestein.cu", "cplx.cuh", "sft_internal.h"))
-        roof = {"kernel": "bluestein (chirp-convolution DFT)", "bound": "alu", "achieved": ach,
+        rader = info["fft_size"] == 0
+        dft_tag = "rader_n2p26_s1000" if rader else "bluestein_n2p26_s1000"
+        dft_src = ("rader.cu" if rader else "bluestein.cu", "fft_radix.cuh", "cplx.cuh",
+                   "sft_internal.h")
+        dft_traffic = profiled_traffic(dft_tag, source_digest(*dft_src))
+        roof = {"kernel": ("rader (mixed-radix FFT convolution DFT)" if rader
+                           else "bluestein (chirp-convolution DFT)"),
+                "bound": "alu", "achieved": ach,
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
                 "traffic": dft_traffic * B if dft_traffic is not None else None,
                 "algorithmic_flops": fl,
                 "units": f"{B} SFTs x {info['n_shifts'] * info['n_sub'] * info['K']} transforms "
-                         f"of length {info['fft_size']} per launch",
+                         + (f"of lengths p - 1 = {[p - 1 for p in info['primes']]}" if rader
+                            else f"of length {info['fft_size']}") + " per launch",
                 "peak_source": f"{n_sm} SMs (device properties) x 128 FP32 lanes x 2 flop x "
                                "sm_max_mhz"}
         # the pipe that actually limits it: shared-memory wavefronts (ncu count per SFT of the
         # same source, x B) per second against one 128-byte wavefront per SM per clock
-        wav = profiled_traffic("bluestein_n2p26_s1000",
-                               source_digest("bluestein.cu", "cplx.cuh", "sft_internal.h"),
-                               key="smem_wavefronts_per_sft")
+        wav = profiled_traffic(dft_tag, source_digest(*dft_src), key="smem_wavefronts_per_sft")
         if wav is not None:
             wps = B * wav / (per_launch_us["chirp_dft"] * 1e-6)
             peak_w = n_sm * sm_mhz * 1e6
@@ -1121,7 +1134,7 @@ def run_reference(args, rank, world):
     N, s = args.N, args.s
     f = _oracle_input(N, s)
     plan = make_plan(N, s, kappa=PLAN["kappa"], K=PLAN["K"], c_p=PLAN["c_p"],
-                     alpha=PLAN["alpha"], beta=PLAN["beta"], seed=PLAN["seed"])
+                     alpha=PLAN["alpha"], beta=PLAN["beta"], seed=PLAN["seed"], pool=PLAN["pool"])
     nq = len(plan.shifts)
     for w in range(args.warmup):
         ussft_shift(f, plan, plan.shifts[w % nq])
@@ -1148,6 +1161,7 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    PLAN["pool"] = args.pool
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

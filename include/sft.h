@@ -51,6 +51,10 @@ enum { SFT_DMSFT4 = 4, SFT_DMSFT6 = 6 };
 
 typedef enum { SFT_FP32 = 0, SFT_FP64 = 1 } sft_precision;
 typedef enum { SFT_IN_C64 = 0, SFT_IN_C128 = 1 } sft_input_type;
+/* Pool of the randomized inner SFT's primes (sft_variant.pool). */
+typedef enum { SFT_POOL_ALL = 0, SFT_POOL_SMOOTH = 1 } sft_pool;
+/* How the length-p_j DFTs of the measurements are taken (sft_variant.dft). */
+typedef enum { SFT_DFT_AUTO = 0, SFT_DFT_CHIRP = 1, SFT_DFT_RADER = 2 } sft_dft;
 
 /*
  * Method parameters.  Fill with sft_variant_init() and override fields.
@@ -81,6 +85,18 @@ typedef enum { SFT_IN_C64 = 0, SFT_IN_C128 = 1 } sft_input_type;
  *             DFTs' rounding, about 1e-6 of the largest bin, instead of meeting 1e-5 relative).
  *             Plans of one batch must agree on it.
  *  input      element type of f: SFT_IN_C64 (interleaved float re,im) or SFT_IN_C128 (double).
+ *  pool       randomized inner SFT only: SFT_POOL_ALL draws the K primes from the 4K smallest
+ *             primes >= max(ceil(c_p s), 5); SFT_POOL_SMOOTH from the 4K smallest such primes
+ *             whose p - 1 has no prime factor above 13, so that every length-p DFT can be taken
+ *             by Rader's algorithm (below).  Any K distinct primes serve the randomized inner SFT
+ *             (Lemma SFT_Ident_Coef_Est_in_Noise); the smooth pool reaches a little higher (its
+ *             mean prime is about 1.15 c_p s near c_p s = 3000 against 1.03 c_p s).
+ *  dft        how the length-p DFTs are taken.  SFT_DFT_CHIRP: a chirp convolution (Bluestein)
+ *             over an FFT of length r 2^k >= 2p - 1 (p <= 8192 FP32, 4096 FP64).
+ *             SFT_DFT_RADER: Rader's algorithm, a cyclic convolution of length p - 1 over a
+ *             mixed-radix FFT of that length (every p - 1 must be a product of 2, 3, 5, 7, 11,
+ *             13; p <= 13313 FP32, 6657 FP64); about half the work of the chirp form.
+ *             SFT_DFT_AUTO (default): Rader when every p_j allows it, else the chirp form.
  */
 typedef struct {
   int32_t kappa;
@@ -93,6 +109,8 @@ typedef struct {
   uint64_t seed;
   int32_t deterministic;
   int32_t refine_fp64;
+  int32_t pool;
+  int32_t dft;
 } sft_variant;
 
 /*
@@ -126,26 +144,28 @@ typedef struct {
   int64_t nodes;                      /* distinct nodes m = n_sub * sum_j p_j */
   int32_t fft_size;                   /* chirp-convolution length: the smallest of 2^k >= 64,
                                          3 2^k >= 96, 5 2^k >= 640, 7 2^k >= 896 that is
-                                         >= 2 p_K - 1 */
+                                         >= 2 p_K - 1; 0 when the plan uses Rader's form */
   int32_t precision;
   int32_t input;
-  int32_t reserved;
+  int32_t dft;                        /* SFT_DFT_CHIRP or SFT_DFT_RADER: the form in use */
 } sft_plan_desc;
 
 /* Fill *v with the defaults: kappa 6 (DMSFT-6), FP32, complex64 input, K 5, c_p 3,
- * alpha = beta = 1.5, seed 0, randomized inner SFT, refine_fp64 1.  Returns SFT_EINVAL if v is
- * NULL. */
+ * alpha = beta = 1.5, seed 0, randomized inner SFT, refine_fp64 1, SFT_POOL_ALL, SFT_DFT_AUTO.
+ * Returns SFT_EINVAL if v is NULL. */
 sft_status sft_variant_init(sft_variant* v);
 
 /*
  * Build a plan for length-N inputs and sparsity s (Algorithm 1, its set-up lines: c1, c2, L and the
  * shifts q_j = -ceil(N/2) + 1 + (2j - 1) L).
  *  n_shifts      0 = ceil(alpha sqrt(ln N)/2); otherwise that many shifts (must still cover B).
- *  primes        NULL = K primes chosen by v->seed from the 4K smallest primes >= max(c_p s, 5);
+ *  primes        NULL = K primes chosen by v->seed from v->pool (the 4K smallest primes
+ *                >= max(c_p s, 5), or the 4K smallest of those whose p - 1 is 13-smooth);
  *                else n_primes distinct primes (1 <= n_primes <= SFT_MAX_K) used as given.
  *  small_moduli  NULL = the smallest primes, none equal to a p_j, until p_1 prod(t) >= N;
  *                else n_small pairwise-coprime moduli >= 2, coprime to every p_j, p_1 prod >= N.
- * Requires 2 <= N < 2^31, 1 <= s <= N, 2 kappa + 1 <= N, every p_j <= 8192 (FP32) or 4096 (FP64).
+ * Requires 2 <= N < 2^31, 1 <= s <= N, 2 kappa + 1 <= N, and every p_j within the limits of the
+ * DFT form (v->dft: chirp p <= 8192 FP32 / 4096 FP64; Rader p <= 13313 FP32 / 6657 FP64).
  * (Theorem MainTHM is stated for s >= 2; s = 1 is accepted, since Algorithm 1 itself is defined
  * for it: one term per shift, the largest kept.)
  * Allocates the plan's device tables and scratch on the current device (sft_plan_device_bytes).
@@ -177,6 +197,13 @@ sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_de
  */
 sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                              int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);
+
+/* Host only: as sft_choose_moduli with the primes drawn from `pool` (SFT_POOL_ALL gives the same
+ * moduli as sft_choose_moduli; SFT_POOL_SMOOTH the 4K smallest primes >= max(ceil(c_p s), 5) whose
+ * p - 1 has no prime factor above 13). */
+sft_status sft_choose_moduli_pool(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
+                                  int32_t pool, int64_t* primes_out, int32_t* small_out,
+                                  int32_t* n_small_out);
 
 /* Host only: the moduli of the deterministic inner SFT (sft_variant.deterministic = 1) for N, s,
  * c_p: the K smallest primes >= max(ceil(c_p s), 5), K = 2 (s - 1) floor(log_{p_1}(N - 1)) + 1,

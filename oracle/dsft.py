@@ -72,18 +72,49 @@ def primes_from(lo: int, count: int) -> list[int]:
     return out
 
 
-def choose_primes(s: int, K: int, c_p: float, seed: int) -> list[int]:
-    """K distinct primes drawn by a seeded partial Fisher-Yates shuffle from the 4K smallest primes
+SMOOTH_FACTORS = (2, 3, 5, 7, 11, 13)
+
+
+def is_smooth(n: int, factors=SMOOTH_FACTORS) -> bool:
+    """True when n >= 1 has no prime factor outside `factors` (trial division)."""
+    if n < 1:
+        return False
+    for t in factors:
+        while n % t == 0:
+            n //= t
+    return n == 1
+
+
+def smooth_primes_from(lo: int, count: int) -> list[int]:
+    """The `count` smallest primes p >= lo whose p - 1 has no prime factor above 13."""
+    out, n = [], max(3, lo)
+    while len(out) < count:
+        if is_prime(n) and is_smooth(n - 1):
+            out.append(n)
+        n += 1
+    return out
+
+
+def choose_primes(s: int, K: int, c_p: float, seed: int, pool: str = "all") -> list[int]:
+    """K distinct primes drawn by a seeded partial Fisher-Yates shuffle from a pool of 4K primes
     >= max(ceil(c_p * s), 5); returned ascending.  The Monte Carlo variant reads a random subset of
-    the deterministic algorithm's moduli (Lemma SFT_Ident_Coef_Est_in_Noise, second paragraph)."""
+    the deterministic algorithm's moduli (Lemma SFT_Ident_Coef_Est_in_Noise, second paragraph).
+    pool "all": the 4K smallest primes; pool "smooth" (a choice of this build): the 4K smallest
+    primes whose p - 1 has no prime factor above 13 (the measurements are then DFTs of prime
+    length p whose p - 1 is a product of small radices)."""
     lo = max(int(math.ceil(c_p * s)), 5)
-    pool = primes_from(lo, 4 * K)
+    if pool == "all":
+        cands = primes_from(lo, 4 * K)
+    elif pool == "smooth":
+        cands = smooth_primes_from(lo, 4 * K)
+    else:
+        raise ValueError(pool)
     state = seed & MASK64
     for i in range(K):
         state, r = splitmix64(state)
-        j = i + (r % (len(pool) - i))
-        pool[i], pool[j] = pool[j], pool[i]
-    return sorted(pool[:K])
+        j = i + (r % (len(cands) - i))
+        cands[i], cands[j] = cands[j], cands[i]
+    return sorted(cands[:K])
 
 
 def deterministic_primes(N: int, s: int, c_p: float) -> list[int]:
@@ -143,7 +174,8 @@ def ceil_half(N: int) -> int:
 
 def make_plan(N: int, s: int, kappa: int = 6, alpha: float = 1.5, beta: float = 1.5,
               K: int = 5, c_p: float = 3.0, seed: int = 0, primes=None, small=None,
-              n_shifts: int | None = None, deterministic: bool = False) -> Plan:
+              n_shifts: int | None = None, deterministic: bool = False,
+              pool: str = "all") -> Plan:
     """c1 = beta sqrt(ln N) / N, c2 = alpha sqrt(ln N) / 2, L = ceil(N / (alpha sqrt(ln N))),
     q_j = -ceil(N/2) + 1 + (2j - 1) L for j = 1..ceil(c2)  (Algorithm 1)."""
     if N < 2 or not (1 <= s <= N):
@@ -158,7 +190,8 @@ def make_plan(N: int, s: int, kappa: int = 6, alpha: float = 1.5, beta: float = 
         raise ValueError("the bands [q-L, q+L) do not cover B")
     shifts = [-ceil_half(N) + 1 + (2 * j - 1) * L for j in range(1, nq + 1)]
     if primes is None:
-        primes = deterministic_primes(N, s, c_p) if deterministic else choose_primes(s, K, c_p, seed)
+        primes = (deterministic_primes(N, s, c_p) if deterministic
+                  else choose_primes(s, K, c_p, seed, pool))
     primes = sorted(int(p) for p in primes)
     if small is None:
         small = choose_small_moduli(N, primes)

@@ -17,6 +17,8 @@ SFT_OK, SFT_EINVAL, SFT_ENOMEM, SFT_ECUDA, SFT_ETIMEOUT, SFT_EBUSY = range(6)
 SFT_DMSFT4, SFT_DMSFT6 = 4, 6
 SFT_FP32, SFT_FP64 = 0, 1
 SFT_IN_C64, SFT_IN_C128 = 0, 1
+SFT_POOL_ALL, SFT_POOL_SMOOTH = 0, 1
+SFT_DFT_AUTO, SFT_DFT_CHIRP, SFT_DFT_RADER = 0, 1, 2
 SFT_MAX_K, SFT_MAX_SMALL, SFT_MAX_SHIFTS = 512, 12, 32
 BUF_SAMPLES, BUF_BINS, BUF_CAND, BUF_RESID, BUF_COUNTERS, BUF_VOTED = range(6)
 
@@ -34,7 +36,8 @@ class sft_variant(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("input", ctypes.c_int32), ("K", ctypes.c_int32), ("c_p", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("deterministic", ctypes.c_int32), ("refine_fp64", ctypes.c_int32)]
+                ("deterministic", ctypes.c_int32), ("refine_fp64", ctypes.c_int32),
+                ("pool", ctypes.c_int32), ("dft", ctypes.c_int32)]
 
 
 class sft_plan_desc(ctypes.Structure):
@@ -45,7 +48,7 @@ class sft_plan_desc(ctypes.Structure):
                 ("shifts", ctypes.c_int64 * SFT_MAX_SHIFTS), ("L", ctypes.c_int64),
                 ("c1", ctypes.c_double), ("nodes", ctypes.c_int64), ("fft_size", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("input", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("dft", ctypes.c_int32)]
 
 
 class sft_tuning(ctypes.Structure):
@@ -160,6 +163,11 @@ EXPORTS = {
                                          ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32)]),
+    "sft_choose_moduli_pool": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32)]),
 }
 
 
@@ -269,6 +277,18 @@ def sft_choose_moduli(N: int, s: int, K: int = 5, c_p: float = 3.0, seed: int = 
     return list(pr), list(sm[: ns.value])
 
 
+def sft_choose_moduli_pool(N: int, s: int, K: int = 5, c_p: float = 3.0, seed: int = 0,
+                           pool: int = SFT_POOL_ALL):
+    """Host-only: the (primes, small moduli) sft_plan would choose from the given prime pool."""
+    pr = (ctypes.c_int64 * K)()
+    sm = (ctypes.c_int32 * SFT_MAX_SMALL)()
+    ns = ctypes.c_int32()
+    _check(load().sft_choose_moduli_pool(int(N), int(s), int(K), float(c_p),
+                                         int(seed) & (2**64 - 1), int(pool), pr, sm,
+                                         ctypes.byref(ns)))
+    return list(pr), list(sm[: ns.value])
+
+
 def sft_choose_moduli_deterministic(N: int, s: int, c_p: float = 3.0):
     """Host-only: the (primes, small moduli) of the deterministic inner SFT."""
     pr = (ctypes.c_int64 * SFT_MAX_K)()
@@ -288,7 +308,7 @@ def sft_plan_info(plan: Plan) -> dict:
         "n_shifts": d.n_shifts, "n_sub": d.n_sub, "primes": list(d.primes[: d.K]),
         "small": list(d.small[: d.n_small]), "shifts": list(d.shifts[: d.n_shifts]),
         "L": d.L, "c1": d.c1, "nodes": d.nodes, "fft_size": d.fft_size,
-        "precision": d.precision, "input": d.input,
+        "precision": d.precision, "input": d.input, "dft": d.dft,
     }
 
 

@@ -71,6 +71,7 @@ int signal_blocks(const DevPlan& d, int kind, const sft_tuning& tu) {
     case kStFinalRank: return rank_blocks(d, kind);
     case kStReest: return d.prec == SFT_FP32 ? d.nq * d.K * d.nchunk : 0;
     case kStRefine: return d.prec == SFT_FP32 ? (d.s + kRefineThreads - 1) / kRefineThreads : 0;
+    case kStRader: return d.rader ? d.nq * d.K * d.nsub : 0;
     default:
       if (kind >= kStBluestein0 && kind < kStCount) {
         const int M = fft_stage_length(kind);
@@ -88,6 +89,7 @@ LaunchSet single_launch_set(const DevPlan& d) {
     ls.blk[k] = nullptr;
   }
   ls.pmax = d.pmax;
+  ls.rlmax = d.rader ? d.rLmax : 0;
   ls.kmax = d.K;
   return ls;
 }
@@ -191,6 +193,8 @@ sft_status sft_variant_init(sft_variant* v) {
   v->seed = 0;
   v->deterministic = 0;
   v->refine_fp64 = 1;
+  v->pool = SFT_POOL_ALL;
+  v->dft = SFT_DFT_AUTO;
   return SFT_OK;
 }
 
@@ -251,6 +255,7 @@ sft_status sft_plan_info(sft_plan_t plan, sft_plan_desc* o) {
   for (int i = 0; i < d.nq; ++i) o->shifts[i] = d.q[i];
   o->L = d.L; o->c1 = d.c1; o->nodes = d.m; o->fft_size = d.fftM;
   o->precision = d.prec; o->input = d.input;
+  o->dft = d.rader ? SFT_DFT_RADER : SFT_DFT_CHIRP;
   return SFT_OK;
 }
 
@@ -339,6 +344,12 @@ int64_t sft_plan_launches(sft_plan_t plan) { return plan ? plan->P.launches : 0;
 sft_status sft_choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
                              int64_t* primes_out, int32_t* small_out, int32_t* n_small_out) {
   return sft::choose_moduli(N, s, K, c_p, seed, primes_out, small_out, n_small_out);
+}
+
+sft_status sft_choose_moduli_pool(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
+                                  int32_t pool, int64_t* primes_out, int32_t* small_out,
+                                  int32_t* n_small_out) {
+  return sft::choose_moduli(N, s, K, c_p, seed, primes_out, small_out, n_small_out, pool);
 }
 
 sft_status sft_choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t* primes_out,

@@ -57,13 +57,24 @@ int64_t inv_mod(int64_t a, int64_t m) {
   return ((x % m) + m) % m;
 }
 
-// The inner SFT's K primes: a seeded partial Fisher-Yates draw from the 4K smallest primes
-// >= max(ceil(c_p s), 5), returned ascending (randomized inner SFT reading a random subset of moduli).
-std::vector<int32_t> choose_primes(int32_t s, int K, double c_p, uint64_t seed) {
+// True when n >= 1 has no prime factor above 13.
+bool smooth13(int64_t n) {
+  if (n < 1) return false;
+  for (int64_t t : {2, 3, 5, 7, 11, 13})
+    while (n % t == 0) n /= t;
+  return n == 1;
+}
+
+// The inner SFT's K primes: a seeded partial Fisher-Yates draw from a pool of 4K primes
+// >= max(ceil(c_p s), 5), returned ascending (randomized inner SFT reading a random subset of
+// moduli).  SFT_POOL_ALL: the 4K smallest such primes; SFT_POOL_SMOOTH: the 4K smallest whose
+// p - 1 has no prime factor above 13.
+std::vector<int32_t> choose_primes(int32_t s, int K, double c_p, uint64_t seed,
+                                   int pool_kind = SFT_POOL_ALL) {
   int64_t lo = std::max<int64_t>((int64_t)ceil(c_p * (double)s), 5);
   std::vector<int64_t> pool;
   for (int64_t n = lo; (int)pool.size() < 4 * K; ++n)
-    if (is_prime(n)) pool.push_back(n);
+    if (is_prime(n) && (pool_kind != SFT_POOL_SMOOTH || smooth13(n - 1))) pool.push_back(n);
   uint64_t state = seed;
   for (int i = 0; i < K; ++i) {
     uint64_t r = splitmix64(&state);
@@ -158,6 +169,84 @@ cd expi_turns(int64_t num, int64_t den) {
   return cd(cos(a), sin(a));
 }
 
+// Forward DFT of any length whose prime factors are small, by recursive decimation in time on
+// the smallest prime factor r: with A_t the transforms of a[r n + t] (length m = L / r),
+// X[k + m u] = sum_t e^{-2 pi i t (k + m u) / L} A_t[k].  Twiddles are reduced exactly.
+void host_fft_mixed(std::vector<cd>& a) {
+  const int64_t L = (int64_t)a.size();
+  if (L <= 1) return;
+  int64_t r = 2;
+  while (L % r) ++r;
+  const int64_t m = L / r;
+  std::vector<std::vector<cd>> A(r, std::vector<cd>(m));
+  for (int64_t t = 0; t < r; ++t) {
+    for (int64_t n = 0; n < m; ++n) A[t][n] = a[r * n + t];
+    host_fft_mixed(A[t]);
+  }
+  for (int64_t k = 0; k < m; ++k)
+    for (int64_t u = 0; u < r; ++u) {
+      const int64_t kk = k + m * u;
+      cd x = A[0][k];
+      for (int64_t t = 1; t < r; ++t) x += expi_turns(-t * kk, L) * A[t][k];
+      a[kk] = x;
+    }
+}
+
+// Pass schedule of a length-L mixed-radix FFT for Rader's form: the radices multiply to L and each
+// is one of the in-register DFTs (2, 3, 4, 5, 6, 7, 8, 10, 11, 12, 13, 14, 16): every 7, 5 and 3
+// takes a factor 2 (14, 10) or 4 (12) or 2 (6) while any is left, 11 and 13 stand alone, the
+// remaining powers of two go in radix-16 passes and one last 8, 4 or 2; largest radix first.
+// False when L has a prime factor above 13, L < 2 or the schedule is too long.
+bool rader_schedule(int L, std::vector<int>& rad) {
+  rad.clear();
+  if (L < 2) return false;
+  int e[6] = {0, 0, 0, 0, 0, 0};
+  const int f[6] = {2, 3, 5, 7, 11, 13};
+  int n = L;
+  for (int i = 0; i < 6; ++i)
+    while (n % f[i] == 0) { n /= f[i]; ++e[i]; }
+  if (n != 1) return false;
+  int a2 = e[0];
+  for (int i = 0; i < e[3]; ++i) { if (a2 > 0) { rad.push_back(14); --a2; } else rad.push_back(7); }
+  for (int i = 0; i < e[2]; ++i) { if (a2 > 0) { rad.push_back(10); --a2; } else rad.push_back(5); }
+  for (int i = 0; i < e[1]; ++i) {
+    if (a2 >= 2) { rad.push_back(12); a2 -= 2; }
+    else if (a2 == 1) { rad.push_back(6); --a2; }
+    else rad.push_back(3);
+  }
+  for (int i = 0; i < e[4]; ++i) rad.push_back(11);
+  for (int i = 0; i < e[5]; ++i) rad.push_back(13);
+  while (a2 >= 4) { rad.push_back(16); a2 -= 4; }
+  if (a2 > 0) rad.push_back(1 << a2);
+  std::sort(rad.begin(), rad.end(), [](int x, int y) { return x > y; });
+  return (int)rad.size() <= kRaderMaxPasses;
+}
+
+// Smallest primitive root modulo the prime p (p - 1 13-smooth): g with g^((p-1)/q) != 1 for every
+// prime q dividing p - 1.
+int64_t pow_mod(int64_t b, int64_t e, int64_t m) {
+  int64_t r = 1 % m;
+  b %= m;
+  while (e) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return r;
+}
+int64_t primitive_root(int64_t p) {
+  std::vector<int64_t> qs;
+  int64_t n = p - 1;
+  for (int64_t q : {2, 3, 5, 7, 11, 13})
+    if (n % q == 0) { qs.push_back(q); while (n % q == 0) n /= q; }
+  for (int64_t g = 2; g < p; ++g) {
+    bool ok = true;
+    for (int64_t q : qs) ok = ok && pow_mod(g, (p - 1) / q, p) != 1;
+    if (ok) return g;
+  }
+  return 1;   // p = 2
+}
+
 template <typename T>
 void put(std::vector<char>& blob, size_t off, const std::vector<cd>& v, bool fp64) {
   if (fp64) {
@@ -226,7 +315,8 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   } else {
     if (v->K < 1 || v->K > kMaxK) { set_error("K must be 1.." + std::to_string(kMaxK)); return SFT_EINVAL; }
     if (v->c_p * (double)s > 1.0e6) { set_error("c_p * s too large"); return SFT_EINVAL; }
-    primes = choose_primes(s, v->K, v->c_p, v->seed);
+    if (v->pool != SFT_POOL_ALL && v->pool != SFT_POOL_SMOOTH) { set_error("bad prime pool"); return SFT_EINVAL; }
+    primes = choose_primes(s, v->K, v->c_p, v->seed, v->pool);
   }
   std::vector<int32_t> small;
   if (small_in) {
@@ -257,18 +347,38 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   for (int32_t t : small) nsub += t - 1;
   if (nsub > kMaxSub) { set_error("too many node subsets (sum of t_l - 1 must be < 128)"); return SFT_EINVAL; }
   const int32_t pmax = primes.back();
-  const int M = fft_length(2 * (int64_t)pmax - 1, fp64 ? kMaxFFT64 : kMaxFFT32);
-  if (M == 0) {
-    set_error(fp64 ? "FP64 plans need every p_j <= 4096" : "FP32 plans need every p_j <= 8192");
+  if (v->dft != SFT_DFT_AUTO && v->dft != SFT_DFT_CHIRP && v->dft != SFT_DFT_RADER) {
+    set_error("bad DFT form"); return SFT_EINVAL;
+  }
+  // Rader's form when every p_j - 1 has a pass schedule and the two buffers fit shared memory
+  std::vector<std::vector<int>> rsched(primes.size());
+  bool rader_ok = v->dft != SFT_DFT_CHIRP;
+  for (size_t j = 0; rader_ok && j < primes.size(); ++j)
+    rader_ok = primes[j] >= 3 && (primes[j] - 1) <= (fp64 ? kRaderMaxL64 : kRaderMaxL32) &&
+               rader_schedule(primes[j] - 1, rsched[j]);
+  if (v->dft == SFT_DFT_RADER && !rader_ok) {
+    set_error(std::string("Rader's form needs every p_j - 1 to have no prime factor above 13 and "
+                          "p_j <= ") + (fp64 ? "6801 (FP64)" : "13601 (FP32)"));
     return SFT_EINVAL;
   }
-  const int logM = fft_log2(M);
+  const bool rader = rader_ok;
+  const int M = rader ? 0 : fft_length(2 * (int64_t)pmax - 1, fp64 ? kMaxFFT64 : kMaxFFT32);
+  if (!rader && M == 0) {
+    set_error(fp64 ? "FP64 plans need every p_j <= 4096 (chirp form; Rader's form reaches 6801 "
+                     "when every p_j - 1 is 13-smooth)"
+                   : "FP32 plans need every p_j <= 8192 (chirp form; Rader's form reaches 13601 "
+                     "when every p_j - 1 is 13-smooth)");
+    return SFT_EINVAL;
+  }
+  const int logM = rader ? 0 : fft_log2(M);
 
   // ---- fill the device-plan scalars
   d.N = N; d.s = s; d.kappa = v->kappa; d.K = K; d.nT = nT; d.nq = (int32_t)nq; d.nsub = nsub;
   d.prec = v->precision; d.input = v->input;
   d.refine = (v->precision == SFT_FP32 && v->refine_fp64) ? 1 : 0;
   d.fftM = M; d.fftLog2 = logM; d.pmax = pmax;
+  d.rader = rader ? 1 : 0;
+  d.rLmax = rader ? pmax - 1 : 0;
   int64_t sump = 0;
   for (int j = 0; j < K; ++j) {
     d.p[j] = primes[j];
@@ -333,6 +443,11 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   const size_t o_wp = off;     off = align256(off + (size_t)K * pmax * 8);
   const size_t o_gar = off;    off = align256(off + (size_t)K * std::max(nT, 1) * 4);
   const size_t o_pinv = off;   off = align256(off + (size_t)K * std::max(nT, 1) * 4);
+  const size_t rk = rader ? (size_t)K : 0;
+  const size_t o_rsch = off;   off = align256(off + rk * kRaderSched * 4);
+  const size_t o_rperm = off;  off = align256(off + rk * 2 * pmax * 4);
+  const size_t o_rV = off;     off = align256(off + rk * pmax * cs);
+  const size_t o_rtw = off;    off = align256(off + rk * pmax * cs);
   const size_t table_bytes = off;
   std::vector<char> blob(table_bytes, 0);
   {
@@ -346,13 +461,14 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
     std::vector<cd> ch((size_t)K * pmax, cd(0, 0)), vh((size_t)K * M), wp((size_t)K * pmax, cd(0, 0));
     for (int j = 0; j < K; ++j) {
       const int64_t p = primes[j];
+      for (int64_t n = 0; n < p; ++n) wp[(size_t)j * pmax + n] = expi_turns(-n, p);
+      if (rader) continue;
       std::vector<cd> V(M, cd(0, 0));
       for (int64_t n = 0; n < p; ++n) {
         cd w = expi_turns(-((n * n) % (2 * p)), 2 * p);  // exp(-pi i n^2 / p)
         ch[(size_t)j * pmax + n] = w;
         V[n] = std::conj(w);
         if (n > 0) V[M - n] = std::conj(w);
-        wp[(size_t)j * pmax + n] = expi_turns(-n, p);
       }
       host_fft(V);
       for (int n = 0; n < M; ++n) vh[(size_t)j * M + n] = V[n] / ((double)M * (double)p);
@@ -360,6 +476,48 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
     put<cd>(blob, o_chirp, ch, fp64);
     put<cd>(blob, o_vhat, vh, fp64);
     put<cd>(blob, o_wp, wp, false);
+  }
+  if (rader) {
+    // Rader's form (per prime): L = p - 1, g a primitive root; a_n = h_{g^n}, b_n = e^{-2 pi i g^{-n} / p}
+    // and E_{g^{-m}} = h_0 / p + (a (*) b)[m] / p (cyclic convolution), E_0 = (h_0 + sum_n a_n) / p.
+    int32_t* sch = reinterpret_cast<int32_t*>(blob.data() + o_rsch);
+    int32_t* perm = reinterpret_cast<int32_t*>(blob.data() + o_rperm);
+    std::vector<cd> rv((size_t)K * pmax, cd(0, 0)), rt((size_t)K * pmax, cd(1, 0));
+    for (int j = 0; j < K; ++j) {
+      const int64_t p = primes[j], L = p - 1;
+      const int64_t g = primitive_root(p), ginv = pow_mod(g, p - 2, p);
+      int32_t* pin = perm + (size_t)j * 2 * pmax;
+      int32_t* pout = pin + pmax;
+      int64_t x = 1, y = 1;
+      std::vector<cd> b(L);
+      for (int64_t n = 0; n < L; ++n) {
+        pin[n] = (int32_t)x;                 // g^n mod p
+        pout[n] = (int32_t)y;                // g^{-n} mod p
+        b[n] = expi_turns(-y, p);
+        x = x * g % p;
+        y = y * ginv % p;
+      }
+      host_fft_mixed(b);
+      for (int64_t k = 0; k < L; ++k) rv[(size_t)j * pmax + k] = b[k] / ((double)p * (double)L);
+      const std::vector<int>& rad = rsched[j];
+      int32_t* sj = sch + (size_t)j * kRaderSched;
+      sj[0] = (int32_t)rad.size();
+      int64_t span = 1, toff = 0;
+      for (size_t i = 0; i < rad.size(); ++i) {
+        const int R = rad[i];
+        sj[1 + i] = R;
+        sj[16 + i] = (int32_t)toff;
+        for (int row = 0; row < fft_tw_rows(R); ++row)
+          for (int64_t k = 0; k < span; ++k)
+            rt[(size_t)j * pmax + toff + (size_t)row * span + k] =
+                expi_turns(-(int64_t)fft_tw_exp(row) * k, span * R);
+        toff += (int64_t)fft_tw_rows(R) * span;
+        span *= R;
+      }
+      if (toff > pmax) { set_error("internal: Rader twiddle rows overflow"); return SFT_EINVAL; }
+    }
+    put<cd>(blob, o_rV, rv, fp64);
+    put<cd>(blob, o_rtw, rt, fp64);
   }
   {
     std::vector<cd> fw(M, cd(1, 0));
@@ -433,6 +591,12 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   d.twsmall = base + o_tws; d.wp32 = reinterpret_cast<const float2*>(base + o_wp);
   d.garner = reinterpret_cast<const int32_t*>(base + o_gar);
   d.pinv = reinterpret_cast<const int32_t*>(base + o_pinv);
+  if (rader) {
+    d.rsched = reinterpret_cast<const int32_t*>(base + o_rsch);
+    d.rperm = reinterpret_cast<const int32_t*>(base + o_rperm);
+    d.rV = base + o_rV;
+    d.rtw = base + o_rtw;
+  }
   d.samples = base + o_samples; d.bins = base + o_bins;
   d.cand = reinterpret_cast<int64_t*>(base + o_cand);
   d.resid = reinterpret_cast<uint8_t*>(base + o_resid);
@@ -479,11 +643,12 @@ sft_status choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t
 }
 
 sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
-                         int64_t* primes_out, int32_t* small_out, int32_t* n_small_out) {
+                         int64_t* primes_out, int32_t* small_out, int32_t* n_small_out, int pool) {
   if (!primes_out || !small_out || !n_small_out) { set_error("NULL output"); return SFT_EINVAL; }
   if (N < 2 || N >= (int64_t(1) << 31) || s < 1 || s > N) { set_error("need 2 <= N < 2^31, 1 <= s <= N"); return SFT_EINVAL; }
   if (K < 1 || K > kMaxK || !(c_p > 0.0) || c_p * (double)s > 1.0e6) { set_error("bad K or c_p"); return SFT_EINVAL; }
-  std::vector<int32_t> pr = choose_primes(s, K, c_p, seed);
+  if (pool != SFT_POOL_ALL && pool != SFT_POOL_SMOOTH) { set_error("bad prime pool"); return SFT_EINVAL; }
+  std::vector<int32_t> pr = choose_primes(s, K, c_p, seed, pool);
   std::vector<int32_t> sm = choose_small(N, pr);
   if ((int)sm.size() > kMaxT) { set_error("too many small moduli"); return SFT_EINVAL; }
   for (int j = 0; j < K; ++j) primes_out[j] = pr[j];

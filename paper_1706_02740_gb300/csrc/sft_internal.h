@@ -20,6 +20,13 @@ constexpr int kMaxSub = 128;              // node subsets per prime: 1 + sum_l (
 constexpr int kMaxFFT32 = 16384;          // chirp convolution length, FP32 (128 KiB of smem)
 constexpr int kMaxFFT64 = 8192;           // FP64 (128 KiB of smem)
 constexpr int64_t kNoFreq = INT64_MIN;    // "no frequency" marker in candidate arrays
+// Rader's form: cyclic convolutions of length L = p - 1 over two shared-memory buffers of
+// rader_buf(L) elements each (one transform per CTA).
+constexpr int kRaderMaxL32 = 13600;
+constexpr int kRaderMaxL64 = 6800;
+constexpr int kRaderSched = 32;           // per prime: [0] passes, [1..15] radices, [16..30] row offsets
+constexpr int kRaderMaxPasses = 15;
+__host__ __device__ constexpr int rader_buf(int L) { return L + (L - 1) / 16; }
 
 // Record of one voted frequency of one shift (written by the vote/median kernel).
 struct Voted {
@@ -45,7 +52,10 @@ struct DevPlan {
   int32_t refine;             // FP32 path: re-estimate the winners (sft_variant.refine_fp64)
   int64_t m;                  // distinct nodes: nsub * sum_j p_j
   int32_t Ptot;               // sum_j p_j
-  int32_t fftM, fftLog2;      // chirp convolution length (r 2^k, r = 1, 3, 5, 7), floor(log2 fftM)
+  int32_t fftM, fftLog2;      // chirp convolution length (r 2^k, r = 1, 3, 5, 7), floor(log2 fftM);
+                              // 0 when the plan takes Rader's form
+  int32_t rader;              // 1: the length-p_j DFTs by Rader's algorithm (every p_j - 1 13-smooth)
+  int32_t rLmax;              // largest p_j - 1 of a Rader plan
   int32_t p[kMaxK];
   int64_t nodeoff[kMaxK + 1]; // first node of prime j
   int32_t poff[kMaxK + 1];    // first bin of prime j
@@ -76,6 +86,10 @@ struct DevPlan {
   const float2* wp32;         // [K][pmax] exp(-2 pi i n / p_j) for the FP32 re-estimation
   const int32_t* garner;      // [K][nT] (p_j t_1 .. t_{l-1})^{-1} mod t_l
   const int32_t* pinv;        // [K][nT] p_j^{-1} mod t_l
+  const int32_t* rsched;      // [K][kRaderSched] Rader pass schedule of p_j - 1
+  const int32_t* rperm;       // [K][2][pmax]: g^n mod p_j and g^{-n} mod p_j, n < p_j - 1
+  const void* rV;             // [K][pmax]: FFT(b) / (p (p - 1)), b_n = e^{-2 pi i g^{-n} / p} (prec type)
+  const void* rtw;            // [K][pmax]: twiddle rows of the length p_j - 1 FFT passes (prec type)
   int32_t pmax;
   // scratch
   void* samples;              // [nq][m] prec complex
@@ -164,6 +178,7 @@ enum StageKind {
   kStReest,          // shifts * K * chunks
   kStRefine,         // s / 64
   kStFinalRank,      // rank fallback of the final order
+  kStRader,          // Rader's form: one transform per block
   kStBluestein0,     // + log2(M) - 6: chirp-convolution lengths 2^k, 64..16384
   kStBluestein3 = kStBluestein0 + 9,   // + log2(M / 96): lengths M = 3 2^k, 96..12288
   kStBluestein5 = kStBluestein3 + 8,   // + log2(M / 640): lengths M = 5 2^k, 640..10240
@@ -177,6 +192,7 @@ struct LaunchSet {
   int32_t blocks[kStCount];
   const int32_t* blk[kStCount];
   int32_t pmax;               // largest prime over the signals (shared-memory sizing)
+  int32_t rlmax;              // largest p - 1 over the signals in Rader's form (0: none)
   int32_t kmax;               // most prime moduli of any signal (per-thread median arrays)
   sft_tuning tune;            // launch geometry (block shapes; never changes results)
 };
@@ -333,6 +349,8 @@ cudaError_t launch_resample(const DevPlan& d0, const BatchView& bv, const Launch
                             cudaStream_t st);
 cudaError_t launch_bluestein(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
                              cudaStream_t st, int* launched);
+cudaError_t launch_rader(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
+                         cudaStream_t st, int* launched);
 cudaError_t launch_identify(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
                             cudaStream_t st);
 cudaError_t launch_vote(const DevPlan& d0, const BatchView& bv, const LaunchSet& ls,
@@ -378,7 +396,8 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
                       int32_t n_small, DeviceMemory* mem = nullptr);
 void free_plan(Plan* P);
 sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t seed,
-                         int64_t* primes_out, int32_t* small_out, int32_t* n_small_out);
+                         int64_t* primes_out, int32_t* small_out, int32_t* n_small_out,
+                         int pool = SFT_POOL_ALL);
 sft_status choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t* primes_out,
                                        int32_t* K_out, int32_t* small_out, int32_t* n_small_out);
 

@@ -12,11 +12,12 @@ FP32, FP64 = 0, 1
 
 
 def run_gpu(sft, N, s, f, prec=FP32, kappa=6, K=5, c_p=3.0, seed=0, primes=None, small=None,
-            input_type=None, n_shifts=0, keep=False):
+            input_type=None, n_shifts=0, keep=False, pool=0, dft=0):
     import torch
     if input_type is None:
         input_type = 0 if f.dtype == np.complex64 else 1
-    v = sft.sft_variant_init(precision=prec, kappa=kappa, K=K, c_p=c_p, seed=seed, input=input_type)
+    v = sft.sft_variant_init(precision=prec, kappa=kappa, K=K, c_p=c_p, seed=seed, input=input_type,
+                             pool=pool, dft=dft)
     plan = sft.sft_plan(N, s, v, n_shifts=n_shifts, primes=primes, small_moduli=small)
     ft = torch.from_numpy(np.ascontiguousarray(f)).to("cuda")
     w, c, n = sft.execute_torch(plan, ft)

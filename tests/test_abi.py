@@ -35,8 +35,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_sizes_match_header_layout():
-    # sft_variant: 4 x int32, 3 x double, uint64, 2 x int32
-    assert ctypes.sizeof(sft.sft_variant) == 56
+    # sft_variant: 4 x int32, 3 x double, uint64, 4 x int32
+    assert ctypes.sizeof(sft.sft_variant) == 64
     assert sft.SFT_MAX_K == 512
     assert ctypes.sizeof(sft.sft_plan_desc) == 8 + 6 * 4 + 512 * 8 + 12 * 4 + 32 * 8 + 8 + 8 + 8 + 16
 
@@ -52,7 +52,7 @@ def test_tuning_layout_and_defaults(lib):
 
 
 def test_server_structs_and_config_defaults(lib):
-    assert ctypes.sizeof(sft.sft_server_config) == 8 + 4 + 4 + 56 + 13 * 4 + 4   # + tail padding
+    assert ctypes.sizeof(sft.sft_server_config) == 8 + 4 + 4 + 64 + 13 * 4 + 4   # + tail padding
     assert ctypes.sizeof(sft.sft_request_info) == 4 * 4 + 2 * 8
     assert ctypes.sizeof(sft.sft_server_stats) == 8 * 8 + 3 * 8 + 2 * 4
     cfg = sft.sft_server_config()
@@ -95,6 +95,7 @@ def test_variant_defaults(lib):
     v = sft.sft_variant_init()
     assert (v.kappa, v.precision, v.input, v.K) == (6, 0, 0, 5)
     assert (v.c_p, v.alpha, v.beta, v.seed, v.deterministic) == (3.0, 1.5, 1.5, 0, 0)
+    assert (v.refine_fp64, v.pool, v.dft) == (1, sft.SFT_POOL_ALL, sft.SFT_DFT_AUTO)
 
 
 @pytest.mark.parametrize("N,s,K,c_p,seed", [(2 ** 16, 8, 5, 4.0, 0), (2 ** 22, 64, 5, 3.0, 7),
@@ -104,6 +105,34 @@ def test_moduli_choice_matches_oracle(lib, N, s, K, c_p, seed):
     primes, small = sft.sft_choose_moduli(N, s, K, c_p, seed)
     assert primes == O.choose_primes(s, K, c_p, seed)
     assert small == O.choose_small_moduli(N, primes)
+
+
+@pytest.mark.parametrize("N,s,K,c_p,seed", [(2 ** 16, 8, 5, 4.0, 0), (2 ** 26, 1000, 5, 3.0, 1),
+                                            (2 ** 26, 4000, 9, 2.5, 3), (4194301, 64, 7, 3.0, 2),
+                                            (1000003, 3, 3, 10.0, 2 ** 63 + 5)])
+def test_smooth_pool_choice_matches_oracle(lib, N, s, K, c_p, seed):
+    primes, small = sft.sft_choose_moduli_pool(N, s, K, c_p, seed, sft.SFT_POOL_SMOOTH)
+    assert primes == O.choose_primes(s, K, c_p, seed, "smooth")
+    assert all(O.is_smooth(p - 1) for p in primes)
+    assert small == O.choose_small_moduli(N, primes)
+    assert sft.sft_choose_moduli_pool(N, s, K, c_p, seed, sft.SFT_POOL_ALL) == \
+        sft.sft_choose_moduli(N, s, K, c_p, seed)
+
+
+def test_dft_form_limits_are_checked_on_the_host(lib):
+    # Rader's form needs every p_j - 1 13-smooth: 3011 - 1 = 2 5 7 43 is refused
+    with pytest.raises(sft.SftError) as e:
+        sft.sft_plan(2 ** 20, 100, sft.sft_variant_init(dft=sft.SFT_DFT_RADER), primes=[3001, 3011])
+    assert e.value.status == sft.SFT_EINVAL and "13" in sft.sft_last_error()
+    # beyond the chirp form's 8192 only Rader's form reaches (FP32): 12289 - 1 = 2^12 3, but a chirp
+    # plan of it is refused
+    with pytest.raises(sft.SftError) as e:
+        sft.sft_plan(2 ** 20, 100, sft.sft_variant_init(dft=sft.SFT_DFT_CHIRP), primes=[12289])
+    assert e.value.status == sft.SFT_EINVAL and "8192" in sft.sft_last_error()
+    with pytest.raises(sft.SftError):
+        sft.sft_plan(2 ** 20, 100, sft.sft_variant_init(pool=7))
+    with pytest.raises(sft.SftError):
+        sft.sft_plan(2 ** 20, 100, sft.sft_variant_init(dft=9))
 
 
 @pytest.mark.parametrize("kw", [dict(N=1, s=1), dict(N=100, s=0), dict(N=100, s=101),

@@ -53,8 +53,8 @@ def _compare(g, res, cand, tol):
     return len(common), expl, float(np.max(err))
 
 
-def _run(N, s, f, prec, K, c_p, seed):
-    g = U.run_gpu(sft, N, s, f, prec, kappa=6, K=K, c_p=c_p, seed=seed, keep=True)
+def _run(N, s, f, prec, K, c_p, seed, **kw):
+    g = U.run_gpu(sft, N, s, f, prec, kappa=6, K=K, c_p=c_p, seed=seed, keep=True, **kw)
     cand = U.debug_arrays(sft, g["plan"], g["info"])[2]
     g["plan"].destroy()
     return g, cand
@@ -72,6 +72,24 @@ def test_precision_study_n2p26_s1000(trial, prec):
     tol = 1e-5 if prec == U.FP32 else 1e-11
     common, expl, err = _compare(g, res, cand, tol)
     print(f"trial {trial} prec {prec}: common {common}, explained differences {len(expl)}, "
+          f"max rel err {err:.2e}")
+    hits = len(set(g["freqs"][: g["count"]].tolist()) & set(sig.omega.tolist()))
+    assert hits >= 0.95 * s
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_precision_study_n2p26_s1000_rader(prec):
+    """The same workload with the primes drawn from the smooth pool and Rader's form (trial 0)."""
+    N, s = 2 ** 26, 1000
+    sig = make_signal(N, s, 3000, "loguniform", 30.0)
+    f32 = as_complex64(sig.f)
+    f = f32 if prec == U.FP32 else upcast(f32)
+    g, cand = _run(N, s, f, prec, 5, 3.0, 1, pool=sft.SFT_POOL_SMOOTH, dft=sft.SFT_DFT_RADER)
+    assert g["info"]["dft"] == sft.SFT_DFT_RADER
+    res = _oracle(("c3-smooth", 0), upcast(f32), g["info"], N, s)
+    tol = 1e-5 if prec == U.FP32 else 1e-11
+    common, expl, err = _compare(g, res, cand, tol)
+    print(f"rader prec {prec}: common {common}, explained differences {len(expl)}, "
           f"max rel err {err:.2e}")
     hits = len(set(g["freqs"][: g["count"]].tolist()) & set(sig.omega.tolist()))
     assert hits >= 0.95 * s

@@ -36,15 +36,22 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("form", ["chirp", "rader"])
 @pytest.mark.parametrize("prec", [U.FP32, U.FP64])
 @pytest.mark.parametrize("case", CASES)
-def test_stages_and_output_match_oracle(case, prec):
+def test_stages_and_output_match_oracle(case, prec, form):
+    """Every stage against the oracle; `form` chirp: the default prime pool and the chirp
+    convolution; rader: the smooth prime pool (every p_j - 1 13-smooth) and Rader's form."""
     N, s, seed, kappa, K, c_p, snr, mag = case
     sig = make_signal(N, s, seed, mag, snr)
     f32 = as_complex64(sig.f)
     f = upcast(f32)
-    g = U.run_gpu(sft, N, s, f32 if prec == U.FP32 else f, prec, kappa, K, c_p, seed, keep=True)
+    kw = (dict(dft=sft.SFT_DFT_CHIRP) if form == "chirp"
+          else dict(pool=sft.SFT_POOL_SMOOTH, dft=sft.SFT_DFT_RADER))
+    g = U.run_gpu(sft, N, s, f32 if prec == U.FP32 else f, prec, kappa, K, c_p, seed, keep=True,
+                  **kw)
     info, plan = g["info"], g["plan"]
+    assert info["dft"] == (sft.SFT_DFT_CHIRP if form == "chirp" else sft.SFT_DFT_RADER)
     oplan = U.oracle_plan(info, N, s)
     assert oplan.shifts == info["shifts"] and oplan.L == info["L"]
     samples, bins, cand, resid = U.debug_arrays(sft, plan, info)
@@ -140,9 +147,9 @@ def test_mixed_radix_lengths_match_oracle(M, primes, prec):
     f32 = as_complex64(sig.f)
     f = upcast(f32)
     g = U.run_gpu(sft, N, s, f32 if prec == U.FP32 else f, prec, 6, len(primes), 3.0, 0,
-                  primes=primes, keep=True)
+                  primes=primes, keep=True, dft=sft.SFT_DFT_CHIRP)
     info, plan = g["info"], g["plan"]
-    assert info["fft_size"] == M
+    assert info["fft_size"] == M and info["dft"] == sft.SFT_DFT_CHIRP
     oplan = U.oracle_plan(info, N, s)
     _, bins, _, _ = U.debug_arrays(sft, plan, info)
     plan.destroy()
@@ -367,3 +374,60 @@ def test_fp32_path_without_refinement():
     ref = np.array([m1[int(w)] for w in w0])
     assert np.max(np.abs(c0 - ref)) <= 2e-5 * np.max(np.abs(ref))
     assert l1 - l0 == 3
+
+
+# Rader's form: primes whose p - 1 exercises every radix of the pass schedule (2, 3, 4, 5, 6, 7, 8,
+# 10, 11, 12, 13, 14, 16), one-pass transforms (p = 3, 5, 7, 11, 13, 17), and the largest primes
+# each precision accepts (13441 - 1 = 2^7 3 5 7 for FP32, 6761 - 1 = 2^3 5 13^2 for FP64).
+RADER_PRIMES = [[3, 5, 7], [11, 13, 17], [23, 29, 31], [37, 53, 67], [79, 89, 97],
+                [1459, 2017, 2161], [3001, 3137, 3361], [6553, 6761], [12289, 13441]]
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+@pytest.mark.parametrize("primes", RADER_PRIMES)
+def test_rader_lengths_match_oracle(primes, prec):
+    if prec == U.FP64 and max(primes) > 6801:
+        pytest.skip("FP64 Rader transforms stop at p = 6801")
+    N, s = 2 ** 14, 2
+    sig = make_signal(N, s, sum(primes), "unit", 30.0)
+    f32 = as_complex64(sig.f)
+    f = upcast(f32)
+    g = U.run_gpu(sft, N, s, f32 if prec == U.FP32 else f, prec, 6, len(primes), 3.0, 0,
+                  primes=primes, keep=True, dft=sft.SFT_DFT_RADER)
+    info, plan = g["info"], g["plan"]
+    assert info["dft"] == sft.SFT_DFT_RADER and info["fft_size"] == 0
+    oplan = U.oracle_plan(info, N, s)
+    _, bins, _, _ = U.debug_arrays(sft, plan, info)
+    plan.destroy()
+    tol = 2e-6 if prec == U.FP32 else 1e-13
+    for qi, q in enumerate(info["shifts"]):
+        for j, p in enumerate(primes):
+            Z = U.subbins(info, bins[qi], j)
+            Y = O.measure(f, oplan, q, p)
+            bmax = np.max(np.abs(Y))
+            assert np.max(np.abs(Z[0] - Y)) <= tol * bmax, (p, qi)
+            for l, t in enumerate(info["small"]):
+                Xr = U.folded_subbins(info, Z, l)
+                X = O.measure(f, oplan, q, p * t)
+                b = np.arange(p)
+                for r in range(t):
+                    u = ((r - b) * pow(p, -1, t)) % t
+                    assert np.max(np.abs(Xr[r] - X[b + p * u])) <= tol * bmax, (p, qi, t)
+
+
+def test_rader_and_chirp_forms_agree():
+    """The same plan parameters in both forms: same support, coefficients within the FP32 path's
+    tolerance of each other, and Rader's form at least as accurate against the oracle."""
+    import torch
+    N, s = 2 ** 20, 40
+    sig = make_signal(N, s, 71, "loguniform", 40.0)
+    f32 = as_complex64(sig.f)
+    primes = O.choose_primes(s, 5, 3.0, 4, "smooth")
+    outs = {}
+    for form in (sft.SFT_DFT_CHIRP, sft.SFT_DFT_RADER):
+        g = U.run_gpu(sft, N, s, f32, U.FP32, 6, 5, 3.0, 4, primes=primes, dft=form)
+        outs[form] = g
+    res = O.dsft(upcast(f32), U.oracle_plan(outs[sft.SFT_DFT_RADER]["info"], N, s))
+    for form, g in outs.items():
+        n = g["count"]
+        U.assert_same_output(g["freqs"][:n], g["coefs"][:n], res.freqs, res.coefs, 1e-5)
