@@ -90,6 +90,7 @@ LaunchSet single_launch_set(const DevPlan& d) {
   }
   ls.pmax = d.pmax;
   ls.rlmax = d.rader ? d.rLmax : 0;
+  ls.rtpt = d.rader ? d.rTpt : 0;
   ls.kmax = d.K;
   return ls;
 }

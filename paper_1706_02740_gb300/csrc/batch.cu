@@ -251,10 +251,12 @@ sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n
   B.ls.tune = default_tuning();
   B.ls.pmax = 0;
   B.ls.rlmax = 0;
+  B.ls.rtpt = 0;
   B.ls.kmax = 0;
   for (int i = 0; i < n; ++i) {
     B.ls.pmax = std::max(B.ls.pmax, ps[i]->d.pmax);
     if (ps[i]->d.rader) B.ls.rlmax = std::max(B.ls.rlmax, ps[i]->d.rLmax);
+    if (ps[i]->d.rader) B.ls.rtpt = std::max(B.ls.rtpt, ps[i]->d.rTpt);
     B.ls.kmax = std::max(B.ls.kmax, ps[i]->d.K);
   }
   std::vector<int32_t> prefix;
@@ -478,6 +480,7 @@ sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
   for (int i = 0; i < n; ++i) {
     ls.pmax = std::max(ls.pmax, ps[i]->d.pmax);
     if (ps[i]->d.rader) ls.rlmax = std::max(ls.rlmax, ps[i]->d.rLmax);
+    if (ps[i]->d.rader) ls.rtpt = std::max(ls.rtpt, ps[i]->d.rTpt);
     ls.kmax = std::max(ls.kmax, ps[i]->d.K);
   }
   std::vector<int32_t> prefix;

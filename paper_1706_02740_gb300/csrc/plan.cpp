@@ -222,6 +222,32 @@ bool rader_schedule(int L, std::vector<int>& rad) {
   return (int)rad.size() <= kRaderMaxPasses;
 }
 
+// Threads per Rader transform (one transform per CTA): the whole-warp count in 32..512 that
+// maximises resident CTAs per SM over the pass iterations of the plan's transforms.  A CTA's
+// threads take a pass's L/R items in ceil(L/(R t)) rounds; residency is bounded by shared memory
+// (two buffers of rader_buf(Lmax) elements), registers (64 a thread FP32, 128 FP64) and 2048
+// threads per SM.  Ties go to fewer threads.
+int rader_threads(const std::vector<std::vector<int>>& sched, const std::vector<int32_t>& primes,
+                  int Lmax, bool fp64) {
+  const double smem = 2.0 * rader_buf(Lmax) * (fp64 ? 16 : 8) + 1024;
+  const int regs = fp64 ? 128 : 64;
+  int best_t = 256;
+  double best = -1;
+  for (int t = 32; t <= 512; t += 32) {
+    const int by_smem = (int)((228.0 * 1024) / smem);
+    const int ctas = std::min(std::min(by_smem, 65536 / (regs * t)), std::min(2048 / t, 32));
+    if (ctas < 1) continue;
+    int64_t rounds = 0;
+    for (size_t j = 0; j < primes.size(); ++j) {
+      const int L = primes[j] - 1;
+      for (int R : sched[j]) rounds += (L / R + t - 1) / t;
+    }
+    const double rate = (double)ctas / (double)rounds;
+    if (rate > best * (1 + 1e-9)) { best = rate; best_t = t; }
+  }
+  return best_t;
+}
+
 // Smallest primitive root modulo the prime p (p - 1 13-smooth): g with g^((p-1)/q) != 1 for every
 // prime q dividing p - 1.
 int64_t pow_mod(int64_t b, int64_t e, int64_t m) {
@@ -379,6 +405,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   d.fftM = M; d.fftLog2 = logM; d.pmax = pmax;
   d.rader = rader ? 1 : 0;
   d.rLmax = rader ? pmax - 1 : 0;
+  d.rTpt = rader ? rader_threads(rsched, primes, pmax - 1, fp64) : 0;
   int64_t sump = 0;
   for (int j = 0; j < K; ++j) {
     d.p[j] = primes[j];

@@ -12,8 +12,10 @@
 // One transform per CTA: two shared-memory buffers of L elements (padded, one slot per 16) and
 // out-of-place Stockham passes that alternate between them (one barrier per pass, one item of at
 // most 16 values per thread at a time).  The radix of each pass comes from the plan's schedule at
-// run time; each radix is a compile-time in-register DFT.  The first pass gathers a_n from the
-// samples in global memory through the table g^n; the last pass of the first FFT multiplies by V
+// run time; each radix is a compile-time in-register DFT.  The samples h_1 .. h_{p-1} are first
+// staged in order (coalesced loads) and the first pass gathers a_n from them through the table g^n
+// (reading them from global memory in that order instead costs a 32-byte sector per 8-byte
+// sample once a batch's samples exceed L2); the last pass of the first FFT multiplies by V
 // and conjugates; the last pass of the second FFT writes conj(.) + h_0/p to shared memory at
 // position g^{-m} - 1, from where the p outputs are stored contiguously.
 #include <stdint.h>
@@ -53,7 +55,7 @@ __device__ __forceinline__ void twiddle_rows(const C* __restrict__ W, int S, int
 }
 
 // Where a pass reads and writes.
-enum { kRdSmem = 0, kRdGather = 1 };                   // shared memory, or a_n = h[g^n] (global)
+enum { kRdSmem = 0, kRdGather = 1 };                   // in order, or a_n = h[g^n] (staged h)
 enum { kWrSmem = 0, kWrFilter = 1, kWrScatter = 2 };   // plain, x V then conj, or permuted output
 
 template <typename C>
@@ -81,7 +83,7 @@ __device__ __forceinline__ void rader_pass(const C* __restrict__ src, C* __restr
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
       const int n = i + r * NI;
-      if constexpr (RD == kRdGather) v[r] = __ldg(io.in + __ldg(io.pin + n));
+      if constexpr (RD == kRdGather) v[r] = src[pad16(__ldg(io.pin + n) - 1)];
       else v[r] = src[pad16(n)];
     }
     if (S > 1) twiddle_rows<C, RAD>(W, S, k, v);
@@ -157,7 +159,10 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) rader_kernel(Batc
   io.h0p = cscale(h0, inv_p);
   const int lt = threadIdx.x, tpt = blockDim.x;
 
-  // forward FFT of a (gathered through g^n), then x V and conj in its last pass
+  // h_1 .. h_{p-1} staged in order (coalesced loads); the first pass gathers a_n = h_{g^n} from it
+  for (int n = lt; n < L; n += tpt) bufB[pad16(n)] = __ldg(io.in + 1 + n);
+  __syncthreads();
+  // forward FFT of a, then x V and conj in its last pass
   C* src = bufB;
   C* dst = bufA;
   int S = 1;
@@ -190,19 +195,12 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) rader_kernel(Batc
   for (int n = lt; n < L; n += tpt) out[1 + n] = src[pad16(n)];
 }
 
-// Threads per transform: about L / 12 (a radix-12 pass has one item per thread), whole warps,
-// 32 .. 512.
-int rader_threads(int L) {
-  int t = ((L / 12 + 31) / 32) * 32;
-  return t < 32 ? 32 : (t > 512 ? 512 : t);
-}
-
 template <typename R>
 cudaError_t launch_rader_prec(const BatchView& bv, const LaunchSet& ls, cudaStream_t st,
                               int* launched) {
   using C = typename Cx<R>::T;
   const unsigned grid = (unsigned)ls.blocks[kStRader];
-  const int threads = rader_threads(ls.rlmax);
+  const int threads = ls.rtpt > 0 ? ls.rtpt : 256;
   const size_t smem = 2 * (size_t)rader_buf(ls.rlmax) * sizeof(C);
   cudaError_t e = ensure_dynamic_smem<rader_kernel<R>>(smem);
   if (e != cudaSuccess) return e;

@@ -236,6 +236,7 @@ cudaError_t launch_slot(Server& S, Slot& sl, const std::vector<Request*>& rq, in
     memcpy(sl.host + sizeof(DevPlan) * i, &d, sizeof(DevPlan));
     ls.pmax = std::max(ls.pmax, d.pmax);
     if (d.rader) ls.rlmax = std::max(ls.rlmax, d.rLmax);
+    if (d.rader) ls.rtpt = std::max(ls.rtpt, d.rTpt);
     ls.kmax = std::max(ls.kmax, d.K);
     ptr[i] = const_cast<void*>(rq[i]->f);
     ptr[n + i] = rq[i]->w;

@@ -56,6 +56,7 @@ struct DevPlan {
                               // 0 when the plan takes Rader's form
   int32_t rader;              // 1: the length-p_j DFTs by Rader's algorithm (every p_j - 1 13-smooth)
   int32_t rLmax;              // largest p_j - 1 of a Rader plan
+  int32_t rTpt;               // threads per Rader transform chosen for this plan's schedules
   int32_t p[kMaxK];
   int64_t nodeoff[kMaxK + 1]; // first node of prime j
   int32_t poff[kMaxK + 1];    // first bin of prime j
@@ -193,6 +194,7 @@ struct LaunchSet {
   const int32_t* blk[kStCount];
   int32_t pmax;               // largest prime over the signals (shared-memory sizing)
   int32_t rlmax;              // largest p - 1 over the signals in Rader's form (0: none)
+  int32_t rtpt;               // threads per Rader transform (largest rTpt over those signals)
   int32_t kmax;               // most prime moduli of any signal (per-thread median arrays)
   sft_tuning tune;            // launch geometry (block shapes; never changes results)
 };
