@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--pool", choices=sorted(POOLS), default="all",
                     help="prime pool of the plans: all primes, or those whose p - 1 is 13-smooth "
                          "(Rader's form of the DFTs)")
+    ap.add_argument("--s-list", default="", help="sweep-s: comma-separated s values to run")
     ap.add_argument("--precision-trials", type=int, default=10,
                     help="seeded inputs of the precision study compared with the oracle")
     ap.add_argument("--batched-signals", type=int, default=4096)
@@ -891,7 +892,10 @@ def run_study(args):
     if args.study == "sweep-n":
         points = [(2 ** e, 50, None) for e in range(16, 31, 2)]
     elif args.study == "sweep-s":
-        points = [(2 ** 26, s, None) for s in (50, 100, 200, 400, 1000, 2000, 4000)]
+        s_list = (50, 100, 200, 400, 1000, 2000, 4000)
+        if args.s_list:
+            s_list = tuple(int(x) for x in args.s_list.split(","))
+        points = [(2 ** 26, s, None) for s in s_list]
     else:
         points = [(2 ** 22, 50, snr) for snr in (0, 10, 20, 30, 40, 50, 60, 70, 80)]
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -911,12 +915,28 @@ def run_study(args):
 
     # Section 5.1: the parameters of each randomized method are chosen per (N, s) so that all s
     # frequencies are recovered in at least 90% of the trials; here the first rung of this ladder
-    # of (K, c_p) that does so (c_p capped so that every prime stays <= 8192, the limit of the
-    # FP32 chirp convolution)
+    # of (K, c_p) that does so.  Where the rung's primes would pass 8192 (the FP32 chirp
+    # convolution's limit) the plan draws them from the smooth pool and takes Rader's form (primes
+    # up to 13601), with c_p lowered in steps of 0.1 only as far as that limit needs.
     ladder = [(5, 3.0), (7, 4.0), (9, 5.0), (11, 6.0), (13, 8.0), (15, 8.0)]
 
+    def make_plan(N, s, kappa, K, c_p):
+        pool = sft.SFT_POOL_ALL if c_p * s * 1.1 <= 8192 else sft.SFT_POOL_SMOOTH
+        while True:
+            try:
+                v = sft.sft_variant_init(kappa=kappa, K=K, c_p=c_p, seed=1, pool=pool)
+                return sft.sft_plan(N, s, v), c_p, pool
+            except sft.SftError:
+                if pool == sft.SFT_POOL_ALL:
+                    pool = sft.SFT_POOL_SMOOTH
+                elif c_p > 1.05:
+                    c_p = round(c_p - 0.1, 1)
+                else:
+                    raise
+
     def trial_run(N, s, snr, kappa, K, c_p, trials, stages=False):
-        plan = sft.sft_plan(N, s, sft.sft_variant_init(kappa=kappa, K=K, c_p=c_p, seed=1))
+        plan, c_p, pool = make_plan(N, s, kappa, K, c_p)
+        form = "rader" if plan.info()["dft"] == sft.SFT_DFT_RADER else "chirp"
         times, ok, l1 = [], 0, []
         st = None
         for t in range(trials):
@@ -944,16 +964,16 @@ def run_study(args):
                 l1.append(sum(abs(truth[k] - got[k]) for k in truth) / s)
             del f
         plan.destroy()
-        return {"K": K, "c_p": c_p, "ms_p50": float(np.median(times)), "exact_support": ok / trials,
+        return {"K": K, "c_p": c_p, "pool": "smooth" if pool else "all", "dft": form,
+                "ms_p50": float(np.median(times)), "exact_support": ok / trials,
                 "avg_l1_error": float(np.mean(l1)) if l1 else None, "stages_us": st}
 
     for N, s, snr in points:
-        cp_cap = min(8.0, math.floor(10 * 7600 / s) / 10)
         rec = {"study": args.study, "N": N, "s": s, "snr_db": snr, "trials": args.trials}
         for kappa in (4, 6):
             best = None
             for K, c_p in ladder:
-                r = trial_run(N, s, snr, kappa, K, min(c_p, cp_cap), args.trials)
+                r = trial_run(N, s, snr, kappa, K, c_p, args.trials)
                 if best is None or r["exact_support"] > best["exact_support"]:
                     best = r
                 if r["exact_support"] >= 0.9:

@@ -76,9 +76,10 @@ __device__ __forceinline__ void rader_pass(const C* __restrict__ src, C* __restr
                                            const C* __restrict__ W, int L, int S, int lt, int tpt,
                                            const RaderIO<C>& io) {
   const int NI = L / RAD;
+  // i = q S + k, advanced by tpt = tq S + tr per round (two divisions per pass, none per item)
+  const int tq = tpt / S, tr = tpt - tq * S;
+  int q = lt / S, k = lt - q * S;
   for (int i = lt; i < NI; i += tpt) {
-    const int q = i / S;
-    const int k = i - q * S;
     C v[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
@@ -100,6 +101,12 @@ __device__ __forceinline__ void rader_pass(const C* __restrict__ src, C* __restr
       } else {
         dst[pad16(c)] = v[r];
       }
+    }
+    q += tq;
+    k += tr;
+    if (k >= S) {
+      k -= S;
+      ++q;
     }
   }
 }
@@ -124,8 +131,8 @@ __device__ __forceinline__ void pass_any(int R, const C* src, C* dst, const C* W
   }
 }
 
-// One transform per CTA (blockDim.x threads); the CTA of block x takes transform x of its signal
-// (shift, prime and node subset as in the chirp-convolution kernel).  FP32 builds are held to 64
+// One transform per CTA (blockDim.x threads); the CTA of block x takes transform x of its signal,
+// counted prime by prime (then shift, then node subset).  FP32 builds are held to 64
 // registers (several CTAs per SM), FP64 builds to 128.
 template <typename R>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) rader_kernel(BatchView bv) {
@@ -135,12 +142,14 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) rader_kernel(Batc
   __shared__ C a0;
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
-  const int per_q = d.K * d.nsub;
-  if (lb >= per_q * d.nq) return;                 // (the block count is exact; kept as a guard)
-  const int qi = lb / per_q;
-  const int rem = lb - qi * per_q;
-  const int j = rem / d.nsub;
-  const int sub = rem - j * d.nsub;
+  // prime-major order: the CTAs resident at one time mostly share a prime, so its tables
+  // (twiddle rows, V, permutations: ~24 L bytes) stay in L1
+  const int per_j = d.nq * d.nsub;
+  if (lb >= per_j * d.K) return;                  // (the block count is exact; kept as a guard)
+  const int j = lb / per_j;
+  const int rem = lb - j * per_j;
+  const int qi = rem / d.nsub;
+  const int sub = rem - qi * d.nsub;
   const int p = d.p[j], L = p - 1;
   const int64_t off = (int64_t)qi * d.m + d.nodeoff[j] + (int64_t)sub * p;
   C* bufA = reinterpret_cast<C*>(smem_raw);
