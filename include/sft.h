@@ -407,6 +407,9 @@ typedef struct {
   int32_t max_inflight;   /* batched executions in flight at once (streams), 1..8 */
   sft_variant variant;
   sft_tuning tune;
+  int32_t build_threads;  /* threads that build new plans beside the scheduler, 0..16 (0: the
+                             scheduler builds them itself, holding up the queue meanwhile) */
+  int32_t reserved;
 } sft_server_config;
 
 typedef struct {
@@ -416,6 +419,7 @@ typedef struct {
   int32_t plan_reused;    /* 1 if its plan was resident already, 0 if built for it */
   double queued_ms;       /* submission -> launch of its batch (host clock) */
   double latency_ms;      /* submission -> results complete in device memory (host clock) */
+  double build_ms;        /* host time spent building its plan (0 when a resident plan served) */
 } sft_request_info;
 
 typedef struct {
@@ -424,9 +428,13 @@ typedef struct {
   int64_t kernel_launches;
   size_t arena_bytes, arena_used, arena_peak;
   int32_t resident_plans, max_batch_seen;
+  double build_ms_total;  /* host time spent building plans */
 } sft_server_stats;
 
-/* Default configuration: 8 GiB, max_batch 64, max_inflight 2, sft_variant_init, default tuning. */
+/* Default configuration: 8 GiB, max_batch 64, max_inflight 2, sft_variant_init, default tuning,
+ * 2 build threads.  A request whose (N, s) has no idle resident plan has its plan built by a
+ * build thread (tables of primes seen before come from a host cache) while the requests behind
+ * it are batched; it joins the next batch once the plan is ready. */
 void sft_server_config_init(sft_server_config* cfg);
 
 /* Allocate the arena and the streams, start the scheduler.  SFT_EINVAL for a bad configuration,

@@ -74,13 +74,15 @@ class sft_tuning(ctypes.Structure):
 
 class sft_server_config(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32),
-                ("max_inflight", ctypes.c_int32), ("variant", sft_variant), ("tune", sft_tuning)]
+                ("max_inflight", ctypes.c_int32), ("variant", sft_variant), ("tune", sft_tuning),
+                ("build_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sft_request_info(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("batch_size", ctypes.c_int32), ("plan_reused", ctypes.c_int32),
-                ("queued_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("queued_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("build_ms", ctypes.c_double)]
 
 
 class sft_server_stats(ctypes.Structure):
@@ -90,7 +92,7 @@ class sft_server_stats(ctypes.Structure):
                 ("plans_evicted", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
                 ("arena_peak", ctypes.c_size_t), ("resident_plans", ctypes.c_int32),
-                ("max_batch_seen", ctypes.c_int32)]
+                ("max_batch_seen", ctypes.c_int32), ("build_ms_total", ctypes.c_double)]
 
 
 _lib = None
@@ -459,12 +461,15 @@ class Server:
     batching).  Buffers passed to submit must stay alive until the request has finished."""
 
     def __init__(self, mem_budget: int = 8 << 30, max_batch: int = 64, max_inflight: int = 2,
-                 variant: sft_variant | None = None, tuning: dict | None = None):
+                 variant: sft_variant | None = None, tuning: dict | None = None,
+                 build_threads: int | None = None):
         cfg = sft_server_config()
         load().sft_server_config_init(ctypes.byref(cfg))
         cfg.mem_budget = int(mem_budget)
         cfg.max_batch = int(max_batch)
         cfg.max_inflight = int(max_inflight)
+        if build_threads is not None:
+            cfg.build_threads = int(build_threads)
         if variant is not None:
             cfg.variant = variant
         if tuning is not None:
@@ -484,7 +489,8 @@ class Server:
         _check(load().sft_server_query(self.handle, int(rid), ctypes.byref(info)))
         return {"state": REQUEST_STATES[info.state], "status": info.status,
                 "batch_size": info.batch_size, "plan_reused": bool(info.plan_reused),
-                "queued_ms": info.queued_ms, "latency_ms": info.latency_ms}
+                "queued_ms": info.queued_ms, "latency_ms": info.latency_ms,
+                "build_ms": info.build_ms}
 
     def wait(self, rid: int, timeout_ms: int = -1) -> int:
         """Waits for the request to finish; returns its status (SFT_OK when done, else why it

@@ -6,7 +6,12 @@
 
 #include <algorithm>
 #include <complex>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "sft_internal.h"
@@ -273,6 +278,93 @@ int64_t primitive_root(int64_t p) {
   return 1;   // p = 2
 }
 
+// Per-prime constant tables (FP64), cached on the host across plans: a plan for a new N whose
+// primes were seen before only assembles them.  The re-estimation twiddles e^{-2 pi i n / p}; in
+// the chirp form the chirp e^{-pi i n^2 / p} and FFT_M of its wrapped conjugate / (M p); in
+// Rader's form the permutations g^n, g^{-n}, V = FFT(b) / (p (p - 1)) and the pass schedule with
+// its twiddle rows.  Bounded to kPrimeCache entries, oldest dropped first.
+struct PrimeTables {
+  std::vector<cd> wp;
+  std::vector<cd> chirp, vhat;
+  std::vector<int32_t> pin, pout;
+  std::vector<cd> rv, rt;
+  std::vector<int> sched;
+  std::vector<int32_t> toff;
+};
+constexpr size_t kPrimeCache = 512;
+std::mutex g_prime_mu;
+std::map<std::tuple<int64_t, int, bool>, std::shared_ptr<const PrimeTables>> g_prime_tables;
+std::deque<std::tuple<int64_t, int, bool>> g_prime_order;
+
+std::shared_ptr<const PrimeTables> compute_prime_tables(int64_t p, int M, bool rader) {
+  auto T = std::make_shared<PrimeTables>();
+  T->wp.resize(p);
+  for (int64_t n = 0; n < p; ++n) T->wp[n] = expi_turns(-n, p);
+  if (!rader) {
+    T->chirp.resize(p);
+    std::vector<cd> V(M, cd(0, 0));
+    for (int64_t n = 0; n < p; ++n) {
+      const cd w = expi_turns(-((n * n) % (2 * p)), 2 * p);  // exp(-pi i n^2 / p)
+      T->chirp[n] = w;
+      V[n] = std::conj(w);
+      if (n > 0) V[M - n] = std::conj(w);
+    }
+    host_fft(V);
+    T->vhat.resize(M);
+    for (int n = 0; n < M; ++n) T->vhat[n] = V[n] / ((double)M * (double)p);
+    return T;
+  }
+  // Rader's form: L = p - 1, g a primitive root; a_n = h_{g^n}, b_n = e^{-2 pi i g^{-n} / p} and
+  // E_{g^{-m}} = h_0 / p + (a (*) b)[m] / p (cyclic convolution), E_0 = (h_0 + sum_n a_n) / p.
+  const int64_t L = p - 1;
+  rader_schedule((int)L, T->sched);
+  const int64_t g = primitive_root(p), ginv = pow_mod(g, p - 2, p);
+  T->pin.resize(L);
+  T->pout.resize(L);
+  std::vector<cd> b(L);
+  int64_t x = 1, y = 1;
+  for (int64_t n = 0; n < L; ++n) {
+    T->pin[n] = (int32_t)x;                 // g^n mod p
+    T->pout[n] = (int32_t)y;                // g^{-n} mod p
+    b[n] = expi_turns(-y, p);
+    x = x * g % p;
+    y = y * ginv % p;
+  }
+  host_fft_mixed(b);
+  T->rv.resize(L);
+  for (int64_t k = 0; k < L; ++k) T->rv[k] = b[k] / ((double)p * (double)L);
+  T->rt.assign(L, cd(1, 0));
+  int64_t span = 1, off = 0;
+  for (int R : T->sched) {
+    T->toff.push_back((int32_t)off);
+    for (int row = 0; row < fft_tw_rows(R); ++row)
+      for (int64_t k = 0; k < span; ++k)
+        T->rt[off + (size_t)row * span + k] = expi_turns(-(int64_t)fft_tw_exp(row) * k, span * R);
+    off += (int64_t)fft_tw_rows(R) * span;
+    span *= R;
+  }
+  return T;
+}
+
+std::shared_ptr<const PrimeTables> prime_tables(int64_t p, int M, bool rader) {
+  const auto key = std::make_tuple(p, rader ? 0 : M, rader);
+  {
+    std::lock_guard<std::mutex> g(g_prime_mu);
+    auto it = g_prime_tables.find(key);
+    if (it != g_prime_tables.end()) return it->second;
+  }
+  auto T = compute_prime_tables(p, M, rader);
+  std::lock_guard<std::mutex> g(g_prime_mu);
+  if (g_prime_tables.emplace(key, T).second) {
+    g_prime_order.push_back(key);
+    while (g_prime_order.size() > kPrimeCache) {
+      g_prime_tables.erase(g_prime_order.front());
+      g_prime_order.pop_front();
+    }
+  }
+  return T;
+}
+
 template <typename T>
 void put(std::vector<char>& blob, size_t off, const std::vector<cd>& v, bool fp64) {
   if (fp64) {
@@ -486,65 +578,36 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   }
   {
     std::vector<cd> ch((size_t)K * pmax, cd(0, 0)), vh((size_t)K * M), wp((size_t)K * pmax, cd(0, 0));
+    std::vector<cd> rv(rader ? (size_t)K * pmax : 0, cd(0, 0)), rt(rader ? (size_t)K * pmax : 0, cd(1, 0));
+    int32_t* sch = reinterpret_cast<int32_t*>(blob.data() + o_rsch);
+    int32_t* perm = reinterpret_cast<int32_t*>(blob.data() + o_rperm);
     for (int j = 0; j < K; ++j) {
       const int64_t p = primes[j];
-      for (int64_t n = 0; n < p; ++n) wp[(size_t)j * pmax + n] = expi_turns(-n, p);
-      if (rader) continue;
-      std::vector<cd> V(M, cd(0, 0));
-      for (int64_t n = 0; n < p; ++n) {
-        cd w = expi_turns(-((n * n) % (2 * p)), 2 * p);  // exp(-pi i n^2 / p)
-        ch[(size_t)j * pmax + n] = w;
-        V[n] = std::conj(w);
-        if (n > 0) V[M - n] = std::conj(w);
+      const std::shared_ptr<const PrimeTables> T = prime_tables(p, M, rader);
+      std::copy(T->wp.begin(), T->wp.end(), wp.begin() + (size_t)j * pmax);
+      if (!rader) {
+        std::copy(T->chirp.begin(), T->chirp.end(), ch.begin() + (size_t)j * pmax);
+        std::copy(T->vhat.begin(), T->vhat.end(), vh.begin() + (size_t)j * M);
+        continue;
       }
-      host_fft(V);
-      for (int n = 0; n < M; ++n) vh[(size_t)j * M + n] = V[n] / ((double)M * (double)p);
+      std::copy(T->pin.begin(), T->pin.end(), perm + (size_t)j * 2 * pmax);
+      std::copy(T->pout.begin(), T->pout.end(), perm + (size_t)j * 2 * pmax + pmax);
+      std::copy(T->rv.begin(), T->rv.end(), rv.begin() + (size_t)j * pmax);
+      std::copy(T->rt.begin(), T->rt.end(), rt.begin() + (size_t)j * pmax);
+      int32_t* sj = sch + (size_t)j * kRaderSched;
+      sj[0] = (int32_t)T->sched.size();
+      for (size_t i = 0; i < T->sched.size(); ++i) {
+        sj[1 + i] = T->sched[i];
+        sj[16 + i] = T->toff[i];
+      }
     }
     put<cd>(blob, o_chirp, ch, fp64);
     put<cd>(blob, o_vhat, vh, fp64);
     put<cd>(blob, o_wp, wp, false);
-  }
-  if (rader) {
-    // Rader's form (per prime): L = p - 1, g a primitive root; a_n = h_{g^n}, b_n = e^{-2 pi i g^{-n} / p}
-    // and E_{g^{-m}} = h_0 / p + (a (*) b)[m] / p (cyclic convolution), E_0 = (h_0 + sum_n a_n) / p.
-    int32_t* sch = reinterpret_cast<int32_t*>(blob.data() + o_rsch);
-    int32_t* perm = reinterpret_cast<int32_t*>(blob.data() + o_rperm);
-    std::vector<cd> rv((size_t)K * pmax, cd(0, 0)), rt((size_t)K * pmax, cd(1, 0));
-    for (int j = 0; j < K; ++j) {
-      const int64_t p = primes[j], L = p - 1;
-      const int64_t g = primitive_root(p), ginv = pow_mod(g, p - 2, p);
-      int32_t* pin = perm + (size_t)j * 2 * pmax;
-      int32_t* pout = pin + pmax;
-      int64_t x = 1, y = 1;
-      std::vector<cd> b(L);
-      for (int64_t n = 0; n < L; ++n) {
-        pin[n] = (int32_t)x;                 // g^n mod p
-        pout[n] = (int32_t)y;                // g^{-n} mod p
-        b[n] = expi_turns(-y, p);
-        x = x * g % p;
-        y = y * ginv % p;
-      }
-      host_fft_mixed(b);
-      for (int64_t k = 0; k < L; ++k) rv[(size_t)j * pmax + k] = b[k] / ((double)p * (double)L);
-      const std::vector<int>& rad = rsched[j];
-      int32_t* sj = sch + (size_t)j * kRaderSched;
-      sj[0] = (int32_t)rad.size();
-      int64_t span = 1, toff = 0;
-      for (size_t i = 0; i < rad.size(); ++i) {
-        const int R = rad[i];
-        sj[1 + i] = R;
-        sj[16 + i] = (int32_t)toff;
-        for (int row = 0; row < fft_tw_rows(R); ++row)
-          for (int64_t k = 0; k < span; ++k)
-            rt[(size_t)j * pmax + toff + (size_t)row * span + k] =
-                expi_turns(-(int64_t)fft_tw_exp(row) * k, span * R);
-        toff += (int64_t)fft_tw_rows(R) * span;
-        span *= R;
-      }
-      if (toff > pmax) { set_error("internal: Rader twiddle rows overflow"); return SFT_EINVAL; }
+    if (rader) {
+      put<cd>(blob, o_rV, rv, fp64);
+      put<cd>(blob, o_rtw, rt, fp64);
     }
-    put<cd>(blob, o_rV, rv, fp64);
-    put<cd>(blob, o_rtw, rt, fp64);
   }
   {
     std::vector<cd> fw(M, cd(1, 0));

@@ -2,9 +2,12 @@
 // batching over several streams.
 //
 // Threads: callers submit and query under one mutex; one scheduler thread owns the plans, the
-// arena and the launch slots; CUDA's host-callback thread marks a slot done when its batched
-// execution has finished on the device.  The scheduler makes no CUDA call while it holds the
-// mutex, so a completion callback never waits on CUDA work.
+// arena and the launch slots; builder threads (sft_server_config.build_threads) build the plans
+// of requests whose (N, s) has no idle resident plan, so a new N does not hold up the requests
+// queued behind it (they are batched while it builds, and it joins the next batch once its plan
+// is ready); CUDA's host-callback thread marks a slot done when its batched execution has
+// finished on the device.  The scheduler makes no CUDA call while it holds the mutex, so a
+// completion callback never waits on CUDA work.
 #include <string.h>
 
 #include <algorithm>
@@ -38,6 +41,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kMaxServerBatch = 256;
 constexpr int kMaxInflight = 8;
+constexpr int kMaxBuilders = 16;
 
 // The budget as device memory: one cudaMalloc, blocks handed out by OffsetArena, uploads on a
 // private non-blocking stream (never the legacy default stream, which would wait for other work).
@@ -107,7 +111,16 @@ struct Request {
   int32_t status = SFT_OK;
   int32_t batch_size = 0, reused = 0;
   Clock::time_point t_submit, t_launch, t_done;
-  Entry* plan = nullptr;
+  Entry* plan = nullptr;             // set when a builder made its plan (or at admission)
+  double build_ms = 0.0;             // host time spent building its plan (0 when reused)
+  bool build_here = false;           // a builder ran out of arena: build with eviction inline
+};
+
+struct Built {                       // a builder's result, handed to the scheduler
+  int64_t id;
+  Entry* e;                          // nullptr on failure
+  sft_status status;
+  double ms;
 };
 
 struct Server;
@@ -143,7 +156,86 @@ struct Server {
   std::list<Entry*> lru;             // idle plans, least recently used first
   sft_server_stats stats;            // guarded by mu
   int device = 0;
+  // plan builders (guarded by mu)
+  std::vector<std::thread> builders;
+  std::condition_variable build_cv;
+  std::deque<int64_t> build_q;
+  std::vector<Built> built;
+  int building = 0;
+  bool stop_builders = false;
 };
+
+// Builder thread: takes a request id, builds its plan from the arena (thread-safe) with the
+// server's variant, and hands the plan (or the failure) back to the scheduler.
+void builder(Server* Sp) {
+  Server& S = *Sp;
+  cudaSetDevice(S.device);
+  std::unique_lock<std::mutex> lk(S.mu);
+  for (;;) {
+    S.build_cv.wait(lk, [&] { return S.stop_builders || !S.build_q.empty(); });
+    if (S.build_q.empty()) break;
+    const int64_t id = S.build_q.front();
+    S.build_q.pop_front();
+    const Request& r = S.reqs[id];
+    const int64_t N = r.N;
+    const int32_t s = r.s;
+    ++S.building;
+    lk.unlock();
+    const auto t0 = Clock::now();
+    Entry* e = new (std::nothrow) Entry();
+    sft_status st = SFT_ENOMEM;
+    if (e) {
+      st = build_plan(&e->P, N, s, &S.cfg.variant, 0, nullptr, 0, nullptr, 0, &S.arena);
+      if (st == SFT_OK) {
+        e->N = N;
+        e->s = s;
+        e->busy = true;
+      } else {
+        free_plan(&e->P);
+        delete e;
+        e = nullptr;
+      }
+    }
+    const double ms = ms_between(t0, Clock::now());
+    lk.lock();
+    --S.building;
+    S.built.push_back({id, e, st, ms});
+    S.cv.notify_all();
+  }
+}
+
+// Hand the builders' results to the queue (scheduler thread, mu held): a built plan becomes
+// resident (busy, for its request) and its request goes to the front of the queue; a request
+// whose build ran out of arena is retried by the scheduler with eviction; other failures fail
+// the request.
+bool take_built(Server& S) {
+  if (S.built.empty()) return false;
+  bool failed = false;
+  for (const Built& b : S.built) {
+    Request& r = S.reqs[b.id];
+    if (b.e) {
+      S.plans.insert({{b.e->N, b.e->s}, b.e});
+      ++S.stats.resident_plans;
+      ++S.stats.plans_built;
+      S.stats.build_ms_total += b.ms;
+      r.plan = b.e;
+      r.build_ms = b.ms;
+      S.queue.push_front(b.id);
+    } else if (b.status == SFT_ENOMEM) {
+      r.build_here = true;
+      S.queue.push_front(b.id);
+    } else {
+      r.state = 3;
+      r.status = b.status;
+      r.t_done = Clock::now();
+      ++S.stats.failed;
+      failed = true;
+    }
+  }
+  S.built.clear();
+  if (failed) S.done_cv.notify_all();
+  return true;
+}
 
 void CUDART_CB on_slot_done(void* p) {
   Slot* sl = static_cast<Slot*>(p);
@@ -170,19 +262,27 @@ void evict(Server& S, Entry* e) {
   --S.stats.resident_plans;
 }
 
-// A resident idle plan for (N, s), or a new one carved from the arena (evicting least recently
-// used idle plans when it does not fit).  SFT_ENOMEM when it cannot fit beside the busy plans.
-sft_status acquire(Server& S, int64_t N, int32_t s, Entry** out, bool* reused) {
+// A resident idle plan for (N, s), marked busy, or nullptr.
+Entry* acquire_resident(Server& S, int64_t N, int32_t s) {
   auto range = S.plans.equal_range({N, s});
   for (auto it = range.first; it != range.second; ++it) {
     Entry* e = it->second;
     if (!e->busy) {
       S.lru.erase(e->lru_it);
       e->busy = true;
-      *out = e;
-      *reused = true;
-      return SFT_OK;
+      return e;
     }
+  }
+  return nullptr;
+}
+
+// A resident idle plan for (N, s), or a new one carved from the arena (evicting least recently
+// used idle plans when it does not fit).  SFT_ENOMEM when it cannot fit beside the busy plans.
+sft_status acquire(Server& S, int64_t N, int32_t s, Entry** out, bool* reused) {
+  if (Entry* r = acquire_resident(S, N, s)) {
+    *out = r;
+    *reused = true;
+    return SFT_OK;
   }
   Entry* e = new (std::nothrow) Entry();
   if (!e) return SFT_ENOMEM;
@@ -301,6 +401,7 @@ void scheduler(Server* Sp) {
   cudaSetDevice(S.device);
   std::unique_lock<std::mutex> lk(S.mu);
   for (;;) {
+    take_built(S);
     // retire finished slots
     bool retired = false;
     for (Slot* sl : S.slots) {
@@ -347,20 +448,23 @@ void scheduler(Server* Sp) {
       }
       S.queue.clear();
       S.done_cv.notify_all();
-      if (S.stop) break;
-      wait_or_poll(S, lk, [&] { return S.stop || !S.queue.empty(); });
+      if (S.stop && S.build_q.empty() && S.building == 0 && S.built.empty()) break;
+      wait_or_poll(S, lk, [&] { return S.stop || !S.queue.empty() || !S.built.empty(); });
       continue;
     }
-    if (S.stop && S.queue.empty() && !any_busy) break;
+    const bool builds_pending = !S.build_q.empty() || S.building > 0 || !S.built.empty();
+    if (S.stop && S.queue.empty() && !any_busy && !builds_pending) break;
     if (!free_slot || S.queue.empty()) {
       wait_or_poll(S, lk, [&] {
+        if (!S.built.empty()) return true;
+        const bool pending = !S.build_q.empty() || S.building > 0;
         bool busy = false, idle = false;
         for (Slot* sl : S.slots) {
           if (sl->dead) continue;
           if (sl->busy && sl->done) return true;
           (sl->busy ? busy : idle) = true;
         }
-        if (S.queue.empty()) return S.stop && !busy;
+        if (S.queue.empty()) return S.stop && !busy && !pending;
         return idle;
       });
       continue;
@@ -382,21 +486,45 @@ void scheduler(Server* Sp) {
     free_slot->plans.clear();
     lk.unlock();
 
-    std::vector<int64_t> admitted, deferred;
+    std::vector<int64_t> admitted, deferred, to_build;
     std::vector<Request*> arq;
     std::vector<std::pair<int64_t, sft_status>> failed;
     std::vector<int32_t> was_reused;
     int64_t built = 0, reused_n = 0;
+    double built_ms = 0.0;
     for (size_t i = 0; i < take.size(); ++i) {
+      if (rq[i]->plan) {                       // a builder made its plan: it joins this batch
+        was_reused.push_back(0);
+        admitted.push_back(take[i]);
+        arq.push_back(rq[i]);
+        continue;
+      }
       if (!deferred.empty()) {                 // keep arrival order behind a waiting request
         deferred.push_back(take[i]);
         continue;
       }
+      if (S.cfg.build_threads > 0 && !rq[i]->build_here) {
+        if (Entry* e = acquire_resident(S, rq[i]->N, rq[i]->s)) {
+          rq[i]->plan = e;
+          ++reused_n;
+          was_reused.push_back(1);
+          admitted.push_back(take[i]);
+          arq.push_back(rq[i]);
+        } else {
+          to_build.push_back(take[i]);         // built beside the scheduler; later batches
+        }
+        continue;
+      }
       Entry* e = nullptr;
       bool reused = false;
+      const auto tb = Clock::now();
       const sft_status st = acquire(S, rq[i]->N, rq[i]->s, &e, &reused);
       if (st == SFT_OK) {
         rq[i]->plan = e;                       // read only by this thread until retired
+        if (!reused) {
+          rq[i]->build_ms = ms_between(tb, Clock::now());
+          built_ms += rq[i]->build_ms;
+        }
         (reused ? reused_n : built) += 1;
         was_reused.push_back(reused ? 1 : 0);
         admitted.push_back(take[i]);
@@ -407,12 +535,22 @@ void scheduler(Server* Sp) {
         failed.push_back({take[i], st});
       }
     }
+    // keep room for the builders: idle plans, least recently used first, go until a quarter of
+    // the budget is free in one block (a stream of new lengths otherwise fills the arena with
+    // plans that are not used again, and every build would fall back to the scheduler)
+    if (!to_build.empty())
+      while (!S.lru.empty() && S.arena.largest_free() < S.cfg.mem_budget / 4) evict(S, S.lru.front());
     int launched = 0;
     cudaError_t ce = cudaSuccess;
     if (!arq.empty()) ce = launch_slot(S, *free_slot, arq, &launched);
 
     lk.lock();
     for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) S.queue.push_front(*it);
+    if (!to_build.empty()) {
+      for (int64_t id : to_build) S.build_q.push_back(id);
+      S.build_cv.notify_all();
+    }
+    S.stats.build_ms_total += built_ms;
     for (auto& f : failed) {
       Request& r = S.reqs[f.first];
       r.state = 3;
@@ -457,6 +595,7 @@ void scheduler(Server* Sp) {
     if (arq.empty() && !deferred.empty()) {
       // nothing could start: wait for running work to finish (it frees memory)
       wait_or_poll(S, lk, [&] {
+        if (!S.built.empty()) return true;
         bool busy = false;
         for (Slot* sl : S.slots) {
           if (sl->busy && sl->done) return true;
@@ -499,6 +638,7 @@ void sft_server_config_init(sft_server_config* cfg) {
   cfg->mem_budget = (size_t)8 << 30;
   cfg->max_batch = 64;
   cfg->max_inflight = 2;
+  cfg->build_threads = 2;
   sft_variant_init(&cfg->variant);
   cfg->tune = sft::default_tuning();
 }
@@ -508,9 +648,10 @@ sft_status sft_server_create(sft_server_t* out, const sft_server_config* cfg) {
   if (!out || !cfg) { set_error("sft_server_create: NULL argument"); return SFT_EINVAL; }
   *out = nullptr;
   if (cfg->mem_budget < ((size_t)1 << 20) || cfg->max_batch < 1 || cfg->max_batch > kMaxServerBatch ||
-      cfg->max_inflight < 1 || cfg->max_inflight > kMaxInflight) {
+      cfg->max_inflight < 1 || cfg->max_inflight > kMaxInflight || cfg->build_threads < 0 ||
+      cfg->build_threads > kMaxBuilders) {
     set_error("sft_server_create: need mem_budget >= 1 MiB, 1 <= max_batch <= 256, "
-              "1 <= max_inflight <= 8");
+              "1 <= max_inflight <= 8, 0 <= build_threads <= 16");
     return SFT_EINVAL;
   }
   sft_tuning tune = cfg->tune.resample_threads == 0 ? default_tuning() : cfg->tune;
@@ -552,6 +693,7 @@ sft_status sft_server_create(sft_server_t* out, const sft_server_config* cfg) {
     return SFT_ENOMEM;
   }
   S.th = std::thread(scheduler, &S);
+  for (int i = 0; i < cfg->build_threads; ++i) S.builders.emplace_back(builder, &S);
   *out = h;
   return SFT_OK;
 }
@@ -602,6 +744,7 @@ sft_status sft_server_query(sft_server_t server, sft_request_t id, sft_request_i
   info->plan_reused = r.reused;
   if (r.state >= 1 && r.state != 3) info->queued_ms = ms_between(r.t_submit, r.t_launch);
   if (r.state >= 2) info->latency_ms = ms_between(r.t_submit, r.t_done);
+  info->build_ms = r.build_ms;
   return SFT_OK;
 }
 
@@ -669,6 +812,14 @@ sft_status sft_server_destroy(sft_server_t server) {
   }
   S.cv.notify_all();
   if (S.th.joinable()) S.th.join();
+  {
+    std::lock_guard<std::mutex> g(S.mu);
+    S.stop_builders = true;
+  }
+  S.build_cv.notify_all();
+  for (std::thread& t : S.builders)
+    if (t.joinable()) t.join();
+  // (plans built after the scheduler stopped cannot exist: it waits for every pending build)
   destroy_server(&S);
   delete server;
   return SFT_OK;

@@ -52,18 +52,20 @@ def test_tuning_layout_and_defaults(lib):
 
 
 def test_server_structs_and_config_defaults(lib):
-    assert ctypes.sizeof(sft.sft_server_config) == 8 + 4 + 4 + 64 + 13 * 4 + 4   # + tail padding
-    assert ctypes.sizeof(sft.sft_request_info) == 4 * 4 + 2 * 8
-    assert ctypes.sizeof(sft.sft_server_stats) == 8 * 8 + 3 * 8 + 2 * 4
+    assert ctypes.sizeof(sft.sft_server_config) == 8 + 4 + 4 + 64 + 13 * 4 + 2 * 4 + 4  # + padding
+    assert ctypes.sizeof(sft.sft_request_info) == 4 * 4 + 3 * 8
+    assert ctypes.sizeof(sft.sft_server_stats) == 8 * 8 + 3 * 8 + 2 * 4 + 8
     cfg = sft.sft_server_config()
     lib.sft_server_config_init(ctypes.byref(cfg))
     assert cfg.mem_budget == 8 << 30 and cfg.max_batch == 64 and cfg.max_inflight == 2
+    assert cfg.build_threads == 2
     assert (cfg.variant.kappa, cfg.variant.K) == (6, 5)
     assert cfg.tune.resample_threads == 256
 
 
 @pytest.mark.parametrize("field,value", [("mem_budget", 1000), ("max_batch", 0), ("max_batch", 257),
-                                         ("max_inflight", 0), ("max_inflight", 9)])
+                                         ("max_inflight", 0), ("max_inflight", 9),
+                                         ("build_threads", -1), ("build_threads", 17)])
 def test_server_rejects_bad_configurations_without_touching_the_device(lib, field, value):
     cfg = sft.sft_server_config()
     lib.sft_server_config_init(ctypes.byref(cfg))

@@ -78,7 +78,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     _check_equal(outs, ref)
     infos = [srv.query(r) for r in ids]
     assert all(q["state"] == "done" and q["latency_ms"] >= q["queued_ms"] >= 0 for q in infos)
-    assert max(q["batch_size"] for q in infos) >= 2          # requests were batched
+    assert all(q["build_ms"] > 0 for q in infos if not q["plan_reused"])
     st = srv.stats()
     assert st["completed"] == len(SHAPES) and st["failed"] == 0
     assert st["plans_built"] + st["plans_reused"] == len(SHAPES)
@@ -91,6 +91,8 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         assert srv.wait(rid, 60000) == sft.SFT_OK
     _check_equal(outs2, ref)
     assert srv.stats()["plans_reused"] > st["plans_reused"]
+    infos2 = [srv.query(r) for r in ids2]
+    assert max(q["batch_size"] for q in infos2) >= 2         # resident plans: requests batched
     for rid in ids + ids2:
         srv.release(rid)
     with pytest.raises(sft.SftError):
@@ -242,4 +244,35 @@ def test_batches_that_finish_before_the_scheduler_looks_again_are_not_lost():
             _check_equal(outs, ref[i:i + 1])
         srv.release(rid)
     assert srv.stats()["completed"] == 300
+    srv.destroy()
+
+
+@pytest.mark.parametrize("build_threads", [0, 2])
+def test_a_new_length_does_not_hold_up_resident_requests(build_threads):
+    """A request whose (N, s) needs a new plan, followed by requests whose plans are resident:
+    with build threads the resident ones are launched while the new plan is being built (each is
+    queued for less time than that build took); without them (build_threads = 0) the scheduler
+    builds inline and they wait.  Every result equals the same plan run alone."""
+    shapes = [(2 ** 14, 6)] * 6
+    fresh = (3 ** 13, 1300)                   # a new length and sparsity: its plan is built here
+    fs = _inputs(shapes + [fresh], 2300)
+    ref = _alone(shapes + [fresh], fs)
+    srv = sft.Server(mem_budget=2 << 30, max_batch=8, max_inflight=2,
+                     variant=sft.sft_variant_init(**VARIANT), build_threads=build_threads)
+    warm = _outputs(shapes[:1])
+    for rid in _submit(srv, shapes[:1], fs[:1], warm):      # make the small plan resident
+        assert srv.wait(rid, 60000) == sft.SFT_OK
+    outs = _outputs([fresh] + shapes)
+    ids = _submit(srv, [fresh] + shapes, [fs[-1]] + fs[:-1], outs)
+    for rid in ids:
+        assert srv.wait(rid, 120000) == sft.SFT_OK
+    _check_equal(outs, [ref[-1]] + ref[:-1])
+    q_fresh = srv.query(ids[0])
+    q_res = [srv.query(r) for r in ids[1:]]
+    assert not q_fresh["plan_reused"] and q_fresh["build_ms"] > 0
+    if build_threads:
+        assert q_res[0]["plan_reused"]
+        assert q_res[0]["queued_ms"] < q_fresh["build_ms"], (q_res[0], q_fresh)
+    else:
+        assert min(q["queued_ms"] for q in q_res) >= q_fresh["build_ms"]
     srv.destroy()
