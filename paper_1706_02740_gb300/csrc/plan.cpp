@@ -655,6 +655,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   char* base = nullptr;
   cudaError_t e = cudaSuccess;
   P->mem = mem;
+  P->want_bytes = total;
   if (mem) {
     base = static_cast<char*>(mem->alloc(total));
     if (!base) {

@@ -62,7 +62,6 @@ class DeviceArena final : public DeviceMemory {
   }
   void* alloc(size_t bytes) override {
     std::lock_guard<std::mutex> g(mu_);
-    last_request_ = bytes;
     const int64_t off = book_.alloc(bytes);
     return off < 0 ? nullptr : base_ + off;
   }
@@ -75,7 +74,6 @@ class DeviceArena final : public DeviceMemory {
     cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st_);
     return e == cudaSuccess ? cudaStreamSynchronize(st_) : e;
   }
-  size_t last_request() { std::lock_guard<std::mutex> g(mu_); return last_request_; }
   size_t largest_free() { std::lock_guard<std::mutex> g(mu_); return book_.largest_free(); }
   void usage(size_t* cap, size_t* used, size_t* peak) {
     std::lock_guard<std::mutex> g(mu_);
@@ -88,7 +86,6 @@ class DeviceArena final : public DeviceMemory {
   char* base_ = nullptr;
   cudaStream_t st_ = nullptr;
   OffsetArena book_;
-  size_t last_request_ = 0;
   std::mutex mu_, up_mu_;
 };
 
@@ -163,6 +160,11 @@ struct Server {
   std::vector<Built> built;
   int building = 0;
   bool stop_builders = false;
+  // shutdown: sft_server_destroy waits for the scheduler; past its limit it sets `abort`, and the
+  // scheduler fails what is queued instead of running it
+  bool abort = false;
+  bool exited = false;
+  std::condition_variable exit_cv;
 };
 
 // Builder thread: takes a request id, builds its plan from the arena (thread-safe) with the
@@ -289,15 +291,18 @@ sft_status acquire(Server& S, int64_t N, int32_t s, Entry** out, bool* reused) {
   for (;;) {
     sft_status st = build_plan(&e->P, N, s, &S.cfg.variant, 0, nullptr, 0, nullptr, 0, &S.arena);
     if (st == SFT_OK) break;
+    const size_t need = e->P.want_bytes;
     free_plan(&e->P);
     e->P = Plan();
     if (st != SFT_ENOMEM || S.lru.empty()) {
       delete e;
       return st;
     }
-    // evict until a block of the requested size is free, then build again
-    const size_t need = S.arena.last_request();
-    while (!S.lru.empty() && S.arena.largest_free() < need) evict(S, S.lru.front());
+    // evict at least one idle plan, and on until a block of this plan's size is free (builders
+    // allocate concurrently, so the retry may still miss), then build again
+    do {
+      evict(S, S.lru.front());
+    } while (!S.lru.empty() && S.arena.largest_free() < need);
   }
   e->N = N;
   e->s = s;
@@ -402,6 +407,20 @@ void scheduler(Server* Sp) {
   std::unique_lock<std::mutex> lk(S.mu);
   for (;;) {
     take_built(S);
+    if (S.abort) {
+      // shutdown past its limit: fail what has not started, finish what runs, then stop
+      for (std::deque<int64_t>* q : {&S.queue, &S.build_q})
+        for (int64_t id : *q) {
+          Request& r = S.reqs[id];
+          r.state = 3;
+          r.status = SFT_ETIMEOUT;
+          r.t_done = Clock::now();
+          ++S.stats.failed;
+        }
+      S.queue.clear();
+      S.build_q.clear();
+      S.done_cv.notify_all();
+    }
     // retire finished slots
     bool retired = false;
     for (Slot* sl : S.slots) {
@@ -454,6 +473,16 @@ void scheduler(Server* Sp) {
     }
     const bool builds_pending = !S.build_q.empty() || S.building > 0 || !S.built.empty();
     if (S.stop && S.queue.empty() && !any_busy && !builds_pending) break;
+    if (S.abort && S.queue.empty()) {
+      if (!any_busy && !builds_pending) break;
+      wait_or_poll(S, lk, [&] {
+        if (!S.built.empty()) return true;
+        for (Slot* sl : S.slots)
+          if (sl->busy && sl->done) return true;
+        return false;
+      });
+      continue;
+    }
     if (!free_slot || S.queue.empty()) {
       wait_or_poll(S, lk, [&] {
         if (!S.built.empty()) return true;
@@ -469,14 +498,30 @@ void scheduler(Server* Sp) {
       });
       continue;
     }
-    // take up to max_batch queued requests, in arrival order
+    // take up to max_batch queued requests: first those whose plan was built for them (they need
+    // no memory, and the memory their plans hold comes free only once they run), then the rest
+    // in arrival order.  (Taking in arrival order alone can fill the batch with requests that
+    // wait for memory held by the ready ones behind them, and nothing would ever run.)
     std::vector<int64_t> take;
+    for (auto it = S.queue.begin(); it != S.queue.end() && (int)take.size() < S.cfg.max_batch;) {
+      if (S.reqs[*it].plan) {
+        take.push_back(*it);
+        it = S.queue.erase(it);
+      } else {
+        ++it;
+      }
+    }
     while (!S.queue.empty() && (int)take.size() < S.cfg.max_batch) {
       take.push_back(S.queue.front());
       S.queue.pop_front();
     }
     std::vector<Request*> rq;
     for (int64_t id : take) rq.push_back(&S.reqs[id]);   // records stay put until released
+    // arena memory that will come free: plans of running batches, of requests whose plan was
+    // built for them and waits to run, and of builds in flight
+    bool held = any_busy || S.building > 0 || !S.build_q.empty() || !S.built.empty();
+    for (Request* r : rq) held = held || r->plan != nullptr;
+    for (int64_t id : S.queue) held = held || S.reqs[id].plan != nullptr;
     // Claim the slot before its work exists: its completion callback may fire before this thread
     // takes the lock again, and must find the slot busy with `done` clear so the completion is
     // not overwritten.
@@ -529,7 +574,7 @@ void scheduler(Server* Sp) {
         was_reused.push_back(reused ? 1 : 0);
         admitted.push_back(take[i]);
         arq.push_back(rq[i]);
-      } else if (st == SFT_ENOMEM && (any_busy || !admitted.empty())) {
+      } else if (st == SFT_ENOMEM && (held || !admitted.empty())) {
         deferred.push_back(take[i]);           // memory frees up when running work finishes
       } else {
         failed.push_back({take[i], st});
@@ -593,7 +638,8 @@ void scheduler(Server* Sp) {
     }
     if (!failed.empty() || ce != cudaSuccess) S.done_cv.notify_all();
     if (arq.empty() && !deferred.empty()) {
-      // nothing could start: wait for running work to finish (it frees memory)
+      // nothing could start: wait for running work or a build to finish (either frees memory
+      // or brings a plan)
       wait_or_poll(S, lk, [&] {
         if (!S.built.empty()) return true;
         bool busy = false;
@@ -601,10 +647,12 @@ void scheduler(Server* Sp) {
           if (sl->busy && sl->done) return true;
           busy = busy || sl->busy;
         }
-        return !busy;
+        return !busy && S.building == 0 && S.build_q.empty();
       });
     }
   }
+  S.exited = true;
+  S.exit_cv.notify_all();
 }
 
 void destroy_server(Server* S) {
@@ -811,6 +859,15 @@ sft_status sft_server_destroy(sft_server_t server) {
     S.stop = true;
   }
   S.cv.notify_all();
+  {
+    // queued and running requests finish; past a minute without the scheduler exiting, what has
+    // not started fails (SFT_ETIMEOUT) and the scheduler stops after the running work
+    std::unique_lock<std::mutex> lk(S.mu);
+    if (!S.exit_cv.wait_for(lk, std::chrono::seconds(60), [&] { return S.exited; })) {
+      S.abort = true;
+      S.cv.notify_all();
+    }
+  }
   if (S.th.joinable()) S.th.join();
   {
     std::lock_guard<std::mutex> g(S.mu);
@@ -819,7 +876,13 @@ sft_status sft_server_destroy(sft_server_t server) {
   S.build_cv.notify_all();
   for (std::thread& t : S.builders)
     if (t.joinable()) t.join();
-  // (plans built after the scheduler stopped cannot exist: it waits for every pending build)
+  // plans a builder finished after an aborted scheduler stopped were never made resident
+  for (Built& b : S.built)
+    if (b.e) {
+      free_plan(&b.e->P);
+      delete b.e;
+    }
+  S.built.clear();
   destroy_server(&S);
   delete server;
   return SFT_OK;

@@ -336,6 +336,7 @@ struct Plan {
   std::vector<int64_t> shifts;
   std::vector<int32_t> primes, small;
   size_t device_bytes = 0;
+  size_t want_bytes = 0;         // device bytes the last build asked for (set even when it failed)
   std::vector<void*> allocations;
   DeviceMemory* mem = nullptr;   // nullptr: allocations came from cudaMalloc
   int device = 0;
