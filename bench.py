@@ -65,6 +65,7 @@ def parse():
                     help="prime pool of the plans: all primes, or those whose p - 1 is 13-smooth "
                          "(Rader's form of the DFTs)")
     ap.add_argument("--s-list", default="", help="sweep-s: comma-separated s values to run")
+    ap.add_argument("--rung", default="", help="studies: fixed 'K,c_p' instead of the ladder")
     ap.add_argument("--precision-trials", type=int, default=10,
                     help="seeded inputs of the precision study compared with the oracle")
     ap.add_argument("--batched-signals", type=int, default=4096)
@@ -352,6 +353,17 @@ def run_ours(args, rank, world, local_rank):
         return sorted(a.elapsed_time(b) for a, b in ev) or [float("nan")]
     single_graph = single_latency(True)
     single = single_latency(False)
+    # where one SFT's time goes: per-stage CUDA events of direct launches, one SFT at a time
+    single_stages = None
+    if not args.timed_only:
+        sft.sft_plan_profile(p0, True)
+        for i in range(20):
+            sft.sft_execute(p0, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
+                            stream.cuda_stream)
+        torch.cuda.synchronize()
+        st_ms, cnt = sft.sft_plan_profile_read(p0)
+        sft.sft_plan_profile(p0, False)
+        single_stages = {k: round(1e3 * v / max(cnt, 1), 1) for k, v in st_ms.items()}
 
     # per-stage times: CUDA events between the stages, direct launches (the graph has none)
     n_prof = 0 if args.timed_only else 10
@@ -592,6 +604,7 @@ def run_ours(args, rank, world, local_rank):
         "config": dict(workload_config(args, B), tuning=tuning, graph=True),
         "latency_ms": {"p50": pct(single, 0.5), "p99": pct(single, 0.99),
                        "plan_graph_p50": pct(single_graph, 0.5),
+                       "stages_us_one_sft": single_stages,
                        "what": "device time of one SFT executed alone (sft_execute, direct launches "
                                "with programmatic dependent launch; 20 warm-ups, 128 timed, 16 "
                                "rotating inputs); plan_graph_p50: the plan's CUDA graph instead"},
@@ -1093,8 +1106,12 @@ def run_study(args):
                 "ms_p50": float(np.median(times)), "exact_support": ok / trials,
                 "avg_l1_error": float(np.mean(l1)) if l1 else None, "stages_us": st}
 
+    if args.rung:
+        K0, c0 = args.rung.split(",")
+        ladder = [(int(K0), float(c0))]
     for N, s, snr in points:
-        rec = {"study": args.study, "N": N, "s": s, "snr_db": snr, "trials": args.trials}
+        rec = {"study": args.study, "N": N, "s": s, "snr_db": snr, "trials": args.trials,
+               "ladder": ladder}
         for kappa in (4, 6):
             best = None
             for K, c_p in ladder:
