@@ -353,6 +353,28 @@ def run_ours(args, rank, world, local_rank):
         return sorted(a.elapsed_time(b) for a, b in ev) or [float("nan")]
     single_graph = single_latency(True)
     single = single_latency(False)
+    # the same without the FP32 path's refinement (refine_fp64 = 0): lower latency, the FP32
+    # medians as they are (their error against the oracle is in precision.no_refinement)
+    p_nr = sft.sft_plan(N, s, sft.sft_variant_init(**dict(
+        precision=sft.SFT_FP32, kappa=PLAN["kappa"], K=PLAN["K"], c_p=PLAN["c_p"],
+        alpha=PLAN["alpha"], beta=PLAN["beta"], seed=PLAN["seed"], pool=POOLS[PLAN["pool"]],
+        refine_fp64=0)))
+    single_nr = []
+    if not args.timed_only:
+        for i in range(20):
+            sft.sft_execute(p_nr, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
+                            stream.cuda_stream)
+        torch.cuda.synchronize()
+        for i in range(128):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            sft.sft_execute(p_nr, inputs[i % n_in].data_ptr(), w_ptrs[0], c_ptrs[0], n_ptrs[0],
+                            stream.cuda_stream)
+            b.record()
+            torch.cuda.synchronize()
+            single_nr.append(a.elapsed_time(b))
+        single_nr.sort()
+    p_nr.destroy()
     # where one SFT's time goes: per-stage CUDA events of direct launches, one SFT at a time
     single_stages = None
     if not args.timed_only:
@@ -605,6 +627,7 @@ def run_ours(args, rank, world, local_rank):
         "latency_ms": {"p50": pct(single, 0.5), "p99": pct(single, 0.99),
                        "plan_graph_p50": pct(single_graph, 0.5),
                        "stages_us_one_sft": single_stages,
+                       "p50_without_refinement": (pct(single_nr, 0.5) if single_nr else None),
                        "what": "device time of one SFT executed alone (sft_execute, direct launches "
                                "with programmatic dependent launch; 20 warm-ups, 128 timed, 16 "
                                "rotating inputs); plan_graph_p50: the plan's CUDA graph instead"},
@@ -1238,6 +1261,13 @@ def cpu_and_precision(args, dev, sft, var):
                      "thread)"}
     precision = precision_vs_oracle(gpu0["freqs"], gpu0["coefs"], gpu0["count"], res0)
     precision["residual_energy"] = rho
+    var_nr = sft.sft_variant_init(precision=var.precision, kappa=var.kappa, K=var.K, c_p=var.c_p,
+                                  alpha=var.alpha, beta=var.beta, seed=var.seed, pool=var.pool,
+                                  refine_fp64=0)
+    gpu_nr, _, _ = _gpu_trial(args, dev, sft, var_nr, 0)
+    nr = precision_vs_oracle(gpu_nr["freqs"], gpu_nr["coefs"], gpu_nr["count"], res0)
+    precision["no_refinement"] = {k: nr[k] for k in ("support_common", "support_differs",
+                                                     "rel_err_max", "rel_err_p50", "rel_err_p99")}
     precision["noise_energy_share"] = 1.0 / (1.0 + 10.0 ** 3.0)   # SNR 30 dB
     trials = [_precision_record(gpu0, res0, 0)]
     for k in ("vs", "tolerance"):
