@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--only", choices=["batched", "serving"], default=None,
                     help="run one extra leg alone and print its JSON")
-    ap.add_argument("--study", choices=["sweep-n", "sweep-s", "noise"], default=None,
+    ap.add_argument("--study", choices=["sweep-n", "sweep-s", "noise", "theorem"], default=None,
                     help="the paper's experiments instead of the bench line (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
     ap.add_argument("--pool", choices=sorted(POOLS), default="all",
@@ -1033,6 +1033,80 @@ def serving_fresh_lengths(args, dev, sft, variant, seed, capacity_resident):
 # ------------------------------------------------------------------------------------------
 # the paper's experiments (Section 5): runtime against N and s, noise robustness
 # ------------------------------------------------------------------------------------------
+def run_theorem_study(args, sft, dev):
+    """Theorem total_convolution_error's parameters (beta = 6 sqrt(r), half-width
+    ceil(6 r ln N / (sqrt 2 pi)) + 1) at N = 2^26, s = 1000 on the precision-study inputs: one
+    request alone (device time, plan graph) and batches of 16 (graph replay over 4 rotating inputs),
+    with the stage times and the generic gather kernel's algorithmic bytes against the measured
+    copy bandwidth."""
+    import torch
+    from synth.device_signals import make_device_signal
+    N, s, B = args.N, args.s, 16
+    peaks, _ = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    inputs = [make_device_signal(N, s, 3000 + i, "loguniform", 30.0, dev)[0] for i in range(4)]
+    torch.cuda.synchronize()
+    for r in (1.0, 1.5):                      # half-widths 26 and 38 at N = 2^26 (at most 48)
+        v = sft.sft_variant_theorem(N, r, K=5, c_p=3.0, seed=1)
+        plans = [sft.sft_plan(N, s, v) for _ in range(B)]
+        info = plans[0].info()
+        w = torch.empty(B, s, dtype=torch.int64, device=dev)
+        c = torch.empty(B, s, dtype=torch.complex128, device=dev)
+        n = torch.empty(B, dtype=torch.int32, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        p0 = plans[0]
+        sft.sft_plan_graph(p0, True)
+        lat = []
+        for i in range(25):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            sft.sft_execute(p0, inputs[i % 4].data_ptr(), w[0].data_ptr(), c[0].data_ptr(),
+                            n[0].data_ptr(), st)
+            b.record()
+            torch.cuda.synchronize()
+            if i >= 5:
+                lat.append(a.elapsed_time(b))
+        sft.sft_plan_graph(p0, False)
+        batch = sft.Batch(plans)
+        ws = [w[i].data_ptr() for i in range(B)]
+        cs = [c[i].data_ptr() for i in range(B)]
+        ns = [n[i:i + 1].data_ptr() for i in range(B)]
+
+        def step(k):
+            batch.execute([inputs[(k * B + i) % 4].data_ptr() for i in range(B)], ws, cs, ns, st)
+        batch.profile(True)
+        for k in range(5):
+            step(k)
+        torch.cuda.synchronize()
+        stage_ms, cnt = batch.profile_read()
+        batch.profile(False)
+        batch.graph(True)
+        for k in range(3):
+            step(k)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(10):
+            step(k)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        per = {k: 1e3 * v / max(cnt, 1) for k, v in stage_ms.items()}
+        gbytes = B * 8 * (2 * info["kappa"] + 1) * info["nodes"]
+        print(json.dumps({"study": "theorem", "N": N, "s": s, "r": r, "kappa": info["kappa"],
+                          "taps": 2 * info["kappa"] + 1, "beta": v.beta,
+                          "single_ms_p50": sorted(lat)[len(lat) // 2],
+                          "batch": B, "ms_per_batch": ms, "sfts_per_s": 1e3 * B / ms,
+                          "stages_us_per_batch": {k: round(x, 1) for k, x in per.items()},
+                          "gather_algorithmic_tbs": gbytes / (per["resample"] * 1e-6) / 1e12,
+                          "gather_frac_of_measured_hbm": gbytes / (per["resample"] * 1e-6) / 1e9 / hbm}),
+              flush=True)
+        batch.graph(False)
+        batch.destroy()
+        for p in plans:
+            p.destroy()
+
+
 def run_study(args):
     """sweep-n: s = 50, N = 2^16 .. 2^30 (Section 5.2); sweep-s: N = 2^26, s = 50 .. 4000
     (Section 5.3); noise: N = 2^22, s = 50, SNR 0 .. 80 dB, average L1 error over the trials whose
@@ -1050,6 +1124,9 @@ def run_study(args):
     from synth.device_signals import make_device_signal
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.study == "theorem":
+        run_theorem_study(args, sft, dev)
+        return
     if args.study == "sweep-n":
         points = [(2 ** e, 50, None) for e in range(16, 31, 2)]
     elif args.study == "sweep-s":

@@ -107,3 +107,30 @@ def test_config2_n2p22_and_prime(N, prec):
     _compare(g, res, cand, 1e-5 if prec == U.FP32 else 1e-11)
     hits = len(set(g["freqs"][: g["count"]].tolist()) & set(sig.omega.tolist()))
     assert hits >= s - 2
+
+
+def test_fp32_refinement_headroom_over_three_decades():
+    """The FP32 path's re-estimation against the oracle with magnitudes log-uniform over three
+    decades (C3 spans two): N = 2^22, s = 256, SNR 40 dB.  The support equals the oracle's (or
+    differs only by explained frequencies); the relative error of a coefficient grows as its
+    magnitude falls (the re-estimation works from FP32 samples, whose rounding is about eps times
+    the samples' size, so a coefficient's relative error scales as 1 / |c|): within 1e-5 for every
+    coefficient at least 1e-2 of the largest (C3's range), within 1e-4 below that."""
+    N, s = 2 ** 22, 256
+    sig = make_signal(N, s, 3900, "loguniform", 40.0, mag_range=(1e-3, 1.0))
+    f32 = as_complex64(sig.f)
+    g, cand = _run(N, s, f32, U.FP32, 5, 3.0, 9)
+    res = _oracle(("headroom", 0), upcast(f32), g["info"], N, s)
+    U.explain_output_differences(g, res, cand, g["info"], 1e-4, log=print)
+    n = g["count"]
+    gmap = dict(zip(g["freqs"][:n].tolist(), g["coefs"][:n]))
+    omap = dict(zip(res.freqs.tolist(), res.coefs))
+    common = sorted(set(gmap) & set(omap))
+    top = max(abs(c) for c in omap.values())
+    rel = {w: abs(gmap[w] - omap[w]) / abs(omap[w]) for w in common}
+    strong = [rel[w] for w in common if abs(omap[w]) >= 1e-2 * top]
+    weak = [rel[w] for w in common if abs(omap[w]) < 1e-2 * top]
+    print(f"headroom: {len(strong)} coefficients >= 1e-2 of the largest, max rel err "
+          f"{max(strong):.2e}; {len(weak)} below, max rel err {max(weak) if weak else 0:.2e}")
+    assert max(strong) <= 1e-5
+    assert not weak or max(weak) <= 1e-4
