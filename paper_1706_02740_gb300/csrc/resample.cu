@@ -196,14 +196,30 @@ resample_kernel(BatchView bv) {
   }
 }
 
-// Any window half-width up to kMaxKappa (theorem-parameter mode): scalar loads, runtime loops.
+// Shifts accumulated together by the wide-window kernel (more shifts run in further groups, the
+// window then read again from cache).
+constexpr int kWideShifts = 16;
+constexpr int kWideChunk = 8;     // window taps loaded together
+
+// Any window half-width up to kMaxKappa (theorem-parameter mode): the window in chunks of taps
+// loaded together, the shifts in groups with register accumulators.
 template <typename R, typename IN>
 __global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_generic(BatchView bv) {
   pdl_begin();
   using C = typename Cx<R>::T;
+  // the shift-phase table e^{-2 pi i (q i mod N) / N} [shifts][taps] in shared memory: every node
+  // reads all of it (uniform addresses)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   int lb, nb;
   const int b = batch_signal(bv, lb, nb);
   const DevPlan& d = bv.plans[b];
+  {
+    const C* Tg = reinterpret_cast<const C*>(d.Ttab);
+    C* Ts = reinterpret_cast<C*>(smem_raw);
+    const int n = d.nq * (2 * d.kappa + 1);
+    for (int i = threadIdx.x; i < n; i += kResampleGenericThreads) Ts[i] = __ldg(Tg + i);
+    __syncthreads();
+  }
   const int64_t node = (int64_t)lb * kResampleGenericThreads + threadIdx.x;
   if (node >= d.m) return;
   const IN* __restrict__ f = reinterpret_cast<const IN*>(batch_f(bv, b));
@@ -213,20 +229,46 @@ __global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_gener
   const int KAPPA = d.kappa, W = 2 * KAPPA + 1;
   const R v0 = (R)g.d0 / (R)g.PP;
   const R gam = gamma_of<R>(d), G0 = g0_of<R>(d);
-  const C* T = reinterpret_cast<const C*>(d.Ttab);
+  const C* T = reinterpret_cast<const C*>(smem_raw);
   C* out = reinterpret_cast<C*>(d.samples);
-  C acc[kMaxQ];
-  for (int qi = 0; qi < d.nq; ++qi) acc[qi] = czero<C>();
-  for (int i = 0; i < W; ++i) {
-    int64_t idx = g.jp - KAPPA + i;
-    if (idx < 0) idx += d.N;
-    if (idx >= d.N) idx -= d.N;
-    const R v = v0 - (R)(i - KAPPA);
-    const C fw = cscale(widen<R, C, IN>(InLoad<IN>::one(f, idx)), G0 * r_exp(-gam * v * v));
-    for (int qi = 0; qi < d.nq; ++qi) acc[qi] = cadd(acc[qi], cmul(fw, __ldg(T + qi * W + i)));
+  const int64_t start = g.jp - KAPPA;
+  const bool inside = start >= 0 && start + W <= d.N;       // no wrap around the ends of f
+  for (int q0 = 0; q0 < d.nq; q0 += kWideShifts) {
+    C acc[kWideShifts];
+#pragma unroll
+    for (int t = 0; t < kWideShifts; ++t) acc[t] = czero<C>();
+    for (int i0 = 0; i0 < W; i0 += kWideChunk) {
+      // the chunk's window values first (independent loads in flight), then the arithmetic
+      C fw[kWideChunk];
+#pragma unroll
+      for (int u = 0; u < kWideChunk; ++u) {
+        const int i = i0 + u;
+        fw[u] = czero<C>();
+        if (i < W) {
+          int64_t idx = start + i;
+          if (!inside) {
+            if (idx < 0) idx += d.N;
+            if (idx >= d.N) idx -= d.N;
+          }
+          fw[u] = widen<R, C, IN>(InLoad<IN>::one(f, idx));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kWideChunk; ++u) {
+        const int i = i0 + u;
+        if (i >= W) break;
+        const R v = v0 - (R)(i - KAPPA);
+        const C x = cscale(fw[u], G0 * r_exp(-gam * v * v));
+#pragma unroll
+        for (int t = 0; t < kWideShifts; ++t)
+          if (q0 + t < d.nq) acc[t] = cadd(acc[t], cmul(x, T[(q0 + t) * W + i]));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kWideShifts; ++t)
+      if (q0 + t < d.nq)
+        out[(int64_t)(q0 + t) * d.m + node] = cmul(acc[t], node_phase(d, q0 + t, v0, g));
   }
-  for (int qi = 0; qi < d.nq; ++qi)
-    out[(int64_t)qi * d.m + node] = cmul(acc[qi], node_phase(d, qi, v0, g));
 }
 
 template <typename R, typename IN>
@@ -245,7 +287,11 @@ cudaError_t launch_typed(const DevPlan& d0, const BatchView& bv, const LaunchSet
     if (cap) (void)launch_pdl(resample_kernel<4, R, IN, 1>, grid, t, 0, st, v);
     else (void)launch_pdl(resample_kernel<4, R, IN, 0>, grid, t, 0, st, v);
   } else {
-    (void)launch_pdl(resample_kernel_generic<R, IN>, grid, kResampleGenericThreads, 0, st, v);
+    // room for the largest shift table of the batch (the signals share kappa; at most kMaxQ shifts)
+    const size_t smem = (size_t)kMaxQ * (2 * d0.kappa + 1) * sizeof(typename Cx<R>::T);
+    const cudaError_t e = ensure_dynamic_smem<resample_kernel_generic<R, IN>>(smem);
+    if (e != cudaSuccess) return e;
+    (void)launch_pdl(resample_kernel_generic<R, IN>, grid, kResampleGenericThreads, smem, st, v);
   }
   return cudaGetLastError();
 }
