@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--only", choices=["batched", "serving"], default=None,
                     help="run one extra leg alone and print its JSON")
-    ap.add_argument("--study", choices=["sweep-n", "sweep-s", "noise", "theorem"], default=None,
+    ap.add_argument("--study", choices=["sweep-n", "sweep-s", "noise", "theorem", "config2"], default=None,
                     help="the paper's experiments instead of the bench line (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
     ap.add_argument("--pool", choices=sorted(POOLS), default="all",
@@ -1107,6 +1107,102 @@ def run_theorem_study(args, sft, dev):
             p.destroy()
 
 
+def run_config2_study(args, sft, dev, trials=20):
+    """N = 2^22 and the prime N = 4194301, s = 64, unit magnitudes, random phases, SNR 20 dB,
+    complex64 input, 20 seeded trials: the FP32 path and the FP64 path (the same input widened to
+    complex128) with K = 5, c_p = 3, kappa = 6, and a cuFFT C2C of the same input (alone, and with
+    the (-1)^w/N rescale and top-s).  Per path: device time of one request alone (the plan's CUDA
+    graph replayed; median over the trials), the trials whose support equals the generating one,
+    the average L1 error over those trials (Section 5.4's measure), and the largest relative
+    difference between the FP32 and FP64 paths' coefficients on their common frequencies."""
+    import numpy as np
+    import torch
+    from synth.device_signals import make_device_signal
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stream = lambda: torch.cuda.current_stream().cuda_stream
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return min(out)
+
+    s = 64
+    for N in (2 ** 22, 4194301):
+        plans = {name: sft.sft_plan(N, s, sft.sft_variant_init(precision=prec, input=prec, kappa=6,
+                                                                K=5, c_p=3.0, seed=2))
+                 for name, prec in (("fp32", 0), ("fp64", 1))}
+        for pl in plans.values():
+            sft.sft_plan_graph(pl, True)
+        # (-1)^w with w = idx, or idx - N above N/2 (for odd N the two differ in sign)
+        idx_all = torch.arange(N, device=dev)
+        w_all = torch.where(idx_all > N // 2, idx_all - N, idx_all)
+        sign = 1.0 - 2.0 * (w_all % 2).to(torch.float32)
+        del idx_all, w_all
+        rec = {"study": "config2", "N": N, "s": s, "snr_db": 20.0, "trials": trials, "K": 5,
+               "c_p": 3.0, "kappa": 6, "primes": plans["fp32"].info()["primes"]}
+        acc = {k: {"ms": [], "exact": 0, "l1": []} for k in ("fp32", "fp64", "cufft")}
+        cufft_ms, cufft_topk_ms, fp32_vs_fp64 = [], [], 0.0
+        for t in range(trials):
+            f, omega, coef = make_device_signal(N, s, 2000 + t, "unit", 20.0, dev)
+            truth = dict(zip(np.asarray(omega).tolist(), np.asarray(coef)))
+            got = {}
+            for name, pl in plans.items():
+                x = f if name == "fp32" else f.to(torch.complex128)
+                w, c, n = sft.execute_torch(pl, x)
+                acc[name]["ms"].append(timed(lambda: sft.sft_execute(
+                    pl, x.data_ptr(), w.data_ptr(), c.data_ptr(), n.data_ptr(), stream())))
+                nn = int(n.item())
+                got[name] = dict(zip(w.cpu().numpy()[:nn].tolist(), c.cpu().numpy()[:nn]))
+                del x
+            for name in ("fp32", "fp64"):
+                if set(got[name]) == set(truth):
+                    acc[name]["exact"] += 1
+                    acc[name]["l1"].append(sum(abs(truth[k] - got[name][k]) for k in truth) / s)
+            for k in set(got["fp32"]) & set(got["fp64"]):
+                fp32_vs_fp64 = max(fp32_vs_fp64,
+                                   abs(got["fp32"][k] - got["fp64"][k]) / abs(got["fp64"][k]))
+
+            def fft_topk():
+                X = torch.fft.fft(f) * (sign / N)
+                mag = X.real * X.real + X.imag * X.imag
+                return X, torch.topk(mag, s).indices
+            cufft_ms.append(timed(lambda: torch.fft.fft(f)))
+            cufft_topk_ms.append(timed(fft_topk))
+            X, idx = fft_topk()
+            idx = idx.cpu().numpy()
+            Xh = X.cpu().numpy()
+            wts = np.where(idx > N // 2, idx - N, idx)
+            if set(wts.tolist()) == set(truth):
+                acc["cufft"]["exact"] += 1
+                acc["cufft"]["l1"].append(
+                    float(np.mean([abs(truth[int(w_)] - Xh[i]) for w_, i in zip(wts, idx)])))
+            del f, X
+        for name in ("fp32", "fp64"):
+            a = acc[name]
+            rec[name] = {"ms_p50": float(np.median(a["ms"])), "exact_support": a["exact"] / trials,
+                         "avg_l1_error": float(np.mean(a["l1"])) if a["l1"] else None}
+        rec["fp32_vs_fp64_max_rel"] = fp32_vs_fp64
+        rec["cufft"] = {"ms_p50": float(np.median(cufft_ms)),
+                        "topk_ms_p50": float(np.median(cufft_topk_ms)),
+                        "exact_support": acc["cufft"]["exact"] / trials,
+                        "avg_l1_error": float(np.mean(acc["cufft"]["l1"])) if acc["cufft"]["l1"] else None}
+        for pl in plans.values():
+            pl.destroy()
+        del sign
+        torch.backends.cuda.cufft_plan_cache[0].clear()
+        torch.cuda.empty_cache()
+        print(json.dumps(rec), flush=True)
+
+
 def run_study(args):
     """sweep-n: s = 50, N = 2^16 .. 2^30 (Section 5.2); sweep-s: N = 2^26, s = 50 .. 4000
     (Section 5.3); noise: N = 2^22, s = 50, SNR 0 .. 80 dB, average L1 error over the trials whose
@@ -1126,6 +1222,9 @@ def run_study(args):
     torch.cuda.set_device(dev)
     if args.study == "theorem":
         run_theorem_study(args, sft, dev)
+        return
+    if args.study == "config2":
+        run_config2_study(args, sft, dev)
         return
     if args.study == "sweep-n":
         points = [(2 ** e, 50, None) for e in range(16, 31, 2)]
