@@ -67,7 +67,7 @@ __device__ __forceinline__ int residue_t(C z0, const C* Zl, int64_t p, const C* 
   C z[T];
   z[0] = z0;
 #pragma unroll
-  for (int k2 = 1; k2 < T; ++k2) z[k2] = Zl[(int64_t)k2 * p];
+  for (int k2 = 1; k2 < T; ++k2) z[k2] = __ldg(Zl + (int64_t)k2 * p);
   R best = (R)-1;
   int bestu = 1 << 30, bestr = 0;
   auto consider = [&](const C& X, int r, int u) {
@@ -136,7 +136,7 @@ __device__ int residue_any(int t, C z0, const C* Zl, int64_t p, const C* twl, in
     for (int k2 = 1; k2 < t; ++k2) {
       idx += r;
       if (idx >= t) idx -= t;
-      X = cadd(X, cmul(Zl[(int64_t)k2 * p], __ldg(twl + idx)));
+      X = cadd(X, cmul(__ldg(Zl + (int64_t)k2 * p), __ldg(twl + idx)));
     }
     const R m2 = X.x * X.x + X.y * X.y;
     const int u = (((r - bt) % t + t) % t) * pinv % t;
@@ -149,11 +149,45 @@ __device__ int residue_any(int t, C z0, const C* Zl, int64_t p, const C* twl, in
   return bestr;
 }
 
-// The FP32 build is held to 64 registers (two 512-thread CTAs, 32 warps per SM: the kernel waits on
-// its sub-bin loads, so more warps in flight help); the FP64 build would spill there.
+// One small modulus with t = T known at compile time: its residue, then Garner's step
+// x += M_x ((r - x) M_x^{-1} mod T), M_x *= T (divisions by T become multiplications).
+template <int T, typename C, typename R>
+__device__ __forceinline__ int crt_step(const DevPlan& d, int j, int l, int b, C z0, const C* Z,
+                                        int64_t p, const C* tw, int64_t& x, int64_t& Mx) {
+  const C* Zl = Z + (int64_t)(d.subbase[l] - 1) * p;
+  const int r = residue_t<T, C, R>(z0, Zl, p, tw + d.twoff[l], b % T, d.pinv[j * d.nT + l]);
+  const int xm = mod_small(x, T);
+  const int v = ((r - xm + T) % T) * d.garner[j * d.nT + l] % T;
+  x += Mx * v;
+  Mx *= T;
+  return r;
+}
+
+// The small moduli are the first primes 2, 3, 5, ... not among the p_j; when none of the p_j is
+// one of them (every plan with p_1 > 13), they are the first nT of 2, 3, 5, 7, 11, 13 and the
+// whole chain runs with compile-time moduli, fully unrolled; the residues are stored at the end.
+__device__ __forceinline__ int prefix_t(int l) {
+  return l == 0 ? 2 : l == 1 ? 3 : l == 2 ? 5 : l == 3 ? 7 : l == 4 ? 11 : 13;
+}
+
+template <int NT, typename C, typename R>
+__device__ __forceinline__ void crt_prefix(const DevPlan& d, int j, int b, C z0, const C* Z,
+                                           int64_t p, const C* tw, int64_t& x, uint8_t* resid) {
+  int64_t Mx = p;
+  int r[NT];
+  if constexpr (NT >= 1) r[0] = crt_step<2, C, R>(d, j, 0, b, z0, Z, p, tw, x, Mx);
+  if constexpr (NT >= 2) r[1] = crt_step<3, C, R>(d, j, 1, b, z0, Z, p, tw, x, Mx);
+  if constexpr (NT >= 3) r[2] = crt_step<5, C, R>(d, j, 2, b, z0, Z, p, tw, x, Mx);
+  if constexpr (NT >= 4) r[3] = crt_step<7, C, R>(d, j, 3, b, z0, Z, p, tw, x, Mx);
+  if constexpr (NT >= 5) r[4] = crt_step<11, C, R>(d, j, 4, b, z0, Z, p, tw, x, Mx);
+  if constexpr (NT >= 6) r[5] = crt_step<13, C, R>(d, j, 5, b, z0, Z, p, tw, x, Mx);
+#pragma unroll
+  for (int l = 0; l < NT; ++l) resid[l] = (uint8_t)r[l];
+}
+
+// One thread per bin.  The body is shared by the FP32 and FP64 kernels below.
 template <typename R>
-__global__ void __launch_bounds__(kBinMaxThreads, sizeof(R) == 4 ? 2 : 1) identify_kernel(BatchView bv) {
-  pdl_begin();
+__device__ __forceinline__ void identify_bins(const BatchView& bv) {
   using C = typename Cx<R>::T;
   int lb, nb;
   const DevPlan& d = bv.plans[batch_signal(bv, lb, nb)];
@@ -164,34 +198,67 @@ __global__ void __launch_bounds__(kBinMaxThreads, sizeof(R) == 4 ? 2 : 1) identi
   const int p = d.p[j];
   const C* Z = reinterpret_cast<const C*>(d.bins) + (int64_t)qi * d.m + d.nodeoff[j] + b;
   const C* tw = reinterpret_cast<const C*>(d.twsmall);
-  const C z0 = Z[0];
-  int64_t x = b, Mx = p;
-  for (int l = 0; l < d.nT; ++l) {
-    const int t = d.t[l];
-    const C* Zl = Z + (int64_t)(d.subbase[l] - 1) * p;   // Zl[k2 * p] = Z_{k2}[b], k2 >= 1
-    const C* twl = tw + d.twoff[l];
-    const int pinv = d.pinv[j * d.nT + l];
-    const int bt = b % t;
-    int r;
-    switch (t) {
-      case 2: r = residue_t<2, C, R>(z0, Zl, p, twl, bt, pinv); break;
-      case 3: r = residue_t<3, C, R>(z0, Zl, p, twl, bt, pinv); break;
-      case 5: r = residue_t<5, C, R>(z0, Zl, p, twl, bt, pinv); break;
-      case 7: r = residue_t<7, C, R>(z0, Zl, p, twl, bt, pinv); break;
-      case 11: r = residue_t<11, C, R>(z0, Zl, p, twl, bt, pinv); break;
-      case 13: r = residue_t<13, C, R>(z0, Zl, p, twl, bt, pinv); break;
-      default: r = residue_any<C, R>(t, z0, Zl, p, twl, bt, pinv); break;
+  const C z0 = __ldg(Z);
+  int64_t x = b;
+  int prefix = d.nT <= 6 ? d.nT : -1;                     // CTA-uniform: one plan per CTA
+  for (int l = 0; l < d.nT && prefix >= 0; ++l)
+    if (d.t[l] != prefix_t(l)) prefix = -1;
+  if (prefix >= 0) {
+    uint8_t* rs = d.resid + gid * d.nT;
+    switch (prefix) {
+      case 1: crt_prefix<1, C, R>(d, j, b, z0, Z, p, tw, x, rs); break;
+      case 2: crt_prefix<2, C, R>(d, j, b, z0, Z, p, tw, x, rs); break;
+      case 3: crt_prefix<3, C, R>(d, j, b, z0, Z, p, tw, x, rs); break;
+      case 4: crt_prefix<4, C, R>(d, j, b, z0, Z, p, tw, x, rs); break;
+      case 5: crt_prefix<5, C, R>(d, j, b, z0, Z, p, tw, x, rs); break;
+      case 6: crt_prefix<6, C, R>(d, j, b, z0, Z, p, tw, x, rs); break;
+      default: break;                                      // no small modulus: x = b
     }
-    d.resid[gid * d.nT + l] = (uint8_t)r;
-    const int g = d.garner[j * d.nT + l];
-    const int xm = mod_small(x, t);
-    const int v = (((r - xm) % t + t) % t) * g % t;
-    x += Mx * v;
-    Mx *= t;
+  } else {
+    int64_t Mx = p;
+    for (int l = 0; l < d.nT; ++l) {
+      const int t = d.t[l];
+      const C* Zl = Z + (int64_t)(d.subbase[l] - 1) * p;   // Zl[k2 * p] = Z_{k2}[b], k2 >= 1
+      const C* twl = tw + d.twoff[l];
+      const int pinv = d.pinv[j * d.nT + l];
+      const int bt = b % t;
+      int r;
+      switch (t) {
+        case 2: r = residue_t<2, C, R>(z0, Zl, p, twl, bt, pinv); break;
+        case 3: r = residue_t<3, C, R>(z0, Zl, p, twl, bt, pinv); break;
+        case 5: r = residue_t<5, C, R>(z0, Zl, p, twl, bt, pinv); break;
+        case 7: r = residue_t<7, C, R>(z0, Zl, p, twl, bt, pinv); break;
+        case 11: r = residue_t<11, C, R>(z0, Zl, p, twl, bt, pinv); break;
+        case 13: r = residue_t<13, C, R>(z0, Zl, p, twl, bt, pinv); break;
+        default: r = residue_any<C, R>(t, z0, Zl, p, twl, bt, pinv); break;
+      }
+      d.resid[gid * d.nT + l] = (uint8_t)r;
+      const int g = d.garner[j * d.nT + l];
+      const int xm = mod_small(x, t);
+      const int v = (((r - xm) % t + t) % t) * g % t;
+      x += Mx * v;
+      Mx *= t;
+    }
   }
   const int64_t N = d.N;
   int64_t w = (x <= N / 2) ? x : x - d.Mj[j];
   d.cand[gid] = (w > -((N + 1) / 2)) ? w : kNoFreq;
+}
+
+// The FP32 kernel is held to kIdRegs registers.  The kernel waits on its sub-bin loads, so warps
+// per SM count for more than the few spills of the unrolled chain at this cap: per 64 SFTs at
+// N = 2^26, s = 1000, 64 registers (84 bytes of spills) measured 298 us, 72 (none) 309 us, 80 (none)
+// 347 us, 56 (308 bytes) 298 us.  The FP64 kernel takes what it needs at up to 512 threads per CTA.
+constexpr int kIdRegs = 64;
+
+__global__ void __maxnreg__(kIdRegs) identify_kernel_fp32(BatchView bv) {
+  pdl_begin();
+  identify_bins<float>(bv);
+}
+
+__global__ void __launch_bounds__(kBinMaxThreads, 1) identify_kernel_fp64(BatchView bv) {
+  pdl_begin();
+  identify_bins<double>(bv);
 }
 
 // KCAP: capacity of the per-thread arrays (kFewK in registers, or kMaxK for many primes).
@@ -208,6 +275,9 @@ __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   int qi, j, b;
   decode_bin(d, gid, qi, j, b);
   const int64_t* cq = d.cand + (int64_t)qi * d.Ptot;
+  // All K lookups are issued before any decision: a thread that left at the first match of an
+  // earlier prime, or once the majority was out of reach, waited on each lookup in turn
+  // (118 against 106 us per 64 SFTs).
   int cnt = 0, jmin = d.K;
   int bb[KCAP];
   for (int jj = 0; jj < d.K; ++jj) {
@@ -245,9 +315,9 @@ cudaError_t launch_identify(const DevPlan& d0, const BatchView& bv, const Launch
   BatchView v = bv;
   v.blk = ls.blk[kStBins];
   if (d0.prec == SFT_FP32)
-    (void)launch_pdl(identify_kernel<float>, grid, ls.tune.bin_threads, 0, st, v);
+    (void)launch_pdl(identify_kernel_fp32, grid, ls.tune.bin_threads, 0, st, v);
   else
-    (void)launch_pdl(identify_kernel<double>, grid, ls.tune.bin_threads, 0, st, v);
+    (void)launch_pdl(identify_kernel_fp64, grid, ls.tune.bin_threads, 0, st, v);
   return cudaGetLastError();
 }
 
