@@ -332,14 +332,73 @@ sft_status sft_plan_info(sft_plan_t plan, sft_plan_desc* out);
  *              INT64_MIN when the CRT representative lies outside B.
  *   3 residues uint8 [n_shifts][sum_j p_j][n_small]: residue of bin b modulo each t_l.
  *   4 counters int32 [n_shifts + 4]: entry i < n_shifts is the length of shift i's voted list,
- *              entry n_shifts the length of the pooled in-band list, n_shifts + 2 the winner
- *              count.
+ *              entry n_shifts the length of the pooled in-band list, n_shifts + 1 the status
+ *              word (sft_fault bits), n_shifts + 2 the winner count, n_shifts + 3 the site of
+ *              the first index fault (sft_fault_site).
  *   5 voted    [n_shifts][capacity] records of 32 bytes: int64 frequency, double re and im of the
  *              median estimate (with the (-1)^w factor), int32 vote count, int32 first prime index
  *              that found it; shift i's first counters[i] records are valid, in no fixed order.
  * *bytes receives the buffer size.  Returns SFT_EINVAL for an unknown index.
  */
 sft_status sft_plan_debug_buffer(sft_plan_t plan, int32_t which, void** dev_ptr, size_t* bytes);
+
+/*
+ * Faults the kernels record instead of faulting the GPU.  Each execution clears the plan's status
+ * words first (its first kernel), and a kernel that meets one of these conditions sets its bit
+ * and carries on without the access or record in question, so the result is then incomplete:
+ *   SFT_FAULT_VOTED_FULL  a shift's voted list was full (its capacity is sum_j p_j, which no
+ *                         execution reaches unless lowered by sft_plan_debug_limit); records
+ *                         past it were dropped.
+ *   SFT_FAULT_POOL_FULL   the pooled in-band list (n_shifts * s records) was full.
+ *   SFT_FAULT_INDEX       checked build only (libsft_checked.so, compiled with SFT_CHECKED): an
+ *                         index fell outside its buffer; the access was skipped.  The site of the
+ *                         first such fault is kept (sft_fault_site).
+ * The normal build compiles no index checks; its kernels and results are those of the checked
+ * build whenever the latter records nothing.
+ */
+typedef enum {
+  SFT_FAULT_VOTED_FULL = 1,
+  SFT_FAULT_POOL_FULL = 2,
+  SFT_FAULT_INDEX = 4
+} sft_fault;
+
+typedef enum {
+  SFT_SITE_NONE = 0,
+  SFT_SITE_WINDOW = 1,      /* resampling: a node's window centre j' outside [0, N) */
+  SFT_SITE_DFT = 2,         /* a transform's samples or bins outside the plan's buffers */
+  SFT_SITE_SUBBIN = 3,      /* identification: a bin's sub-bins outside the bins buffer */
+  SFT_SITE_VOTE = 4,        /* vote: a candidate lookup or a median bin outside its buffer */
+  SFT_SITE_REESTIMATE = 5   /* re-estimation: a chunk of samples or a winner outside its buffer */
+} sft_fault_site;
+
+/* 1 when the loaded library is the checked build, else 0. */
+int32_t sft_checked_build(void);
+
+/*
+ * Read the plan's status words after its last execution (by sft_execute or in a batch): enqueues
+ * the read on `stream` and waits for the stream.  *faults receives the sft_fault bits (0: none),
+ * *site the sft_fault_site of the first index fault (0: none); either may be NULL.  SFT_EINVAL on
+ * a NULL plan or while `stream` is being captured into a graph, SFT_ECUDA if the read fails.
+ */
+sft_status sft_plan_faults(sft_plan_t plan, void* stream, int32_t* faults, int32_t* site);
+
+/*
+ * Test hook: lower one of the plan's list capacities so that the kernels' capacity checks can be
+ * exercised (which = 0: the voted list's capacity per shift, 1 <= value <= sum_j p_j; the buffer
+ * keeps its size, so every access stays inside it).  Takes effect for executions by sft_execute
+ * with graph replay off and for batches created afterwards.  SFT_EINVAL on a bad argument.
+ */
+sft_status sft_plan_debug_limit(sft_plan_t plan, int32_t which, int32_t value);
+
+/*
+ * Test hook: the library's device and pinned-host allocations (plans, batches, sft_execute_batch,
+ * the server's arena and slots) go through one counter; after `skip` more of them succeed, the
+ * next `fail` ones report cudaErrorMemoryAllocation without allocating, so that each caller's
+ * SFT_ENOMEM path and rollback can be checked.  sft_debug_fail_allocations(0, 0) turns it off.
+ * Process-wide; not for use while other threads allocate through the library.  SFT_EINVAL on a
+ * negative count.
+ */
+sft_status sft_debug_fail_allocations(int32_t skip, int32_t fail);
 
 /*
  * Residual-energy check of a result (after the execution that produced it, in stream order).  With

@@ -21,6 +21,9 @@ SFT_POOL_ALL, SFT_POOL_SMOOTH = 0, 1
 SFT_DFT_AUTO, SFT_DFT_CHIRP, SFT_DFT_RADER = 0, 1, 2
 SFT_MAX_K, SFT_MAX_SMALL, SFT_MAX_SHIFTS = 512, 12, 32
 BUF_SAMPLES, BUF_BINS, BUF_CAND, BUF_RESID, BUF_COUNTERS, BUF_VOTED = range(6)
+SFT_FAULT_VOTED_FULL, SFT_FAULT_POOL_FULL, SFT_FAULT_INDEX = 1, 2, 4
+(SFT_SITE_NONE, SFT_SITE_WINDOW, SFT_SITE_DFT, SFT_SITE_SUBBIN, SFT_SITE_VOTE,
+ SFT_SITE_REESTIMATE) = range(6)
 
 _STATUS = {0: "SFT_OK", 1: "SFT_EINVAL", 2: "SFT_ENOMEM", 3: "SFT_ECUDA", 4: "SFT_ETIMEOUT",
            5: "SFT_EBUSY"}
@@ -170,11 +173,32 @@ EXPORTS = {
                                               ctypes.POINTER(ctypes.c_int64),
                                               ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]),
+    "sft_checked_build": (ctypes.c_int32, []),
+    "sft_plan_faults": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "sft_plan_debug_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    "sft_debug_fail_allocations": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
 }
 
 
 def lib_path() -> str:
     return _build.LIB
+
+
+_loaded = {}
+
+
+def _open(path: str):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} not built ({path}); "
+                           "run paper_1706_02740_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _loaded[path] = lib
+    return lib
 
 
 def load(path: str | None = None):
@@ -183,15 +207,19 @@ def load(path: str | None = None):
     if _lib is not None:
         return _lib
     path = path or lib_path()
-    if not os.path.exists(path):
-        raise RuntimeError(f"libsft.so not built ({path}); run paper_1706_02740_gb300.build.build()")
-    lib = ctypes.CDLL(path)
-    for name, (res, args) in EXPORTS.items():
-        fn = getattr(lib, name)
-        fn.restype = res
-        fn.argtypes = args
-    _lib = lib
-    return lib
+    _lib = _loaded.get(path) or _open(path)
+    return _lib
+
+
+def use_checked(enable: bool = True):
+    """Send every later call of this module to the checked build, libsft_checked.so (every
+    gather, bin and candidate index range-checked; faults recorded in the plan's status words, see
+    sft_plan_faults), or with enable=False back to libsft.so.  Plans, batches and servers belong
+    to the library that made them: destroy them before switching."""
+    global _lib
+    path = _build.LIB_CHECKED if enable else lib_path()
+    _lib = _loaded.get(path) or _open(path)
+    return _lib
 
 
 def _check(status: int):
@@ -201,6 +229,27 @@ def _check(status: int):
 
 def sft_last_error() -> str:
     return load().sft_last_error().decode()
+
+
+def checked_build() -> bool:
+    """True when calls go to the checked build."""
+    return bool(load().sft_checked_build())
+
+
+def sft_plan_faults(plan: "Plan", stream: int = 0):
+    """(fault bits, site of the first index fault) of the plan's last execution; waits for
+    `stream`."""
+    f, st = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().sft_plan_faults(plan.handle, stream, ctypes.byref(f), ctypes.byref(st)))
+    return f.value, st.value
+
+
+def sft_plan_debug_limit(plan: "Plan", which: int, value: int):
+    _check(load().sft_plan_debug_limit(plan.handle, which, value))
+
+
+def sft_debug_fail_allocations(skip: int, fail: int):
+    _check(load().sft_debug_fail_allocations(skip, fail))
 
 
 def sft_variant_init(**overrides) -> sft_variant:

@@ -1,4 +1,5 @@
 // C ABI (include/sft.h): plan life cycle and the stream-ordered execution of Algorithm 1.
+#include <atomic>
 #include <stdint.h>
 #include <string.h>
 
@@ -6,6 +7,7 @@
 #include <new>
 #include <string>
 
+#include "alloc_hook.h"
 #include "sft_internal.h"
 
 namespace sft {
@@ -180,6 +182,38 @@ namespace sft {
 Plan* sft_plan_internal(sft_plan_t plan) { return &plan->P; }
 }  // namespace sft
 
+namespace sft {
+
+// Allocation-failure injection: after `skip` more allocations succeed, the next `fail` ones
+// return cudaErrorMemoryAllocation without allocating.
+namespace {
+std::atomic<int64_t> g_inject_skip{0}, g_inject_fail{0};
+
+bool inject_failure() {
+  if (g_inject_fail.load() <= 0) return false;
+  if (g_inject_skip.fetch_sub(1) > 0) return false;
+  g_inject_skip.store(0);
+  return g_inject_fail.fetch_sub(1) > 0;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (inject_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  if (inject_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+  return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+  if (inject_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+  return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+}
+
+}  // namespace sft
+
 extern "C" {
 
 sft_status sft_variant_init(sft_variant* v) {
@@ -273,6 +307,66 @@ sft_status sft_plan_debug_buffer(sft_plan_t plan, int32_t which, void** dev_ptr,
     case 5: *dev_ptr = d.voted; *bytes = (size_t)d.nq * d.vcap * sizeof(sft::Voted); return SFT_OK;
     default: sft::set_error("unknown buffer index"); return SFT_EINVAL;
   }
+}
+
+sft_status sft_debug_fail_allocations(int32_t skip, int32_t fail) {
+  if (skip < 0 || fail < 0) { sft::set_error("sft_debug_fail_allocations: negative count"); return SFT_EINVAL; }
+  sft::g_inject_fail.store(0);
+  sft::g_inject_skip.store(skip);
+  sft::g_inject_fail.store(fail);
+  return SFT_OK;
+}
+
+int32_t sft_checked_build(void) {
+#ifdef SFT_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+sft_status sft_plan_faults(sft_plan_t plan, void* stream, int32_t* faults, int32_t* site) {
+  if (!plan) { sft::set_error("plan is NULL"); return SFT_EINVAL; }
+  const sft::DevPlan& d = plan->P.d;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    sft::set_error("sft_plan_faults: the stream is being captured (or cannot be queried)");
+    return SFT_EINVAL;
+  }
+  int32_t w[4] = {0, 0, 0, 0};                 // counters[nq .. nq + 3]
+  e = cudaMemcpyAsync(w, d.counters + d.nq, sizeof(w), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sft::set_error(std::string("sft_plan_faults: read failed: ") + cudaGetErrorString(e));
+    return SFT_ECUDA;
+  }
+  if (faults) *faults = w[1];
+  if (site) *site = w[3];
+  return SFT_OK;
+}
+
+sft_status sft_plan_debug_limit(sft_plan_t plan, int32_t which, int32_t value) {
+  if (!plan) { sft::set_error("plan is NULL"); return SFT_EINVAL; }
+  Plan& P = plan->P;
+  if (which != 0) { sft::set_error("sft_plan_debug_limit: unknown limit"); return SFT_EINVAL; }
+  int64_t built = 0;                           // the voted list's built capacity: sum_j p_j
+  for (int32_t pj : P.primes) built += pj;
+  if (value < 1 || value > built) {
+    sft::set_error("sft_plan_debug_limit: value must be in 1 .. sum_j p_j");
+    return SFT_EINVAL;
+  }
+  P.d.vcap = value;
+  const cudaError_t e = cudaMemcpy(P.d_dev, &P.d, sizeof(sft::DevPlan), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sft::set_error(std::string("sft_plan_debug_limit: upload failed: ") + cudaGetErrorString(e));
+    return SFT_ECUDA;
+  }
+  return SFT_OK;
 }
 
 sft_status sft_execute(sft_plan_t plan, const void* f_dev, int64_t* out_freqs_dev,

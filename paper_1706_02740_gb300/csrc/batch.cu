@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "sft_internal.h"
 
 namespace sft {
@@ -269,7 +270,7 @@ sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n
   const size_t o_prefix = align256(o_plans + sizeof(DevPlan) * (size_t)n);
   const size_t o_ptrs = align256(o_prefix + prefix.size() * sizeof(int32_t));
   const size_t total = align256(o_ptrs + 4 * (size_t)n * sizeof(void*));
-  cudaError_t e = cudaMalloc((void**)&B.dev, total);
+  cudaError_t e = dev_malloc((void**)&B.dev, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -281,8 +282,7 @@ sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n
   for (int i = 0; i < n; ++i) memcpy(blob.data() + o_plans + sizeof(DevPlan) * i, &ps[i]->d, sizeof(DevPlan));
   memcpy(blob.data() + o_prefix, prefix.data(), prefix.size() * sizeof(int32_t));
   e = cudaMemcpy(B.dev, blob.data(), o_ptrs, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&B.pinned, (size_t)kRing * 4 * n * sizeof(void*),
-                                          cudaHostAllocDefault);
+  if (e == cudaSuccess) e = host_alloc((void**)&B.pinned, (size_t)kRing * 4 * n * sizeof(void*));
   for (int i = 0; e == cudaSuccess && i < kRing; ++i)
     e = cudaEventCreateWithFlags(&B.ring_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -290,7 +290,7 @@ sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n
     free_batch(B);
     delete h;
     set_error(std::string("sft_batch_create: set-up failed: ") + cudaGetErrorString(e));
-    return SFT_ECUDA;
+    return e == cudaErrorMemoryAllocation ? SFT_ENOMEM : SFT_ECUDA;
   }
   B.d_plans = reinterpret_cast<DevPlan*>(B.dev + o_plans);
   B.d_prefix = reinterpret_cast<int32_t*>(B.dev + o_prefix);
@@ -505,7 +505,7 @@ sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
   }
   cudaStream_t st = (cudaStream_t)stream;
   char* dev = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&dev, total, st);
+  cudaError_t e = dev_malloc_async((void**)&dev, total, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error(std::string("sft_execute_batch: cudaMallocAsync failed: ") + cudaGetErrorString(e));

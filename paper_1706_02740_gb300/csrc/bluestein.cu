@@ -21,6 +21,7 @@
 #include <mutex>
 #include <string>
 
+#include "checks.cuh"
 #include "cplx.cuh"
 #include "fft_radix.cuh"
 #include "sft_internal.h"
@@ -227,7 +228,8 @@ bluestein_kernel(BatchView bv) {
   const C* vhat = reinterpret_cast<const C*>(d.vhat) + (int64_t)j * M;
   const C* W = reinterpret_cast<const C*>(d.fftw);
   C* s = buf + g * padded_len<M>();
-  const ChirpIO<C> io{in, chirp, vhat, out, active ? p : 0};
+  const bool inside = active && index_ok(d, off + p - 1, (int64_t)d.nq * d.m, SFT_SITE_DFT);
+  const ChirpIO<C> io{in, chirp, vhat, out, inside ? p : 0};
   // p <= M/2: at most 8 (or 7, 6, 5) input elements per thread.  (The unroll factors of this and
   // the filter sweep are the largest that keep the FP32 builds free of register spills.)
 #pragma unroll 4
@@ -434,6 +436,7 @@ __global__ void noalloc_record_kernel(DevPlan* rec, int n, int batch, int M, voi
   rec->chirp = base;
   rec->vhat = base + kNoAllocChirp;
   rec->fftw = base + kNoAllocChirp + kNoAllocMaxM;
+  rec->counters = nullptr;          // no status words
 }
 
 template <int M>

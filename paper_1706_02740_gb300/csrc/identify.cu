@@ -14,6 +14,7 @@
 // w mod p_j' reconstructed exactly w; it is kept when it has more than K/2 votes and is emitted
 // once, by the smallest such j'.  Its estimate is (-1)^w times the componentwise medians of
 // Z_0[w mod p_j'] over all K primes (eq. GSFT_Estimate).
+#include "checks.cuh"
 #include "cplx.cuh"
 #include "select_sort.cuh"
 #include "sft_internal.h"
@@ -196,7 +197,13 @@ __device__ __forceinline__ void identify_bins(const BatchView& bv) {
   int qi, j, b;
   decode_bin(d, gid, qi, j, b);
   const int p = d.p[j];
-  const C* Z = reinterpret_cast<const C*>(d.bins) + (int64_t)qi * d.m + d.nodeoff[j] + b;
+  const int64_t zoff = (int64_t)qi * d.m + d.nodeoff[j] + b;
+  if (!index_ok(d, b, p, SFT_SITE_SUBBIN) ||
+      !index_ok(d, zoff + (int64_t)(d.nsub - 1) * p, (int64_t)d.nq * d.m, SFT_SITE_SUBBIN)) {
+    d.cand[gid] = kNoFreq;
+    return;
+  }
+  const C* Z = reinterpret_cast<const C*>(d.bins) + zoff;
   const C* tw = reinterpret_cast<const C*>(d.twsmall);
   const C z0 = __ldg(Z);
   int64_t x = b;
@@ -282,6 +289,7 @@ __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   int bb[KCAP];
   for (int jj = 0; jj < d.K; ++jj) {
     bb[jj] = mod_p(w, d.p[jj]);
+    if (!index_ok(d, d.poff[jj] + bb[jj], d.Ptot, SFT_SITE_VOTE)) continue;
     if (cq[d.poff[jj] + bb[jj]] == w) {
       ++cnt;
       if (jj < jmin) jmin = jj;
@@ -291,7 +299,8 @@ __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   const C* Zq = reinterpret_cast<const C*>(d.bins) + (int64_t)qi * d.m;
   R re[KCAP], im[KCAP];
   for (int jj = 0; jj < d.K; ++jj) {
-    const C y = Zq[d.nodeoff[jj] + bb[jj]];
+    const C y = index_ok(d, (int64_t)d.nodeoff[jj] + bb[jj], d.m, SFT_SITE_VOTE)
+                    ? Zq[d.nodeoff[jj] + bb[jj]] : czero<C>();
     re[jj] = y.x;
     im[jj] = y.y;
   }
@@ -304,6 +313,7 @@ __global__ void __launch_bounds__(kBinMaxThreads) vote_kernel(BatchView bv) {
   rec.jmin = jmin;
   const int slot = atomicAdd(d.counters + qi, 1);
   if (slot < d.vcap) d.voted[(int64_t)qi * d.vcap + slot] = rec;
+  else record_fault(d, SFT_FAULT_VOTED_FULL, SFT_SITE_NONE);
 }
 
 }  // namespace

@@ -14,6 +14,7 @@
 #include <tuple>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "sft_internal.h"
 
 namespace sft {
@@ -663,7 +664,7 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
       return SFT_ENOMEM;
     }
   } else {
-    e = cudaMalloc((void**)&base, total);
+    e = dev_malloc((void**)&base, total);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error(std::string("cudaMalloc of plan memory failed: ") + cudaGetErrorString(e));

@@ -20,6 +20,7 @@
 // position g^{-m} - 1, from where the p outputs are stored contiguously.
 #include <stdint.h>
 
+#include "checks.cuh"
 #include "cplx.cuh"
 #include "fft_radix.cuh"
 #include "sft_internal.h"
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) rader_kernel(Batc
   const int sub = rem - qi * d.nsub;
   const int p = d.p[j], L = p - 1;
   const int64_t off = (int64_t)qi * d.m + d.nodeoff[j] + (int64_t)sub * p;
+  if (!index_ok(d, off + p - 1, (int64_t)d.nq * d.m, SFT_SITE_DFT)) return;   // whole CTA
   C* bufA = reinterpret_cast<C*>(smem_raw);
   C* bufB = bufA + rader_buf(d.rLmax);
   const int32_t* sch = d.rsched + j * kRaderSched;

@@ -18,6 +18,7 @@
 // 32-bit.
 #include <algorithm>
 
+#include "checks.cuh"
 #include "cplx.cuh"
 #include "select_sort.cuh"
 #include "sft_internal.h"
@@ -88,6 +89,11 @@ __global__ void __launch_bounds__(kReThreads) reestimate_kernel(BatchView bv) {
   const int p = d.p[jj];
   const int k0 = c * kReChunk;
   const int klen = max(0, min(kReChunk, p - k0));
+  // CTA-uniform checks (the checked build): the shift's winner range and the chunk of samples
+  if (!index_ok(d, beg, d.s, SFT_SITE_REESTIMATE) || !index_ok(d, beg + cnt - 1, d.s, SFT_SITE_REESTIMATE) ||
+      !index_ok(d, (int64_t)qi * d.m + d.nodeoff[jj] + k0 + max(klen, 1) - 1, (int64_t)d.nq * d.m,
+                SFT_SITE_REESTIMATE))
+    return;
   float2* S = sm_re;
   float2* Wt = sm_re + kReChunk;
   const float2* src = reinterpret_cast<const float2*>(d.samples) + (int64_t)qi * d.m + d.nodeoff[jj];
@@ -99,6 +105,7 @@ __global__ void __launch_bounds__(kReThreads) reestimate_kernel(BatchView bv) {
   const float4* S4 = reinterpret_cast<const float4*>(S);
   for (int t = threadIdx.x; t < cnt; t += kReThreads) {
     const int r = d.wlist[beg + t];
+    if (!index_ok(d, r, d.s, SFT_SITE_REESTIMATE)) continue;
     const int b = mod_p32(d.winners[r].w, p);
     // The chunk's sum in blocks of 16 consecutive k = k0 + 16 m + j:
     //     sum_m w^{(k0 + 16 m) b} * sum_{j<16} h_{k0 + 16 m + j} w^{j b},   w = e^{-2 pi i / p},

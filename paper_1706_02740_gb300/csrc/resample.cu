@@ -14,6 +14,7 @@
 // |q d0 / (P N)| <= 1/4 and needs no reduction: the FP32 path forms it as the product of the two
 // correctly rounded ratios d0/P and q/N, the FP64 path from the exact integer q d0.  The FP32
 // path keeps FP64 and 64-bit integer division entirely off its instruction stream.
+#include "checks.cuh"
 #include "cplx.cuh"
 #include "sft_internal.h"
 
@@ -170,6 +171,7 @@ resample_kernel(BatchView bv) {
   int j, k1;
   NodeGeom g;
   decode_node(d, node, j, k1, g);
+  if (!index_ok(d, g.jp, d.N, SFT_SITE_WINDOW)) return;
 
   C win[W];
   fetch_window<KAPPA, C, R, IN>(d, f, g.jp, win);
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_gener
   int j, k1;
   NodeGeom g;
   decode_node(d, node, j, k1, g);
+  if (!index_ok(d, g.jp, d.N, SFT_SITE_WINDOW)) return;
   const int KAPPA = d.kappa, W = 2 * KAPPA + 1;
   const R v0 = (R)g.d0 / (R)g.PP;
   const R gam = gamma_of<R>(d), G0 = g0_of<R>(d);

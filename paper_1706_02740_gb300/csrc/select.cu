@@ -13,6 +13,7 @@
 // branches are launched and each checks the list length on the device.
 #include <algorithm>
 
+#include "checks.cuh"
 #include "cplx.cuh"
 #include "select_sort.cuh"
 #include "sft_internal.h"
@@ -48,6 +49,7 @@ __device__ __forceinline__ void pool_append(const DevPlan& d, const Voted& v, in
   pr.pad = 0;
   const int slot = atomicAdd(d.counters + d.nq, 1);
   if (slot < d.nq * d.s) d.pool[slot] = pr;
+  else record_fault(d, SFT_FAULT_POOL_FULL, SFT_SITE_NONE);
 }
 
 __device__ __forceinline__ uint64_t vkey(const Voted& v) {

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "arena.h"
+#include "alloc_hook.h"
 #include "sft_internal.h"
 
 namespace sft {
@@ -53,7 +54,7 @@ class DeviceArena final : public DeviceMemory {
   }
   cudaError_t init(size_t bytes) {
     book_.reset(bytes);
-    cudaError_t e = cudaMalloc((void**)&base_, book_.capacity());
+    cudaError_t e = dev_malloc((void**)&base_, book_.capacity());
     if (e != cudaSuccess) {
       base_ = nullptr;
       return e;
@@ -730,8 +731,8 @@ sft_status sft_server_create(sft_server_t* out, const sft_server_config* cfg) {
     sl->bytes = slot_bytes;
     S.slots.push_back(sl);
     e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&sl->dev, slot_bytes);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl->host, slot_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = dev_malloc((void**)&sl->dev, slot_bytes);
+    if (e == cudaSuccess) e = host_alloc((void**)&sl->host, slot_bytes);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -162,3 +162,40 @@ def test_plan_rejects_bad_moduli(lib):
 def test_execute_rejects_null_and_partial_outputs(lib):
     with pytest.raises(sft.SftError):
         sft.sft_execute(sft.Plan(None), 0, 0, 0, 0, 0)
+
+
+def _header_enum(prefix):
+    text = open(os.path.join(ROOT, "include", "sft.h")).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + prefix + r"\w+)\s*=\s*(\d+)", text)}
+
+
+def test_checked_build_exports_every_declared_symbol(lib):
+    """The checked build (index checks compiled in) is the same ABI; each library says which it
+    is."""
+    import ctypes as C
+    chk = C.CDLL(sft_build.LIB_CHECKED)
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+    chk.sft_checked_build.restype = C.c_int32
+    assert chk.sft_checked_build() == 1
+    assert lib.sft_checked_build() == 0
+
+
+def test_fault_codes_match_header():
+    faults = _header_enum("SFT_FAULT_")
+    sites = _header_enum("SFT_SITE_")
+    assert faults == {"SFT_FAULT_VOTED_FULL": 1, "SFT_FAULT_POOL_FULL": 2, "SFT_FAULT_INDEX": 4}
+    for k, v in faults.items():
+        assert getattr(sft, k) == v
+    assert len(sites) == 6
+    for k, v in sites.items():
+        assert getattr(sft, k) == v
+
+
+def test_fault_hooks_check_their_arguments_on_the_host(lib):
+    with pytest.raises(sft.SftError) as e:
+        sft.sft_debug_fail_allocations(-1, 1)
+    assert e.value.status == sft.SFT_EINVAL
+    sft.sft_debug_fail_allocations(0, 0)
+    assert lib.sft_plan_faults(None, None, None, None) == sft.SFT_EINVAL
+    assert lib.sft_plan_debug_limit(None, 0, 1) == sft.SFT_EINVAL
