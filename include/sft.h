@@ -289,12 +289,36 @@ sft_status sft_batch_get_tuning(sft_batch_t batch, sft_tuning* t);
  * sft_batch_execute; outputs are overwritten), one knob at a time with the others at their best
  * so far, from the per-stage CUDA-event times of `reps` executions per candidate after one
  * untimed execution, and applies the fastest.  The choice is copied to *chosen when it is not
- * NULL.  Synchronous (returns after the device has finished).  Profiling state is restored.
+ * NULL and stored in the tuning table (below) when the batch's plans share one shape class.
+ * Synchronous (returns after the device has finished).  Profiling state is restored.
  */
 sft_status sft_batch_autotune(sft_batch_t batch, const void* const* f_devs,
                               int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
                               int32_t* const* out_count_devs, void* stream, int32_t reps,
                               sft_tuning* chosen);
+
+/*
+ * Table of tuned launch geometries (process-wide, thread-safe; host only, no device call), keyed
+ * by a shape class: floor(log2 N), floor(log2 s), kappa and precision.  sft_batch_autotune stores
+ * its choice under the class of a batch whose plans all share one, and sft_batch_create starts such
+ * a batch from the class's entry (else from sft_tuning_default).  Entries change launch geometry
+ * only, never results.
+ *   _put / _get   set or read the entry of the class of (N, s, kappa, precision); SFT_EINVAL on a
+ *                 bad key or tuning, or (get) when the class has no entry.
+ *   _save         write the table to a text file (a header line, then one line per entry: the
+ *                 four key fields and the tuning's 13 integers, in struct order), through a
+ *                 temporary file renamed over `path`.
+ *   _load         merge the entries of such a file; SFT_EINVAL, nothing merged, on any bad line.
+ *   _size, _clear the number of entries; empty the table.
+ */
+sft_status sft_tuning_table_put(int64_t N, int32_t s, int32_t kappa, int32_t precision,
+                                const sft_tuning* t);
+sft_status sft_tuning_table_get(int64_t N, int32_t s, int32_t kappa, int32_t precision,
+                                sft_tuning* t);
+sft_status sft_tuning_table_save(const char* path);
+sft_status sft_tuning_table_load(const char* path);
+int32_t sft_tuning_table_size(void);
+void sft_tuning_table_clear(void);
 
 /*
  * enable = 1: the next execution captures the batch's kernel launches once as a CUDA graph (on a

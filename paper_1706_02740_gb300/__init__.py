@@ -178,6 +178,14 @@ EXPORTS = {
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sft_plan_debug_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "sft_debug_fail_allocations": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    "sft_tuning_table_put": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.POINTER(sft_tuning)]),
+    "sft_tuning_table_get": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.POINTER(sft_tuning)]),
+    "sft_tuning_table_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "sft_tuning_table_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "sft_tuning_table_size": (ctypes.c_int32, []),
+    "sft_tuning_table_clear": (None, []),
 }
 
 
@@ -573,6 +581,35 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+def tuning_table_put(N: int, s: int, kappa: int, precision: int, tuning: dict):
+    """Store a launch geometry for the shape class of (N, s, kappa, precision)."""
+    t = sft_tuning.from_dict(tuning)
+    _check(load().sft_tuning_table_put(int(N), int(s), int(kappa), int(precision), ctypes.byref(t)))
+
+
+def tuning_table_get(N: int, s: int, kappa: int, precision: int):
+    """The stored launch geometry of that class, or None."""
+    t = sft_tuning()
+    st = load().sft_tuning_table_get(int(N), int(s), int(kappa), int(precision), ctypes.byref(t))
+    return t.as_dict() if st == SFT_OK else None
+
+
+def tuning_table_save(path: str):
+    _check(load().sft_tuning_table_save(os.fsencode(path)))
+
+
+def tuning_table_load(path: str):
+    _check(load().sft_tuning_table_load(os.fsencode(path)))
+
+
+def tuning_table_size() -> int:
+    return int(load().sft_tuning_table_size())
+
+
+def tuning_table_clear():
+    load().sft_tuning_table_clear()
 
 
 def sft_tuning_default() -> dict:

@@ -22,7 +22,7 @@ OUT_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(OUT_CHECKED, "libsft_checked.so")
 SOURCES = ["api.cu", "batch.cu", "plan.cpp", "server.cpp", "resample.cu", "bluestein.cu", "rader.cu",
            "identify.cu",
-           "select.cu", "refine.cu", "energy.cu"]
+           "select.cu", "refine.cu", "energy.cu", "tuning_table.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -16,6 +16,7 @@
 
 #include "alloc_hook.h"
 #include "sft_internal.h"
+#include "tuning_table.h"
 
 namespace sft {
 
@@ -48,6 +49,17 @@ struct Batch {
 };
 
 namespace {
+
+// The shape class of a batch whose plans all share one (the tuning table's key).
+bool batch_key(const std::vector<Plan*>& ps, TuneKey* k) {
+  for (size_t i = 0; i < ps.size(); ++i) {
+    const DevPlan& d = ps[i]->d;
+    const TuneKey ki = tune_key(d.N, d.s, d.kappa, d.prec);
+    if (i == 0) *k = ki;
+    else if (!same_key(*k, ki)) return false;
+  }
+  return !ps.empty();
+}
 
 void drop_graph(Batch& B) {
   if (B.gexec) cudaGraphExecDestroy(B.gexec);
@@ -250,6 +262,11 @@ sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n
   B.n = n;
   B.d0 = a;
   B.ls.tune = default_tuning();
+  {
+    TuneKey key;
+    sft_tuning stored;
+    if (batch_key(ps, &key) && tuning_table_find(key, &stored)) B.ls.tune = stored;
+  }
   B.ls.pmax = 0;
   B.ls.rlmax = 0;
   B.ls.rtpt = 0;
@@ -433,6 +450,8 @@ sft_status sft_batch_autotune(sft_batch_t batch, const void* const* f_devs,
   }
   const sft_status s2 = apply_tuning(B, best);
   if (s == SFT_OK) s = s2;
+  TuneKey key;
+  if (s == SFT_OK && batch_key(B.plans, &key)) tuning_table_store(key, best);
   profile_enable(B.prof, prof_was ? 1 : 0);
   B.graph_on = graph_was;
   if (s == SFT_OK && chosen) *chosen = best;

@@ -244,6 +244,46 @@ def test_autotune_picks_a_valid_tuning_and_keeps_results():
         p.destroy()
 
 
+def test_autotuned_geometry_is_kept_for_batches_of_the_same_class(tmp_path):
+    """sft_batch_autotune stores its choice under the batch's shape class (floor(log2 N),
+    floor(log2 s), kappa, precision); a new batch of that class starts from it, also after the
+    table went through its file; a batch of mixed classes starts from the default."""
+    import torch
+    sft.tuning_table_clear()
+    shapes = [(2 ** 16, 8), (2 ** 16 + 7, 9), (2 ** 17 - 1, 15), (2 ** 16, 12)]
+    plans = [sft.sft_plan(N, s, sft.sft_variant_init(K=5, c_p=5.0, seed=3)) for N, s in shapes]
+    sigs = [make_signal(N, s, 1300 + i, "unit", 30.0) for i, (N, s) in enumerate(shapes)]
+    fs = [torch.from_numpy(as_complex64(g.f)).cuda() for g in sigs]
+    batch = sft.Batch(plans)
+    assert batch.get_tuning() == sft.sft_tuning_default()
+    chosen = sft.autotune_batch_torch(batch, fs, reps=2)
+    assert sft.tuning_table_get(2 ** 16, 8, 6, 0) == chosen
+    batch.destroy()
+    again = sft.Batch(plans[::-1])
+    assert again.get_tuning() == chosen
+    again.destroy()
+    path = str(tmp_path / "tuning.txt")
+    sft.tuning_table_save(path)
+    sft.tuning_table_clear()
+    assert sft.Batch(plans).get_tuning() == sft.sft_tuning_default()
+    sft.tuning_table_load(path)
+    loaded = sft.Batch(plans)
+    assert loaded.get_tuning() == chosen
+    ref = _host(sft.execute_batch_torch(loaded, fs))
+    loaded.destroy()
+    other = sft.sft_plan(2 ** 18, 8, sft.sft_variant_init(K=5, c_p=5.0, seed=3))
+    mixed = sft.Batch(plans + [other])
+    assert mixed.get_tuning() == sft.sft_tuning_default()
+    got = _host(sft.execute_batch_torch(mixed, fs + [fs[0][:0].new_zeros(2 ** 18)]))
+    for (w, c, n), (rw, rc, rn) in zip(got[:4], ref):       # geometry never changes results
+        assert n == rn and np.array_equal(w, rw) and np.array_equal(c, rc)
+    mixed.destroy()
+    other.destroy()
+    for p in plans:
+        p.destroy()
+    sft.tuning_table_clear()
+
+
 def test_invalid_tunings_are_rejected_and_change_nothing():
     shapes, plans, sigs = _mixed_plans(U.FP32)
     batch = sft.Batch(plans)
