@@ -18,7 +18,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle.dsft import Plan, g_hat, nearest_grid, resample
+from oracle.dsft import Plan, g_hat, g_periodic, nearest_grid, resample
 
 
 def _plan(N, kappa, beta):
@@ -94,7 +94,8 @@ def test_wrong_modulation_sign_is_detected():
     assert np.max(np.abs(h - mirrored)) > 0.1
 
 
-@pytest.mark.parametrize("N,P", [(16, 6), (100, 7), (2 ** 20, 3001), (65521, 4099)])
+@pytest.mark.parametrize("N,P", [(16, 6), (100, 7), (2 ** 20, 3001), (65521, 4099),
+                                 (10, 4), (6, 4), (1026, 4), (2 ** 20 + 6, 12)])
 def test_nearest_grid_is_argmin_with_ties_up(N, P):
     k = np.arange(P, dtype=np.int64)
     jp = nearest_grid(N, P, k)
@@ -102,3 +103,46 @@ def test_nearest_grid_is_argmin_with_ties_up(N, P):
     d2 = 2 * k * N - 2 * jp * P
     assert np.all(np.abs(d2) <= P)
     assert np.all(d2 != P)          # a tie would have been rounded up, leaving d2 == -P
+
+
+@pytest.mark.parametrize("N,P", [(10, 4), (6, 4), (1026, 4), (2 ** 20 + 6, 12)])
+def test_nearest_grid_ties_go_up(N, P):
+    """Where kN/P is a half-integer both neighbours are nearest; the reading taken (R6) rounds up."""
+    k = np.arange(P, dtype=np.int64)
+    ties = [kk for kk in k if (2 * kk * N) % (2 * P) == P]
+    assert ties, "this case must contain ties"
+    for kk in ties:
+        assert nearest_grid(N, P, np.array([kk]))[0] == (kk * N + P // 2) // P
+        assert 2 * kk * N - 2 * nearest_grid(N, P, np.array([kk]))[0] * P == -P
+
+
+@pytest.mark.parametrize("N,P,kappa", [(101, 37, 3), (256, 97, 4), (255, 61, 6)])
+@pytest.mark.parametrize("q", [0, 5, -17])
+def test_window_is_the_nearest_samples_brute_force(N, P, kappa, q):
+    """Lemma fewer_points_error's window: for each node x, the 2 kappa + 1 grid points nearest to
+    x (found by sorting all N circular distances), each weighted g(x - y_j) e^{iq(x - y_j)} / N,
+    summed directly.  Nodes where the choice of nearest points ties are skipped.  A window shifted
+    by one sample, a wrong width or a phase of the wrong sign fails this."""
+    rng = np.random.default_rng(N * 7 + P + q)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    c1 = 1.5 * math.sqrt(math.log(N)) / N
+    plan = Plan(N=N, s=1, kappa=kappa, alpha=1.5, beta=1.5, c1=c1, L=N, shifts=[0],
+                primes=[P], small=[])
+    k = np.arange(P)
+    h = resample(f, plan, P, k, q)
+    y = -math.pi + 2 * math.pi * np.arange(N) / N
+    checked = 0
+    for kk in k:
+        x = -math.pi + 2 * math.pi * kk / P
+        diff = x - y
+        dist = np.abs(np.angle(np.exp(1j * diff)))            # circular distance
+        order = np.argsort(dist, kind="stable")
+        w = 2 * kappa + 1
+        if abs(dist[order[w - 1]] - dist[order[w]]) < 1e-9:   # a tie at the window's edge
+            continue
+        sel = order[:w]
+        dd = np.angle(np.exp(1j * diff[sel]))                 # x - y_j in (-pi, pi]
+        ref = np.sum(f[sel] * g_periodic(dd, c1) * np.exp(1j * q * dd)) / N
+        assert abs(h[kk] - ref) <= 1e-12 * np.sum(np.abs(f[sel]) * g_periodic(dd, c1)) / N, kk
+        checked += 1
+    assert checked >= P // 2
