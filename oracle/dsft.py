@@ -381,8 +381,8 @@ def ussft_shift(f: np.ndarray, plan: Plan, q: int) -> ShiftResult:
     z = np.array([median_estimate(Y, plan.primes, int(w)) for w in voted], dtype=np.complex128)
 
     # R_temp: an s-sparse approximation, the s largest |z| (ties: smaller w first, Section 2).
-    order = np.lexsort((voted, -np.abs(z)))[: plan.s]
-    return ShiftResult(q, Y, residues, margins, cand, voted, votes, z, voted[order], z[order])
+    temp_w, temp_z = best_s_term(voted, z, plan.s)
+    return ShiftResult(q, Y, residues, margins, cand, voted, votes, z, temp_w, temp_z)
 
 
 # --------------------------------------------------------------------------------------------
@@ -418,8 +418,8 @@ def dsft(f: np.ndarray, plan: Plan) -> Result:
     pool_w = np.array(pool_w, dtype=np.int64)
     pool_c = np.array(pool_c, dtype=np.complex128)
     pool_q = np.array(pool_q, dtype=np.int64)
-    order = np.lexsort((pool_w, -np.abs(pool_c)))[: plan.s]
-    return Result(pool_w[order], pool_c[order], shifts, pool_w, pool_c, pool_q)
+    out_w, out_c = best_s_term(pool_w, pool_c, plan.s)      # the final choice of Algorithm 1
+    return Result(out_w, out_c, shifts, pool_w, pool_c, pool_q)
 
 
 # --------------------------------------------------------------------------------------------
