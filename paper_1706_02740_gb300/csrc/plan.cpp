@@ -10,6 +10,9 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <stdexcept>
+#include <thread>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -131,18 +134,29 @@ void host_fft_pow2(std::vector<cd>& a) {
     j ^= bit;
     if (i < j) std::swap(a[i], a[j]);
   }
+  // The twiddles e^{-2 pi i k / M}, k < M/2, each computed once: stage len uses entry k (M / len),
+  // whose angle -2 pi k (M / len) / M is the double -2 pi k / len exactly (M / len is a power of
+  // two), so the result is that of computing every stage's twiddles afresh.
+  std::vector<cd> w(M / 2);
+  for (size_t k = 0; k < M / 2; ++k) {
+    const double ang = -2.0 * kPi * (double)k / (double)M;
+    w[k] = cd(cos(ang), sin(ang));
+  }
   for (size_t len = 2; len <= M; len <<= 1) {
+    const size_t step = M / len;
     for (size_t i = 0; i < M; i += len) {
       for (size_t k = 0; k < len / 2; ++k) {
-        double ang = -2.0 * kPi * (double)k / (double)len;
-        cd w(cos(ang), sin(ang));
-        cd u = a[i + k], v = a[i + k + len / 2] * w;
+        const cd u = a[i + k], v = a[i + k + len / 2] * w[k * step];
         a[i + k] = u + v;
         a[i + k + len / 2] = u - v;
       }
     }
   }
 }
+
+// e^{-2 pi i j / n} for j = 0 .. n - 1, by expi_turns (which reduces its argument exactly, so
+// entry (t k) mod n equals expi_turns(-t k, n)).
+std::vector<cd> twiddle_table(int64_t n);
 
 cd expi_turns(int64_t num, int64_t den);
 
@@ -159,11 +173,12 @@ void host_fft(std::vector<cd>& a) {
     for (size_t n = 0; n < Mp; ++n) A[t][n] = a[r * n + t];
     host_fft_pow2(A[t]);
   }
+  const std::vector<cd> W = twiddle_table((int64_t)M);
   for (size_t k = 0; k < Mp; ++k)
     for (int u = 0; u < r; ++u) {
       const int64_t kk = (int64_t)(k + Mp * u);
       cd x = A[0][k];
-      for (int t = 1; t < r; ++t) x += expi_turns(-(int64_t)t * kk, (int64_t)M) * A[t][k];
+      for (int t = 1; t < r; ++t) x += W[((int64_t)t * kk) % (int64_t)M] * A[t][k];
       a[kk] = x;
     }
 }
@@ -173,6 +188,12 @@ cd expi_turns(int64_t num, int64_t den) {
   int64_t r = ((num % den) + den) % den;
   double a = 2.0 * kPi * (double)r / (double)den;
   return cd(cos(a), sin(a));
+}
+
+std::vector<cd> twiddle_table(int64_t n) {
+  std::vector<cd> W(n);
+  for (int64_t j = 0; j < n; ++j) W[j] = expi_turns(-j, n);
+  return W;
 }
 
 // Forward DFT of any length whose prime factors are small, by recursive decimation in time on
@@ -189,11 +210,12 @@ void host_fft_mixed(std::vector<cd>& a) {
     for (int64_t n = 0; n < m; ++n) A[t][n] = a[r * n + t];
     host_fft_mixed(A[t]);
   }
+  const std::vector<cd> W = twiddle_table(L);
   for (int64_t k = 0; k < m; ++k)
     for (int64_t u = 0; u < r; ++u) {
       const int64_t kk = k + m * u;
       cd x = A[0][k];
-      for (int64_t t = 1; t < r; ++t) x += expi_turns(-t * kk, L) * A[t][k];
+      for (int64_t t = 1; t < r; ++t) x += W[(t * kk) % L] * A[t][k];
       a[kk] = x;
     }
 }
@@ -366,6 +388,52 @@ std::shared_ptr<const PrimeTables> prime_tables(int64_t p, int M, bool rader) {
   return T;
 }
 
+std::shared_ptr<const PrimeTables> cached_prime_tables(int64_t p, int M, bool rader) {
+  std::lock_guard<std::mutex> g(g_prime_mu);
+  auto it = g_prime_tables.find(std::make_tuple(p, rader ? 0 : M, rader));
+  return it == g_prime_tables.end() ? nullptr : it->second;
+}
+
+// The tables of every prime of a plan.  A plan for a new length often brings several primes not
+// seen before, each an FFT of up to 16384 points on the host: those are computed concurrently, at
+// most kTableThreads at a time (this thread takes one of each group; a thread that cannot start,
+// or whose computation throws, leaves its prime to this thread afterwards).
+constexpr size_t kTableThreads = 8;
+
+std::vector<std::shared_ptr<const PrimeTables>> all_prime_tables(const std::vector<int32_t>& primes,
+                                                                 int M, bool rader) {
+  std::vector<std::shared_ptr<const PrimeTables>> tabs(primes.size());
+  std::vector<size_t> missing;
+  for (size_t j = 0; j < primes.size(); ++j) {
+    tabs[j] = cached_prime_tables(primes[j], M, rader);
+    if (!tabs[j]) missing.push_back(j);
+  }
+  for (size_t next = 0; next < missing.size(); next += kTableThreads) {
+    const size_t n = std::min(missing.size() - next, kTableThreads);
+    std::vector<std::thread> th;
+    for (size_t i = 1; i < n; ++i) {
+      const size_t j = missing[next + i];
+      try {
+        th.emplace_back([&tabs, &primes, j, M, rader] {
+          try {
+            tabs[j] = prime_tables(primes[j], M, rader);
+          } catch (...) {
+          }
+        });
+      } catch (...) {
+        break;
+      }
+    }
+    tabs[missing[next]] = prime_tables(primes[missing[next]], M, rader);
+    for (auto& t : th) t.join();
+    for (size_t i = 1; i < n; ++i) {
+      const size_t j = missing[next + i];
+      if (!tabs[j]) tabs[j] = prime_tables(primes[j], M, rader);
+    }
+  }
+  return tabs;
+}
+
 template <typename T>
 void put(std::vector<char>& blob, size_t off, const std::vector<cd>& v, bool fp64) {
   if (fp64) {
@@ -383,9 +451,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
-                      const int64_t* primes_in, int32_t n_primes, const int32_t* small_in,
-                      int32_t n_small, DeviceMemory* mem) {
+namespace {
+
+sft_status build_plan_body(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
+                           const int64_t* primes_in, int32_t n_primes, const int32_t* small_in,
+                           int32_t n_small, DeviceMemory* mem) {
   DevPlan& d = P->d;
   memset(&d, 0, sizeof(d));
   if (!v) { set_error("variant is NULL"); return SFT_EINVAL; }
@@ -582,9 +652,9 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
     std::vector<cd> rv(rader ? (size_t)K * pmax : 0, cd(0, 0)), rt(rader ? (size_t)K * pmax : 0, cd(1, 0));
     int32_t* sch = reinterpret_cast<int32_t*>(blob.data() + o_rsch);
     int32_t* perm = reinterpret_cast<int32_t*>(blob.data() + o_rperm);
+    const std::vector<std::shared_ptr<const PrimeTables>> tabs = all_prime_tables(primes, M, rader);
     for (int j = 0; j < K; ++j) {
-      const int64_t p = primes[j];
-      const std::shared_ptr<const PrimeTables> T = prime_tables(p, M, rader);
+      const std::shared_ptr<const PrimeTables>& T = tabs[j];
       std::copy(T->wp.begin(), T->wp.end(), wp.begin() + (size_t)j * pmax);
       if (!rader) {
         std::copy(T->chirp.begin(), T->chirp.end(), ch.begin() + (size_t)j * pmax);
@@ -715,6 +785,8 @@ sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32
   return SFT_OK;
 }
 
+}  // namespace
+
 sft_status choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int64_t* primes_out,
                                        int32_t* K_out, int32_t* small_out, int32_t* n_small_out) {
   if (!primes_out || !K_out || !small_out || !n_small_out) { set_error("NULL output"); return SFT_EINVAL; }
@@ -747,6 +819,24 @@ sft_status choose_moduli(int64_t N, int32_t s, int32_t K, double c_p, uint64_t s
   for (size_t l = 0; l < sm.size(); ++l) small_out[l] = sm[l];
   *n_small_out = (int32_t)sm.size();
   return SFT_OK;
+}
+
+// The plan build's host containers can throw (std::bad_alloc); no exception leaves the library:
+// the device memory taken so far is released and the failure becomes a status.
+sft_status build_plan(Plan* P, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
+                      const int64_t* primes_in, int32_t n_primes, const int32_t* small_in,
+                      int32_t n_small, DeviceMemory* mem) {
+  try {
+    return build_plan_body(P, N, s, v, n_shifts, primes_in, n_primes, small_in, n_small, mem);
+  } catch (const std::bad_alloc&) {
+    free_plan(P);
+    set_error("host allocation failed while building the plan");
+    return SFT_ENOMEM;
+  } catch (const std::exception& e) {
+    free_plan(P);
+    set_error(std::string("plan build failed: ") + e.what());
+    return SFT_EINVAL;
+  }
 }
 
 void free_plan(Plan* P) {
