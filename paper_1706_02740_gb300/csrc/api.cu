@@ -8,6 +8,7 @@
 #include <string>
 
 #include "alloc_hook.h"
+#include "guard.h"
 #include "sft_internal.h"
 
 namespace sft {
@@ -254,18 +255,20 @@ sft_status sft_variant_theorem(sft_variant* v, int64_t N, double r) {
 sft_status sft_plan(sft_plan_t* out, int64_t N, int32_t s, const sft_variant* v, int32_t n_shifts,
                     const int64_t* primes, int32_t n_primes, const int32_t* small_moduli,
                     int32_t n_small) {
-  if (!out) { sft::set_error("out is NULL"); return SFT_EINVAL; }
-  *out = nullptr;
-  sft_plan_s* h = new (std::nothrow) sft_plan_s();
-  if (!h) { sft::set_error("host allocation failed"); return SFT_ENOMEM; }
-  sft_status st = sft::build_plan(&h->P, N, s, v, n_shifts, primes, n_primes, small_moduli, n_small);
-  if (st != SFT_OK) {
-    sft::free_plan(&h->P);
-    delete h;
-    return st;
-  }
-  *out = h;
-  return SFT_OK;
+  return sft::guarded("sft_plan", [&]() -> sft_status {
+    if (!out) { sft::set_error("out is NULL"); return SFT_EINVAL; }
+    *out = nullptr;
+    sft_plan_s* h = new (std::nothrow) sft_plan_s();
+    if (!h) { sft::set_error("host allocation failed"); return SFT_ENOMEM; }
+    sft_status st = sft::build_plan(&h->P, N, s, v, n_shifts, primes, n_primes, small_moduli, n_small);
+    if (st != SFT_OK) {
+      sft::free_plan(&h->P);
+      delete h;
+      return st;
+    }
+    *out = h;
+    return SFT_OK;
+  });
 }
 
 sft_status sft_plan_destroy(sft_plan_t plan) {

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "alloc_hook.h"
+#include "guard.h"
 #include "sft_internal.h"
 #include "tuning_table.h"
 
@@ -245,87 +246,91 @@ struct sft_batch_s {
 extern "C" {
 
 sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n) {
-  using namespace sft;
-  if (!out) {
-    set_error("sft_batch_create: out is NULL");
-    return SFT_EINVAL;
-  }
-  *out = nullptr;
-  std::vector<Plan*> ps;
-  const sft_status chk = check_plans("sft_batch_create", plans, n, ps);
-  if (chk != SFT_OK) return chk;
-  const DevPlan& a = ps[0]->d;
-  sft_batch_s* h = new (std::nothrow) sft_batch_s();
-  if (!h) { set_error("host allocation failed"); return SFT_ENOMEM; }
-  Batch& B = h->B;
-  B.plans = ps;
-  B.n = n;
-  B.d0 = a;
-  B.ls.tune = default_tuning();
-  {
-    TuneKey key;
-    sft_tuning stored;
-    if (batch_key(ps, &key) && tuning_table_find(key, &stored)) B.ls.tune = stored;
-  }
-  B.ls.pmax = 0;
-  B.ls.rlmax = 0;
-  B.ls.rtpt = 0;
-  B.ls.kmax = 0;
-  for (int i = 0; i < n; ++i) {
-    B.ls.pmax = std::max(B.ls.pmax, ps[i]->d.pmax);
-    if (ps[i]->d.rader) B.ls.rlmax = std::max(B.ls.rlmax, ps[i]->d.rLmax);
-    if (ps[i]->d.rader) B.ls.rtpt = std::max(B.ls.rtpt, ps[i]->d.rTpt);
-    B.ls.kmax = std::max(B.ls.kmax, ps[i]->d.K);
-  }
-  std::vector<int32_t> prefix;
-  if (!make_prefixes(ps, B.ls.tune, prefix, B.ls.blocks)) {
-    delete h;
-    set_error("sft_batch_create: batch too large (a launch would exceed 2^31 - 1 blocks)");
-    return SFT_EINVAL;
-  }
-  const size_t o_plans = 0;
-  const size_t o_prefix = align256(o_plans + sizeof(DevPlan) * (size_t)n);
-  const size_t o_ptrs = align256(o_prefix + prefix.size() * sizeof(int32_t));
-  const size_t total = align256(o_ptrs + 4 * (size_t)n * sizeof(void*));
-  cudaError_t e = dev_malloc((void**)&B.dev, total);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    set_error(std::string("sft_batch_create: cudaMalloc failed: ") + cudaGetErrorString(e));
-    return SFT_ENOMEM;
-  }
-  B.device_bytes = total;
-  std::vector<char> blob(o_ptrs, 0);
-  for (int i = 0; i < n; ++i) memcpy(blob.data() + o_plans + sizeof(DevPlan) * i, &ps[i]->d, sizeof(DevPlan));
-  memcpy(blob.data() + o_prefix, prefix.data(), prefix.size() * sizeof(int32_t));
-  e = cudaMemcpy(B.dev, blob.data(), o_ptrs, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = host_alloc((void**)&B.pinned, (size_t)kRing * 4 * n * sizeof(void*));
-  for (int i = 0; e == cudaSuccess && i < kRing; ++i)
-    e = cudaEventCreateWithFlags(&B.ring_ev[i], cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    free_batch(B);
-    delete h;
-    set_error(std::string("sft_batch_create: set-up failed: ") + cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? SFT_ENOMEM : SFT_ECUDA;
-  }
-  B.d_plans = reinterpret_cast<DevPlan*>(B.dev + o_plans);
-  B.d_prefix = reinterpret_cast<int32_t*>(B.dev + o_prefix);
-  B.d_ptrs = reinterpret_cast<void**>(B.dev + o_ptrs);
-  for (int k = 0; k < kStCount; ++k) B.ls.blk[k] = B.d_prefix + (size_t)k * (n + 1);
-  *out = h;
-  return SFT_OK;
+  return sft::guarded("sft_batch_create", [&]() -> sft_status {
+    using namespace sft;
+    if (!out) {
+      set_error("sft_batch_create: out is NULL");
+      return SFT_EINVAL;
+    }
+    *out = nullptr;
+    std::vector<Plan*> ps;
+    const sft_status chk = check_plans("sft_batch_create", plans, n, ps);
+    if (chk != SFT_OK) return chk;
+    const DevPlan& a = ps[0]->d;
+    sft_batch_s* h = new (std::nothrow) sft_batch_s();
+    if (!h) { set_error("host allocation failed"); return SFT_ENOMEM; }
+    Batch& B = h->B;
+    B.plans = ps;
+    B.n = n;
+    B.d0 = a;
+    B.ls.tune = default_tuning();
+    {
+      TuneKey key;
+      sft_tuning stored;
+      if (batch_key(ps, &key) && tuning_table_find(key, &stored)) B.ls.tune = stored;
+    }
+    B.ls.pmax = 0;
+    B.ls.rlmax = 0;
+    B.ls.rtpt = 0;
+    B.ls.kmax = 0;
+    for (int i = 0; i < n; ++i) {
+      B.ls.pmax = std::max(B.ls.pmax, ps[i]->d.pmax);
+      if (ps[i]->d.rader) B.ls.rlmax = std::max(B.ls.rlmax, ps[i]->d.rLmax);
+      if (ps[i]->d.rader) B.ls.rtpt = std::max(B.ls.rtpt, ps[i]->d.rTpt);
+      B.ls.kmax = std::max(B.ls.kmax, ps[i]->d.K);
+    }
+    std::vector<int32_t> prefix;
+    if (!make_prefixes(ps, B.ls.tune, prefix, B.ls.blocks)) {
+      delete h;
+      set_error("sft_batch_create: batch too large (a launch would exceed 2^31 - 1 blocks)");
+      return SFT_EINVAL;
+    }
+    const size_t o_plans = 0;
+    const size_t o_prefix = align256(o_plans + sizeof(DevPlan) * (size_t)n);
+    const size_t o_ptrs = align256(o_prefix + prefix.size() * sizeof(int32_t));
+    const size_t total = align256(o_ptrs + 4 * (size_t)n * sizeof(void*));
+    cudaError_t e = dev_malloc((void**)&B.dev, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      set_error(std::string("sft_batch_create: cudaMalloc failed: ") + cudaGetErrorString(e));
+      return SFT_ENOMEM;
+    }
+    B.device_bytes = total;
+    std::vector<char> blob(o_ptrs, 0);
+    for (int i = 0; i < n; ++i) memcpy(blob.data() + o_plans + sizeof(DevPlan) * i, &ps[i]->d, sizeof(DevPlan));
+    memcpy(blob.data() + o_prefix, prefix.data(), prefix.size() * sizeof(int32_t));
+    e = cudaMemcpy(B.dev, blob.data(), o_ptrs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = host_alloc((void**)&B.pinned, (size_t)kRing * 4 * n * sizeof(void*));
+    for (int i = 0; e == cudaSuccess && i < kRing; ++i)
+      e = cudaEventCreateWithFlags(&B.ring_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(B);
+      delete h;
+      set_error(std::string("sft_batch_create: set-up failed: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? SFT_ENOMEM : SFT_ECUDA;
+    }
+    B.d_plans = reinterpret_cast<DevPlan*>(B.dev + o_plans);
+    B.d_prefix = reinterpret_cast<int32_t*>(B.dev + o_prefix);
+    B.d_ptrs = reinterpret_cast<void**>(B.dev + o_ptrs);
+    for (int k = 0; k < kStCount; ++k) B.ls.blk[k] = B.d_prefix + (size_t)k * (n + 1);
+    *out = h;
+    return SFT_OK;
+  });
 }
 
 sft_status sft_batch_execute(sft_batch_t batch, const void* const* f_devs,
                              int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
                              int32_t* const* out_count_devs, void* stream) {
-  using namespace sft;
-  if (!batch) { set_error("sft_batch_execute: batch is NULL"); return SFT_EINVAL; }
-  Batch& B = batch->B;
-  sft_status s = check_buffers(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs);
-  if (s != SFT_OK) return s;
-  return execute(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs, (cudaStream_t)stream);
+  return sft::guarded("sft_batch_execute", [&]() -> sft_status {
+    using namespace sft;
+    if (!batch) { set_error("sft_batch_execute: batch is NULL"); return SFT_EINVAL; }
+    Batch& B = batch->B;
+    sft_status s = check_buffers(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs);
+    if (s != SFT_OK) return s;
+    return execute(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs, (cudaStream_t)stream);
+  });
 }
 
 sft_status sft_batch_set_tuning(sft_batch_t batch, const sft_tuning* t) {
@@ -346,116 +351,118 @@ sft_status sft_batch_autotune(sft_batch_t batch, const void* const* f_devs,
                               int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
                               int32_t* const* out_count_devs, void* stream, int32_t reps,
                               sft_tuning* chosen) {
-  using namespace sft;
-  if (!batch || reps < 1) { set_error("sft_batch_autotune: need a batch and reps >= 1"); return SFT_EINVAL; }
-  Batch& B = batch->B;
-  sft_status s = check_buffers(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs);
-  if (s != SFT_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool prof_was = B.prof.on, graph_was = B.graph_on;
-  B.graph_on = false;
-  drop_graph(B);
-  s = profile_enable(B.prof, 1);
-  if (s != SFT_OK) return s;
+  return sft::guarded("sft_batch_autotune", [&]() -> sft_status {
+    using namespace sft;
+    if (!batch || reps < 1) { set_error("sft_batch_autotune: need a batch and reps >= 1"); return SFT_EINVAL; }
+    Batch& B = batch->B;
+    sft_status s = check_buffers(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs);
+    if (s != SFT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool prof_was = B.prof.on, graph_was = B.graph_on;
+    B.graph_on = false;
+    drop_graph(B);
+    s = profile_enable(B.prof, 1);
+    if (s != SFT_OK) return s;
 
-  // Mean milliseconds per execution of the stages s0..s1 under tuning t.
-  auto measure = [&](const sft_tuning& t, int s0, int s1, double* ms) -> sft_status {
-    sft_status r = apply_tuning(B, t);
-    double stage[kStages];
-    int32_t cnt = 0;
-    for (int pass = 0; pass < 2 && r == SFT_OK; ++pass) {
-      const int runs = pass == 0 ? 1 : reps;
-      for (int i = 0; i < runs && r == SFT_OK; ++i)
-        r = execute(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs, st);
-      if (r != SFT_OK) break;
-      if (cudaStreamSynchronize(st) != cudaSuccess) {
-        set_error("sft_batch_autotune: execution failed");
-        r = SFT_ECUDA;
-        break;
+    // Mean milliseconds per execution of the stages s0..s1 under tuning t.
+    auto measure = [&](const sft_tuning& t, int s0, int s1, double* ms) -> sft_status {
+      sft_status r = apply_tuning(B, t);
+      double stage[kStages];
+      int32_t cnt = 0;
+      for (int pass = 0; pass < 2 && r == SFT_OK; ++pass) {
+        const int runs = pass == 0 ? 1 : reps;
+        for (int i = 0; i < runs && r == SFT_OK; ++i)
+          r = execute(B, f_devs, out_freqs_devs, out_coefs_devs, out_count_devs, st);
+        if (r != SFT_OK) break;
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+          set_error("sft_batch_autotune: execution failed");
+          r = SFT_ECUDA;
+          break;
+        }
+        r = profile_read(B.prof, stage, &cnt);
       }
-      r = profile_read(B.prof, stage, &cnt);
-    }
-    if (r == SFT_OK) {
-      double sum = 0;
-      for (int k = s0; k <= s1; ++k) sum += stage[k];
-      *ms = sum / (cnt > 0 ? cnt : 1);
-    }
-    return r;
-  };
-  // Keep the fastest of best and the candidates for stages s0..s1.
-  auto try_knob = [&](sft_tuning& best, const std::vector<sft_tuning>& cands, int s0,
-                      int s1) -> sft_status {
-    double best_ms = 0;
-    sft_status r = measure(best, s0, s1, &best_ms);
-    for (size_t i = 0; i < cands.size() && r == SFT_OK; ++i) {
-      std::string why;
-      if (!tuning_valid(cands[i], &why)) continue;
-      double ms = 0;
-      r = measure(cands[i], s0, s1, &ms);
-      if (r == SFT_OK && ms < best_ms) {
-        best_ms = ms;
-        best = cands[i];
+      if (r == SFT_OK) {
+        double sum = 0;
+        for (int k = s0; k <= s1; ++k) sum += stage[k];
+        *ms = sum / (cnt > 0 ? cnt : 1);
       }
-    }
-    return r;
-  };
+      return r;
+    };
+    // Keep the fastest of best and the candidates for stages s0..s1.
+    auto try_knob = [&](sft_tuning& best, const std::vector<sft_tuning>& cands, int s0,
+                        int s1) -> sft_status {
+      double best_ms = 0;
+      sft_status r = measure(best, s0, s1, &best_ms);
+      for (size_t i = 0; i < cands.size() && r == SFT_OK; ++i) {
+        std::string why;
+        if (!tuning_valid(cands[i], &why)) continue;
+        double ms = 0;
+        r = measure(cands[i], s0, s1, &ms);
+        if (r == SFT_OK && ms < best_ms) {
+          best_ms = ms;
+          best = cands[i];
+        }
+      }
+      return r;
+    };
 
-  sft_tuning best = B.ls.tune;
-  std::vector<sft_tuning> cands;
-  // resampling: CTA size and register cap (kappa 4 and 6 only)
-  if (B.d0.kappa == 4 || B.d0.kappa == 6) {
-    for (int th : {128, 256, 512})
-      for (int cap : {0, 1}) {
+    sft_tuning best = B.ls.tune;
+    std::vector<sft_tuning> cands;
+    // resampling: CTA size and register cap (kappa 4 and 6 only)
+    if (B.d0.kappa == 4 || B.d0.kappa == 6) {
+      for (int th : {128, 256, 512})
+        for (int cap : {0, 1}) {
+          sft_tuning t = best;
+          t.resample_threads = th;
+          t.resample_regcap = cap;
+          cands.push_back(t);
+        }
+      s = try_knob(best, cands, 0, 0);
+    }
+    // chirp convolution: transforms per CTA of every length class present, then the FP32 8192 build
+    // (one or two CTAs per SM)
+    for (int c = 0; c < 9 && s == SFT_OK; ++c) {
+      // the lengths with as many threads per transform as 2^(c+6) (2^k and r 2^k share an entry)
+      bool present = false;
+      for (int k = kStBluestein0; k < kStCount; ++k)
+        present |= B.ls.blocks[k] > 0 && fft_tune_class(fft_stage_length(k)) == c;
+      if (!present) continue;
+      const int M = 64 << c, hi = M >= 4096 ? 1 : 4096 / M;
+      if (hi == 1) continue;
+      cands.clear();
+      for (int g = 1; g <= hi; g *= 2) {
         sft_tuning t = best;
-        t.resample_threads = th;
-        t.resample_regcap = cap;
+        t.dft_per_cta[c] = g;
         cands.push_back(t);
       }
-    s = try_knob(best, cands, 0, 0);
-  }
-  // chirp convolution: transforms per CTA of every length class present, then the FP32 8192 build
-  // (one or two CTAs per SM)
-  for (int c = 0; c < 9 && s == SFT_OK; ++c) {
-    // the lengths with as many threads per transform as 2^(c+6) (2^k and r 2^k share an entry)
-    bool present = false;
-    for (int k = kStBluestein0; k < kStCount; ++k)
-      present |= B.ls.blocks[k] > 0 && fft_tune_class(fft_stage_length(k)) == c;
-    if (!present) continue;
-    const int M = 64 << c, hi = M >= 4096 ? 1 : 4096 / M;
-    if (hi == 1) continue;
-    cands.clear();
-    for (int g = 1; g <= hi; g *= 2) {
-      sft_tuning t = best;
-      t.dft_per_cta[c] = g;
-      cands.push_back(t);
+      s = try_knob(best, cands, 1, 1);
     }
-    s = try_knob(best, cands, 1, 1);
-  }
-  if (s == SFT_OK && B.d0.prec == SFT_FP32 && B.ls.blocks[kStBluestein0 + 7] > 0) {
-    cands.clear();
-    sft_tuning t = best;
-    t.dft_two_ctas = 1 - best.dft_two_ctas;
-    cands.push_back(t);
-    s = try_knob(best, cands, 1, 1);
-  }
-  // residues, CRT and vote: bins per CTA
-  if (s == SFT_OK) {
-    cands.clear();
-    for (int th : {128, 256, 512}) {
+    if (s == SFT_OK && B.d0.prec == SFT_FP32 && B.ls.blocks[kStBluestein0 + 7] > 0) {
+      cands.clear();
       sft_tuning t = best;
-      t.bin_threads = th;
+      t.dft_two_ctas = 1 - best.dft_two_ctas;
       cands.push_back(t);
+      s = try_knob(best, cands, 1, 1);
     }
-    s = try_knob(best, cands, 2, 3);
-  }
-  const sft_status s2 = apply_tuning(B, best);
-  if (s == SFT_OK) s = s2;
-  TuneKey key;
-  if (s == SFT_OK && batch_key(B.plans, &key)) tuning_table_store(key, best);
-  profile_enable(B.prof, prof_was ? 1 : 0);
-  B.graph_on = graph_was;
-  if (s == SFT_OK && chosen) *chosen = best;
-  return s;
+    // residues, CRT and vote: bins per CTA
+    if (s == SFT_OK) {
+      cands.clear();
+      for (int th : {128, 256, 512}) {
+        sft_tuning t = best;
+        t.bin_threads = th;
+        cands.push_back(t);
+      }
+      s = try_knob(best, cands, 2, 3);
+    }
+    const sft_status s2 = apply_tuning(B, best);
+    if (s == SFT_OK) s = s2;
+    TuneKey key;
+    if (s == SFT_OK && batch_key(B.plans, &key)) tuning_table_store(key, best);
+    profile_enable(B.prof, prof_was ? 1 : 0);
+    B.graph_on = graph_was;
+    if (s == SFT_OK && chosen) *chosen = best;
+    return s;
+  });
 }
 
 sft_status sft_batch_graph(sft_batch_t batch, int32_t enable) {
@@ -476,83 +483,85 @@ sft_status sft_batch_destroy(sft_batch_t batch) {
 sft_status sft_execute_batch(const sft_plan_t* plans, const void* const* f_devs,
                              int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
                              int32_t* const* out_count_devs, int32_t n, void* stream) {
-  using namespace sft;
-  std::vector<Plan*> ps;
-  sft_status s = check_plans("sft_execute_batch", plans, n, ps);
-  if (s != SFT_OK) return s;
-  if (!f_devs || !out_freqs_devs || !out_coefs_devs || !out_count_devs) {
-    set_error("sft_execute_batch: NULL argument");
-    return SFT_EINVAL;
-  }
-  const DevPlan& d0 = ps[0]->d;
-  const size_t align = d0.input == SFT_IN_C64 ? 8 : 16;
-  for (int i = 0; i < n; ++i) {
-    if (!f_devs[i] || ((uintptr_t)f_devs[i] % align) || !out_freqs_devs[i] || !out_coefs_devs[i] ||
-        !out_count_devs[i]) {
-      set_error("sft_execute_batch: NULL or misaligned pointer for signal " + std::to_string(i));
+  return sft::guarded("sft_execute_batch", [&]() -> sft_status {
+    using namespace sft;
+    std::vector<Plan*> ps;
+    sft_status s = check_plans("sft_execute_batch", plans, n, ps);
+    if (s != SFT_OK) return s;
+    if (!f_devs || !out_freqs_devs || !out_coefs_devs || !out_count_devs) {
+      set_error("sft_execute_batch: NULL argument");
       return SFT_EINVAL;
     }
-  }
-  LaunchSet ls;
-  memset(&ls, 0, sizeof(ls));
-  ls.tune = default_tuning();
-  for (int i = 0; i < n; ++i) {
-    ls.pmax = std::max(ls.pmax, ps[i]->d.pmax);
-    if (ps[i]->d.rader) ls.rlmax = std::max(ls.rlmax, ps[i]->d.rLmax);
-    if (ps[i]->d.rader) ls.rtpt = std::max(ls.rtpt, ps[i]->d.rTpt);
-    ls.kmax = std::max(ls.kmax, ps[i]->d.K);
-  }
-  std::vector<int32_t> prefix;
-  if (!make_prefixes(ps, ls.tune, prefix, ls.blocks)) {
-    set_error("sft_execute_batch: batch too large (a launch would exceed 2^31 - 1 blocks)");
-    return SFT_EINVAL;
-  }
-  // one device array: records | block prefixes | pointer tables, filled from one host image by a
-  // stream-ordered copy (pageable source: staged before the copy call returns)
-  const size_t o_prefix = align256(sizeof(DevPlan) * (size_t)n);
-  const size_t o_ptrs = align256(o_prefix + prefix.size() * sizeof(int32_t));
-  const size_t total = o_ptrs + 4 * (size_t)n * sizeof(void*);
-  std::vector<char> blob(total, 0);
-  for (int i = 0; i < n; ++i) memcpy(blob.data() + sizeof(DevPlan) * i, &ps[i]->d, sizeof(DevPlan));
-  memcpy(blob.data() + o_prefix, prefix.data(), prefix.size() * sizeof(int32_t));
-  void** hp = reinterpret_cast<void**>(blob.data() + o_ptrs);
-  for (int i = 0; i < n; ++i) {
-    hp[i] = const_cast<void*>(f_devs[i]);
-    hp[n + i] = out_freqs_devs[i];
-    hp[2 * n + i] = out_coefs_devs[i];
-    hp[3 * n + i] = out_count_devs[i];
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  char* dev = nullptr;
-  cudaError_t e = dev_malloc_async((void**)&dev, total, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error(std::string("sft_execute_batch: cudaMallocAsync failed: ") + cudaGetErrorString(e));
-    return SFT_ENOMEM;
-  }
-  e = cudaMemcpyAsync(dev, blob.data(), total, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) {
-    for (int k = 0; k < kStCount; ++k)
-      ls.blk[k] = reinterpret_cast<int32_t*>(dev + o_prefix) + (size_t)k * (n + 1);
-    void** dp = reinterpret_cast<void**>(dev + o_ptrs);
-    BatchView bv;
-    memset(&bv, 0, sizeof(bv));
-    bv.plans = reinterpret_cast<DevPlan*>(dev);
-    bv.n = n;
-    bv.f = const_cast<const void* const*>(dp);
-    bv.out_w = reinterpret_cast<int64_t* const*>(dp + n);
-    bv.out_c = reinterpret_cast<double2* const*>(dp + 2 * n);
-    bv.out_n = reinterpret_cast<int32_t* const*>(dp + 3 * n);
-    int launched = 0;
-    e = run_stages(d0, bv, ls, st, nullptr, &launched);
-  }
-  const cudaError_t ef = cudaFreeAsync(dev, st);
-  if (e == cudaSuccess) e = ef;
-  if (e != cudaSuccess) {
-    set_error(std::string("sft_execute_batch: ") + cudaGetErrorString(e));
-    return SFT_ECUDA;
-  }
-  return SFT_OK;
+    const DevPlan& d0 = ps[0]->d;
+    const size_t align = d0.input == SFT_IN_C64 ? 8 : 16;
+    for (int i = 0; i < n; ++i) {
+      if (!f_devs[i] || ((uintptr_t)f_devs[i] % align) || !out_freqs_devs[i] || !out_coefs_devs[i] ||
+          !out_count_devs[i]) {
+        set_error("sft_execute_batch: NULL or misaligned pointer for signal " + std::to_string(i));
+        return SFT_EINVAL;
+      }
+    }
+    LaunchSet ls;
+    memset(&ls, 0, sizeof(ls));
+    ls.tune = default_tuning();
+    for (int i = 0; i < n; ++i) {
+      ls.pmax = std::max(ls.pmax, ps[i]->d.pmax);
+      if (ps[i]->d.rader) ls.rlmax = std::max(ls.rlmax, ps[i]->d.rLmax);
+      if (ps[i]->d.rader) ls.rtpt = std::max(ls.rtpt, ps[i]->d.rTpt);
+      ls.kmax = std::max(ls.kmax, ps[i]->d.K);
+    }
+    std::vector<int32_t> prefix;
+    if (!make_prefixes(ps, ls.tune, prefix, ls.blocks)) {
+      set_error("sft_execute_batch: batch too large (a launch would exceed 2^31 - 1 blocks)");
+      return SFT_EINVAL;
+    }
+    // one device array: records | block prefixes | pointer tables, filled from one host image by a
+    // stream-ordered copy (pageable source: staged before the copy call returns)
+    const size_t o_prefix = align256(sizeof(DevPlan) * (size_t)n);
+    const size_t o_ptrs = align256(o_prefix + prefix.size() * sizeof(int32_t));
+    const size_t total = o_ptrs + 4 * (size_t)n * sizeof(void*);
+    std::vector<char> blob(total, 0);
+    for (int i = 0; i < n; ++i) memcpy(blob.data() + sizeof(DevPlan) * i, &ps[i]->d, sizeof(DevPlan));
+    memcpy(blob.data() + o_prefix, prefix.data(), prefix.size() * sizeof(int32_t));
+    void** hp = reinterpret_cast<void**>(blob.data() + o_ptrs);
+    for (int i = 0; i < n; ++i) {
+      hp[i] = const_cast<void*>(f_devs[i]);
+      hp[n + i] = out_freqs_devs[i];
+      hp[2 * n + i] = out_coefs_devs[i];
+      hp[3 * n + i] = out_count_devs[i];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    char* dev = nullptr;
+    cudaError_t e = dev_malloc_async((void**)&dev, total, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error(std::string("sft_execute_batch: cudaMallocAsync failed: ") + cudaGetErrorString(e));
+      return SFT_ENOMEM;
+    }
+    e = cudaMemcpyAsync(dev, blob.data(), total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      for (int k = 0; k < kStCount; ++k)
+        ls.blk[k] = reinterpret_cast<int32_t*>(dev + o_prefix) + (size_t)k * (n + 1);
+      void** dp = reinterpret_cast<void**>(dev + o_ptrs);
+      BatchView bv;
+      memset(&bv, 0, sizeof(bv));
+      bv.plans = reinterpret_cast<DevPlan*>(dev);
+      bv.n = n;
+      bv.f = const_cast<const void* const*>(dp);
+      bv.out_w = reinterpret_cast<int64_t* const*>(dp + n);
+      bv.out_c = reinterpret_cast<double2* const*>(dp + 2 * n);
+      bv.out_n = reinterpret_cast<int32_t* const*>(dp + 3 * n);
+      int launched = 0;
+      e = run_stages(d0, bv, ls, st, nullptr, &launched);
+    }
+    const cudaError_t ef = cudaFreeAsync(dev, st);
+    if (e == cudaSuccess) e = ef;
+    if (e != cudaSuccess) {
+      set_error(std::string("sft_execute_batch: ") + cudaGetErrorString(e));
+      return SFT_ECUDA;
+    }
+    return SFT_OK;
+  });
 }
 
 sft_status sft_batch_profile(sft_batch_t batch, int32_t enable) {

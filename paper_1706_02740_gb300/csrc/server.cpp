@@ -27,6 +27,7 @@
 
 #include "arena.h"
 #include "alloc_hook.h"
+#include "guard.h"
 #include "sft_internal.h"
 
 namespace sft {
@@ -693,89 +694,93 @@ void sft_server_config_init(sft_server_config* cfg) {
 }
 
 sft_status sft_server_create(sft_server_t* out, const sft_server_config* cfg) {
-  using namespace sft;
-  if (!out || !cfg) { set_error("sft_server_create: NULL argument"); return SFT_EINVAL; }
-  *out = nullptr;
-  if (cfg->mem_budget < ((size_t)1 << 20) || cfg->max_batch < 1 || cfg->max_batch > kMaxServerBatch ||
-      cfg->max_inflight < 1 || cfg->max_inflight > kMaxInflight || cfg->build_threads < 0 ||
-      cfg->build_threads > kMaxBuilders) {
-    set_error("sft_server_create: need mem_budget >= 1 MiB, 1 <= max_batch <= 256, "
-              "1 <= max_inflight <= 8, 0 <= build_threads <= 16");
-    return SFT_EINVAL;
-  }
-  sft_tuning tune = cfg->tune.resample_threads == 0 ? default_tuning() : cfg->tune;
-  std::string why;
-  if (!tuning_valid(tune, &why)) { set_error("sft_server_create: " + why); return SFT_EINVAL; }
-  sft_server_s* h = new (std::nothrow) sft_server_s();
-  if (!h) { set_error("host allocation failed"); return SFT_ENOMEM; }
-  Server& S = h->S;
-  S.cfg = *cfg;
-  S.cfg.tune = tune;
-  memset(&S.stats, 0, sizeof(S.stats));
-  cudaGetDevice(&S.device);
-  cudaError_t e = S.arena.init(cfg->mem_budget);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    set_error(std::string("sft_server_create: arena allocation failed: ") + cudaGetErrorString(e));
-    return SFT_ENOMEM;
-  }
-  const int nb = cfg->max_batch;
-  const size_t slot_bytes = align256(align256(sizeof(DevPlan) * (size_t)nb) +
-                                     sizeof(int32_t) * (size_t)kStCount * (nb + 1)) +
-                            sizeof(void*) * 4 * (size_t)nb;
-  for (int i = 0; i < cfg->max_inflight && e == cudaSuccess; ++i) {
-    Slot* sl = new (std::nothrow) Slot();
-    if (!sl) { e = cudaErrorMemoryAllocation; break; }
-    sl->srv = &S;
-    sl->bytes = slot_bytes;
-    S.slots.push_back(sl);
-    e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = dev_malloc((void**)&sl->dev, slot_bytes);
-    if (e == cudaSuccess) e = host_alloc((void**)&sl->host, slot_bytes);
-  }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    destroy_server(&S);
-    delete h;
-    set_error(std::string("sft_server_create: set-up failed: ") + cudaGetErrorString(e));
-    return SFT_ENOMEM;
-  }
-  S.th = std::thread(scheduler, &S);
-  for (int i = 0; i < cfg->build_threads; ++i) S.builders.emplace_back(builder, &S);
-  *out = h;
-  return SFT_OK;
+  return sft::guarded("sft_server_create", [&]() -> sft_status {
+    using namespace sft;
+    if (!out || !cfg) { set_error("sft_server_create: NULL argument"); return SFT_EINVAL; }
+    *out = nullptr;
+    if (cfg->mem_budget < ((size_t)1 << 20) || cfg->max_batch < 1 || cfg->max_batch > kMaxServerBatch ||
+        cfg->max_inflight < 1 || cfg->max_inflight > kMaxInflight || cfg->build_threads < 0 ||
+        cfg->build_threads > kMaxBuilders) {
+      set_error("sft_server_create: need mem_budget >= 1 MiB, 1 <= max_batch <= 256, "
+                "1 <= max_inflight <= 8, 0 <= build_threads <= 16");
+      return SFT_EINVAL;
+    }
+    sft_tuning tune = cfg->tune.resample_threads == 0 ? default_tuning() : cfg->tune;
+    std::string why;
+    if (!tuning_valid(tune, &why)) { set_error("sft_server_create: " + why); return SFT_EINVAL; }
+    sft_server_s* h = new (std::nothrow) sft_server_s();
+    if (!h) { set_error("host allocation failed"); return SFT_ENOMEM; }
+    Server& S = h->S;
+    S.cfg = *cfg;
+    S.cfg.tune = tune;
+    memset(&S.stats, 0, sizeof(S.stats));
+    cudaGetDevice(&S.device);
+    cudaError_t e = S.arena.init(cfg->mem_budget);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      set_error(std::string("sft_server_create: arena allocation failed: ") + cudaGetErrorString(e));
+      return SFT_ENOMEM;
+    }
+    const int nb = cfg->max_batch;
+    const size_t slot_bytes = align256(align256(sizeof(DevPlan) * (size_t)nb) +
+                                       sizeof(int32_t) * (size_t)kStCount * (nb + 1)) +
+                              sizeof(void*) * 4 * (size_t)nb;
+    for (int i = 0; i < cfg->max_inflight && e == cudaSuccess; ++i) {
+      Slot* sl = new (std::nothrow) Slot();
+      if (!sl) { e = cudaErrorMemoryAllocation; break; }
+      sl->srv = &S;
+      sl->bytes = slot_bytes;
+      S.slots.push_back(sl);
+      e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = dev_malloc((void**)&sl->dev, slot_bytes);
+      if (e == cudaSuccess) e = host_alloc((void**)&sl->host, slot_bytes);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      destroy_server(&S);
+      delete h;
+      set_error(std::string("sft_server_create: set-up failed: ") + cudaGetErrorString(e));
+      return SFT_ENOMEM;
+    }
+    S.th = std::thread(scheduler, &S);
+    for (int i = 0; i < cfg->build_threads; ++i) S.builders.emplace_back(builder, &S);
+    *out = h;
+    return SFT_OK;
+  });
 }
 
 sft_status sft_server_submit(sft_server_t server, int64_t N, int32_t s, const void* f_dev,
                              int64_t* out_freqs_dev, void* out_coefs_dev, int32_t* out_count_dev,
                              sft_request_t* id) {
-  using namespace sft;
-  if (!server || !f_dev || !out_freqs_dev || !out_coefs_dev || !out_count_dev || !id) {
-    set_error("sft_server_submit: NULL argument");
-    return SFT_EINVAL;
-  }
-  Server& S = server->S;
-  const size_t align = S.cfg.variant.input == SFT_IN_C64 ? 8 : 16;
-  if ((uintptr_t)f_dev % align) { set_error("sft_server_submit: f is misaligned"); return SFT_EINVAL; }
-  {
-    std::lock_guard<std::mutex> g(S.mu);
-    if (S.stop) { set_error("sft_server_submit: the server is stopping"); return SFT_EINVAL; }
-    const int64_t rid = S.next_id++;
-    Request& r = S.reqs[rid];
-    r.N = N;
-    r.s = s;
-    r.f = f_dev;
-    r.w = out_freqs_dev;
-    r.c = out_coefs_dev;
-    r.n = out_count_dev;
-    r.t_submit = Clock::now();
-    S.queue.push_back(rid);
-    ++S.stats.submitted;
-    *id = rid;
-  }
-  S.cv.notify_all();
-  return SFT_OK;
+  return sft::guarded("sft_server_submit", [&]() -> sft_status {
+    using namespace sft;
+    if (!server || !f_dev || !out_freqs_dev || !out_coefs_dev || !out_count_dev || !id) {
+      set_error("sft_server_submit: NULL argument");
+      return SFT_EINVAL;
+    }
+    Server& S = server->S;
+    const size_t align = S.cfg.variant.input == SFT_IN_C64 ? 8 : 16;
+    if ((uintptr_t)f_dev % align) { set_error("sft_server_submit: f is misaligned"); return SFT_EINVAL; }
+    {
+      std::lock_guard<std::mutex> g(S.mu);
+      if (S.stop) { set_error("sft_server_submit: the server is stopping"); return SFT_EINVAL; }
+      const int64_t rid = S.next_id++;
+      Request& r = S.reqs[rid];
+      r.N = N;
+      r.s = s;
+      r.f = f_dev;
+      r.w = out_freqs_dev;
+      r.c = out_coefs_dev;
+      r.n = out_count_dev;
+      r.t_submit = Clock::now();
+      S.queue.push_back(rid);
+      ++S.stats.submitted;
+      *id = rid;
+    }
+    S.cv.notify_all();
+    return SFT_OK;
+  });
 }
 
 sft_status sft_server_query(sft_server_t server, sft_request_t id, sft_request_info* info) {
