@@ -713,6 +713,13 @@ def run_batched_workload(args, dev, sft, steps=5, seed=4000):
     ms = a.elapsed_time(b) / steps
     launches = (batch.launches - l0) // steps
     batch.graph(False)
+    # stage times of one direct execution (CUDA events between the stages)
+    batch.profile(True)
+    batch.execute(*ptrs, stream.cuda_stream)
+    torch.cuda.synchronize()
+    st_ms, n_ex = batch.profile_read()
+    batch.profile(False)
+    stages_ms = {k: round(v / max(n_ex, 1), 3) for k, v in st_ms.items()}
     # a sample of the batch against the same plans executed alone (bit for bit)
     got = [(o[0].cpu(), o[1].cpu(), int(o[2].item())) for o in outs]
     idx = list(range(0, len(plans), max(1, len(plans) // 8)))[:8]
@@ -736,6 +743,7 @@ def run_batched_workload(args, dev, sft, steps=5, seed=4000):
                         "of two), s uniform [16, 512], unit magnitude, SNR 20 dB, complex64",
             "signals": n_sig, "sfts_per_s": n_sig * 1e3 / ms, "ms_per_batch": ms,
             "launches_per_batch": launches, "graph": True, "tuning": tuning,
+            "stages_ms_direct": stages_ms,
             "nodes": nodes, "input_gb": in_bytes / 1e9, "plan_gb": plan_bytes / 1e9,
             "setup_s": setup_s, "autotune_s": tune_s,
             "equal_to_single_execution": f"{same}/{len(idx)} sampled signals bit-identical"}
