@@ -99,9 +99,9 @@ def choose_primes(s: int, K: int, c_p: float, seed: int, pool: str = "all") -> l
     """K distinct primes drawn by a seeded partial Fisher-Yates shuffle from a pool of 4K primes
     >= max(ceil(c_p * s), 5); returned ascending.  The Monte Carlo variant reads a random subset of
     the deterministic algorithm's moduli (Lemma SFT_Ident_Coef_Est_in_Noise, second paragraph).
-    pool "all": the 4K smallest primes; pool "smooth" (a choice of this implementation, not the paper's): the 4K smallest
-    primes whose p - 1 has no prime factor above 13 (the measurements are then DFTs of prime
-    length p whose p - 1 is a product of small radices)."""
+    pool "all": the 4K smallest primes; pool "smooth" (a choice of this implementation, not the
+    paper's): the 4K smallest primes whose p - 1 has no prime factor above 13 (the measurements
+    are then DFTs of prime length p whose p - 1 is a product of small radices)."""
     lo = max(int(math.ceil(c_p * s)), 5)
     if pool == "all":
         cands = primes_from(lo, 4 * K)
