@@ -113,7 +113,8 @@ bool check_turns() {
       const cd e = expi_turns(num, den);
       const int64_t r = ((num % den) + den) % den;
       const ld t = 2 * kPiL * (ld)r / (ld)den;
-      const double err = (double)fmaxl(fabsl((ld)e.real() - cosl(t)), fabsl((ld)e.imag() - sinl(t)));
+      const double err =
+          (double)fmaxl(fabsl((ld)e.real() - cosl(t)), fabsl((ld)e.imag() - sinl(t)));
       if (err > worst) worst = err;
     }
   }
@@ -126,7 +127,8 @@ bool check_turns() {
     worst = 0;
     for (size_t k = 0; k < M / 2; ++k) {
       const ld t = 2 * kPiL * (ld)k / (ld)M;
-      const double err = (double)fmaxl(fabsl((ld)w[2 * k] - cosl(t)), fabsl((ld)w[2 * k + 1] + sinl(t)));
+      const double err =
+          (double)fmaxl(fabsl((ld)w[2 * k] - cosl(t)), fabsl((ld)w[2 * k + 1] + sinl(t)));
       if (err > worst) worst = err;
     }
     const double bound = ((M % 8 == 0 ? 3 * M_PI / 4 : 3 * M_PI) + 1) * kEps;
