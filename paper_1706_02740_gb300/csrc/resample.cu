@@ -198,28 +198,63 @@ resample_kernel(BatchView bv) {
   }
 }
 
-// Shifts accumulated together by the wide-window kernel (more shifts run in further groups, the
-// window then read again from cache).
+// Shifts accumulated together by the wide-window kernel (a plan with more runs further groups,
+// the window then read again from cache), and window taps loaded together.
 constexpr int kWideShifts = 16;
-constexpr int kWideChunk = 8;     // window taps loaded together
+constexpr int kWideChunk = 4;
 
-// Any window half-width up to kMaxKappa (theorem-parameter mode): the window in chunks of taps
-// loaded together, the shifts in groups with register accumulators.
+// Taps of the shared shift-phase table: the window width rounded up to whole chunks.
+__host__ __device__ constexpr int wide_taps(int W) { return (W + kWideChunk - 1) / kWideChunk * kWideChunk; }
+
+// Shared-memory bytes of the wide-window kernel's table for nq shifts and half-width kappa.
+template <typename C>
+constexpr size_t wide_table_bytes(int nq, int kappa) {
+  return (size_t)((nq + kWideShifts - 1) / kWideShifts) * kWideShifts * wide_taps(2 * kappa + 1) *
+         sizeof(C);
+}
+
+// The shifts of one group times one tap's weighted sample: acc[t] += x T[t] for the group's 16
+// table entries of the tap (consecutive in shared memory, read 16 bytes at a time).
+__device__ __forceinline__ void wide_macs(float2 (&acc)[kWideShifts], float2 x, const float2* T) {
+  const float4* T4 = reinterpret_cast<const float4*>(T);
+#pragma unroll
+  for (int h = 0; h < kWideShifts / 2; ++h) {
+    const float4 w = T4[h];
+    acc[2 * h] = cadd(acc[2 * h], cmul(x, make_float2(w.x, w.y)));
+    acc[2 * h + 1] = cadd(acc[2 * h + 1], cmul(x, make_float2(w.z, w.w)));
+  }
+}
+__device__ __forceinline__ void wide_macs(double2 (&acc)[kWideShifts], double2 x, const double2* T) {
+#pragma unroll
+  for (int t = 0; t < kWideShifts; ++t) acc[t] = cadd(acc[t], cmul(x, T[t]));
+}
+
+// Any window half-width up to kMaxKappa (theorem-parameter mode).  The shift-phase table
+// e^{-2 pi i (q i mod N) / N} is staged tap-major in shared memory, [group][tap][16 shifts], with
+// zeros for the shifts past nq and the taps past 2 kappa + 1, so the inner loop has no branches:
+// per chunk of taps the window values are loaded first (independent loads in flight), then each
+// weighted sample updates the group's 16 accumulators from its table row (uniform addresses).
 template <typename R, typename IN>
-__global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_generic(BatchView bv) {
+__global__ void __launch_bounds__(kResampleGenericThreads, sizeof(R) == 4 ? 8 : 1)
+resample_kernel_generic(BatchView bv) {
   pdl_begin();
   using C = typename Cx<R>::T;
-  // the shift-phase table e^{-2 pi i (q i mod N) / N} [shifts][taps] in shared memory: every node
-  // reads all of it (uniform addresses)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int lb, nb;
   const int b = batch_signal(bv, lb, nb);
   const DevPlan& d = bv.plans[b];
+  const int KAPPA = d.kappa, W = 2 * KAPPA + 1, WP = wide_taps(W);
+  const int groups = (d.nq + kWideShifts - 1) / kWideShifts;
+  C* Ts = reinterpret_cast<C*>(smem_raw);
   {
     const C* Tg = reinterpret_cast<const C*>(d.Ttab);
-    C* Ts = reinterpret_cast<C*>(smem_raw);
-    const int n = d.nq * (2 * d.kappa + 1);
-    for (int i = threadIdx.x; i < n; i += kResampleGenericThreads) Ts[i] = __ldg(Tg + i);
+    const int n = groups * WP * kWideShifts;
+    for (int e = threadIdx.x; e < n; e += kResampleGenericThreads) {
+      const int t = e % kWideShifts, row = e / kWideShifts;
+      const int g = row / WP, i = row - g * WP;
+      const int q = g * kWideShifts + t;
+      Ts[e] = (q < d.nq && i < W) ? __ldg(Tg + q * W + i) : czero<C>();
+    }
     __syncthreads();
   }
   const int64_t node = (int64_t)lb * kResampleGenericThreads + threadIdx.x;
@@ -229,19 +264,17 @@ __global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_gener
   NodeGeom g;
   decode_node(d, node, j, k1, g);
   if (!index_ok(d, g.jp, d.N, SFT_SITE_WINDOW)) return;
-  const int KAPPA = d.kappa, W = 2 * KAPPA + 1;
   const R v0 = (R)g.d0 / (R)g.PP;
   const R gam = gamma_of<R>(d), G0 = g0_of<R>(d);
-  const C* T = reinterpret_cast<const C*>(smem_raw);
   C* out = reinterpret_cast<C*>(d.samples);
   const int64_t start = g.jp - KAPPA;
   const bool inside = start >= 0 && start + W <= d.N;       // no wrap around the ends of f
-  for (int q0 = 0; q0 < d.nq; q0 += kWideShifts) {
+  for (int gr = 0; gr < groups; ++gr) {
     C acc[kWideShifts];
 #pragma unroll
     for (int t = 0; t < kWideShifts; ++t) acc[t] = czero<C>();
-    for (int i0 = 0; i0 < W; i0 += kWideChunk) {
-      // the chunk's window values first (independent loads in flight), then the arithmetic
+    const C* Tgr = Ts + (size_t)gr * WP * kWideShifts;
+    for (int i0 = 0; i0 < WP; i0 += kWideChunk) {
       C fw[kWideChunk];
 #pragma unroll
       for (int u = 0; u < kWideChunk; ++u) {
@@ -259,18 +292,16 @@ __global__ void __launch_bounds__(kResampleGenericThreads) resample_kernel_gener
 #pragma unroll
       for (int u = 0; u < kWideChunk; ++u) {
         const int i = i0 + u;
-        if (i >= W) break;
         const R v = v0 - (R)(i - KAPPA);
         const C x = cscale(fw[u], G0 * r_exp(-gam * v * v));
-#pragma unroll
-        for (int t = 0; t < kWideShifts; ++t)
-          if (q0 + t < d.nq) acc[t] = cadd(acc[t], cmul(x, T[(q0 + t) * W + i]));
+        wide_macs(acc, x, Tgr + (size_t)i * kWideShifts);
       }
     }
 #pragma unroll
-    for (int t = 0; t < kWideShifts; ++t)
-      if (q0 + t < d.nq)
-        out[(int64_t)(q0 + t) * d.m + node] = cmul(acc[t], node_phase(d, q0 + t, v0, g));
+    for (int t = 0; t < kWideShifts; ++t) {
+      const int q = gr * kWideShifts + t;
+      if (q < d.nq) out[(int64_t)q * d.m + node] = cmul(acc[t], node_phase(d, q, v0, g));
+    }
   }
 }
 
@@ -291,7 +322,7 @@ cudaError_t launch_typed(const DevPlan& d0, const BatchView& bv, const LaunchSet
     else (void)launch_pdl(resample_kernel<4, R, IN, 0>, grid, t, 0, st, v);
   } else {
     // room for the largest shift table of the batch (the signals share kappa; at most kMaxQ shifts)
-    const size_t smem = (size_t)kMaxQ * (2 * d0.kappa + 1) * sizeof(typename Cx<R>::T);
+    const size_t smem = wide_table_bytes<typename Cx<R>::T>(kMaxQ, d0.kappa);
     const cudaError_t e = ensure_dynamic_smem<resample_kernel_generic<R, IN>>(smem);
     if (e != cudaSuccess) return e;
     (void)launch_pdl(resample_kernel_generic<R, IN>, grid, kResampleGenericThreads, smem, st, v);
