@@ -11,7 +11,9 @@ and the true convolution is (g_q * f)(x) = sum_{w in S} c_w g_hat_{w-q} e^{iwx}.
   form to rounding, for any beta: this pins weights, phases, the modulation sign and window
   placement;
 * with Theorem total_convolution_error's parameters (c1 = 6 sqrt(r ln N)/N, half-width
-  ceil(6 r ln N / (sqrt 2 pi)) + 1) the oracle must be within 3 ||f||_inf N^{-r} of the second.
+  ceil(6 r ln N / (sqrt 2 pi)) + 1) the oracle must be within 3 ||f||_inf N^{-r} of the second;
+* node k of modulus p and node k t of modulus p t (the same point) give the same sample, as the
+  subset moduli p_j t_l of the measurements require.
 """
 import math
 
@@ -146,3 +148,23 @@ def test_window_is_the_nearest_samples_brute_force(N, P, kappa, q):
         assert abs(h[kk] - ref) <= 1e-12 * np.sum(np.abs(f[sel]) * g_periodic(dd, c1)) / N, kk
         checked += 1
     assert checked >= P // 2
+
+
+@pytest.mark.parametrize("N,p,t", [(4099, 101, 3), (2 ** 14, 211, 5), (65521, 97, 13),
+                                   (2 ** 20 + 6, 3001, 2)])
+@pytest.mark.parametrize("q", [0, 37, -1234])
+def test_nodes_of_p_are_the_nodes_kt_of_pt(N, p, t, q):
+    """Node k of modulus p and node k t of modulus p t are the same point -pi + 2 pi k / p, and
+    the integers of the window (j', d = k N - j P, q d mod P N) scale by t, so the oracle's
+    samples agree either way up to the rounding of 2 pi d (a few ulp); a modulus taken as P in
+    one place and p in another, or a node index not scaled, gives an error of order one."""
+    rng = np.random.default_rng(N + p + t)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    plan = _plan(N, 6, 1.5)
+    k = np.arange(p)
+    assert np.array_equal(nearest_grid(N, p, k), nearest_grid(N, p * t, k * t))
+    a = resample(f, plan, p, k, q)
+    b = resample(f, plan, p * t, k * t, q)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
+    c = resample(f, plan, p * t, k * t + 1, q)               # the neighbouring nodes differ
+    assert np.max(np.abs(a - c)) > 1e-3 * np.max(np.abs(a))
