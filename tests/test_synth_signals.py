@@ -3,7 +3,8 @@ spectra of Section 5.1 (s distinct frequencies in B = (-ceil(N/2), floor(N/2)], 
 log-uniform magnitudes on [1e-2, 1], uniform phases), the samples as F^{-1} c in Section 2's
 convention (checked by brute force against the DFT matrix F[w, j] = (-1)^w e^{-2 pi i w j / N} / N),
 the noise of Section 5.4 (SNR = 20 log10(||f|| / ||n||) exactly, zero-mean circular Gaussian), the
-per-configuration seeds, the mixed batch shapes and the Poisson request stream."""
+per-configuration seeds, the mixed batch shapes and the Poisson request stream; and the device-side
+generator (run on the CPU device) against the host one."""
 import math
 
 import numpy as np
@@ -130,3 +131,23 @@ def test_request_stream_is_poisson_with_the_stated_ranges():
     assert s.min() >= 8 and s.max() <= 2048 and np.all(s <= N)
     assert snr.min() >= 10 and snr.max() <= 40 and abs(np.mean(snr) - 25) < 0.5
     assert np.mean(N % 2 == 1) > 0.4                                   # arbitrary integers
+
+
+@pytest.mark.parametrize("N,s,mag", [(1024, 8, "unit"), (3 ** 7, 12, "loguniform"),
+                                     (4099, 5, "unit")])
+def test_device_generator_follows_the_same_recipe(N, s, mag):
+    """synth.device_signals (run here on the CPU device): noiseless it is the host generator's
+    signal; with noise it keeps the spectrum and meets the SNR exactly; the FFT-free direct sum
+    (any N up to 2^31 - 1) gives the same samples, across chunk boundaries."""
+    torch = pytest.importorskip("torch")
+    from synth.device_signals import make_device_signal, make_device_sparse_signal_direct
+    host = make_signal(N, s, seed=N + 1, magnitude=mag)
+    f, w, c = make_device_signal(N, s, N + 1, mag, None, device="cpu", dtype=torch.complex128)
+    assert np.array_equal(w, host.omega) and np.array_equal(c, host.coef)
+    assert np.max(np.abs(f.numpy() - host.f)) <= 1e-12 * np.max(np.abs(host.f))
+    fn, _, _ = make_device_signal(N, s, N + 1, mag, 20.0, device="cpu", dtype=torch.complex128)
+    noise = fn.numpy() - f.numpy()
+    assert abs(20 * math.log10(np.linalg.norm(f.numpy()) / np.linalg.norm(noise)) - 20.0) < 1e-9
+    d = make_device_sparse_signal_direct(N, w, c, device="cpu", chunk=1000)
+    assert d.dtype == torch.complex64
+    assert np.max(np.abs(d.numpy() - host.f)) <= 1e-6 * np.max(np.abs(host.f))
