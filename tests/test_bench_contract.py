@@ -1,5 +1,6 @@
 """The benchmark's reference arm runs on the host alone (it times the oracle): its one JSON line
-carries the keys the measurement contract names, with the oracle described as the baseline."""
+carries the keys the measurement contract names, with the oracle described as the baseline; under
+torchrun only rank 0 prints it."""
 import json
 import os
 import subprocess
@@ -25,3 +26,24 @@ def test_reference_arm_prints_one_complete_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["N"] == 2 ** 26 and d["config"]["s"] == 1000
+
+
+def test_reference_arm_under_torchrun_prints_once_from_rank_0():
+    """Launched as the multi-GPU contract launches it (torchrun, one process per rank), rank 0
+    alone runs the oracle and prints the line; the other rank exits 0 without work."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                          "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                          "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                          "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
+                          "--N", "65536"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["config"]["N"] == 65536 and d["config"]["s"] == 1000
