@@ -199,3 +199,20 @@ def test_fault_hooks_check_their_arguments_on_the_host(lib):
     sft.sft_debug_fail_allocations(0, 0)
     assert lib.sft_plan_faults(None, None, None, None) == sft.SFT_EINVAL
     assert lib.sft_plan_debug_limit(None, 0, 1) == sft.SFT_EINVAL
+
+
+def test_missing_library_fails_loudly():
+    """No fallback: with the compiled library absent, the first call into the module raises."""
+    import subprocess
+    import sys
+    code = ("import paper_1706_02740_gb300 as s, paper_1706_02740_gb300.build as b\n"
+            "b.LIB = '/nonexistent/libsft.so'\n"
+            "try:\n"
+            "    s.sft_variant_init()\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert "raised:" in out.stdout and "not built" in out.stdout
