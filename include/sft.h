@@ -222,6 +222,12 @@ sft_status sft_choose_moduli_deterministic(int64_t N, int32_t s, double c_p, int
  */
 typedef struct sft_batch_s* sft_batch_t;
 
+/* Create a batch of plans[0..n) (1 <= n <= 2^20); *out receives the handle, which the caller owns
+ * and releases with sft_batch_destroy (the plans stay the caller's).  Starts from the tuning
+ * table's entry for the plans' shape class, else sft_tuning_default.  On failure *out is NULL and
+ * nothing is held: SFT_EINVAL for a NULL argument, a NULL or repeated plan, plans that differ in
+ * precision, input type, kappa or refine_fp64, or a launch that would exceed 2^31 - 1 blocks;
+ * SFT_ENOMEM when device or pinned host memory cannot be had; SFT_ECUDA on another failed call. */
 sft_status sft_batch_create(sft_batch_t* out, const sft_plan_t* plans, int32_t n);
 
 /*
@@ -234,6 +240,8 @@ sft_status sft_batch_execute(sft_batch_t batch, const void* const* f_devs,
                              int64_t* const* out_freqs_devs, void* const* out_coefs_devs,
                              int32_t* const* out_count_devs, void* stream);
 
+/* Release the batch's device and host resources (NULL is a no-op; its plans are not touched).
+ * The caller must ensure no execution of the batch is still running on the GPU. */
 sft_status sft_batch_destroy(sft_batch_t batch);
 
 /*
@@ -282,6 +290,7 @@ void sft_tuning_default(sft_tuning* t);
  * device to finish (cudaDeviceSynchronize) before it rewrites the batch's launch tables, and drops
  * a captured graph (sft_batch_graph recaptures at the next execution). */
 sft_status sft_batch_set_tuning(sft_batch_t batch, const sft_tuning* t);
+/* Copy the batch's current launch geometry to *t (SFT_EINVAL for a NULL argument). */
 sft_status sft_batch_get_tuning(sft_batch_t batch, sft_tuning* t);
 
 /*
@@ -329,7 +338,9 @@ void sft_tuning_table_clear(void);
  */
 sft_status sft_batch_graph(sft_batch_t batch, int32_t enable);
 
-/* Per-stage timing and launch count of a batch, as sft_plan_profile / _read / _launches. */
+/* Per-stage timing and launch count of a batch, as sft_plan_profile / _read / _launches
+ * (SFT_EINVAL for a NULL argument; _launches is 0 for NULL), and the device bytes the batch holds
+ * beside its plans (0 for NULL). */
 sft_status sft_batch_profile(sft_batch_t batch, int32_t enable);
 sft_status sft_batch_profile_read(sft_batch_t batch, double* stage_ms, int32_t* n_executions);
 int64_t sft_batch_launches(sft_batch_t batch);
@@ -551,6 +562,7 @@ sft_status sft_server_poll(sft_server_t server, sft_request_t id, int32_t* done)
 /* Forget a finished request's record (SFT_EBUSY while it is queued or running). */
 sft_status sft_server_release(sft_server_t server, sft_request_t id);
 
+/* Snapshot of the server's counters and arena usage into *out (SFT_EINVAL for a NULL argument). */
 sft_status sft_server_stats_read(sft_server_t server, sft_server_stats* out);
 
 /* Finish every queued and running request, stop the scheduler, free everything. */
