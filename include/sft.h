@@ -284,6 +284,7 @@ typedef struct {
   int32_t dft_two_ctas;
 } sft_tuning;
 
+/* Fill *t with the built-in launch geometry (host only; a NULL t is ignored). */
 void sft_tuning_default(sft_tuning* t);
 
 /* Validate and apply a launch geometry (SFT_EINVAL, nothing changed, if invalid).  Waits for the

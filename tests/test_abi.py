@@ -216,3 +216,25 @@ def test_missing_library_fails_loudly():
                          timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert "raised:" in out.stdout and "not built" in out.stdout
+
+
+def test_every_entry_point_is_documented_in_the_header():
+    """Each sft_* declaration of include/sft.h follows a comment block (declarations grouped under
+    one comment share it), so no entry point goes without its argument, ownership and error
+    description."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lines = open(os.path.join(root, "include", "sft.h")).read().split("\n")
+    decl = re.compile(r"^(?:sft_status|void|const char\s*\*|int32_t|int64_t|size_t|double|int)"
+                      r"\s+\**(sft_\w+)\s*\(")
+    contin = re.compile(r"^\s{4,}\S")
+    undocumented = []
+    for i, ln in enumerate(lines):
+        m = decl.match(ln)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and (decl.match(lines[j]) or contin.match(lines[j])):
+            j -= 1
+        if j < 0 or not lines[j].rstrip().endswith("*/"):
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
